@@ -1,0 +1,430 @@
+"""Benchmark: spinor-steps/s of the split-operator massless-Dirac solve on GB300.
+
+Workload (default): the Landau-Zener-Stueckelberg scan -- a 2048x2048 momentum
+grid on [-10,10]^2 eV, 20-cycle sin^2 x-linear pulse, 1e5 time steps, seeded
+(omega, E0) samples; each benchmark step is one whole solve of one sample
+(evolve all steps, fused projection, density reduction), FP32-mixed.  The
+FP64 solve of the same workload is timed beside it.  Inputs are synthetic.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1607_03062_gb300 import workloads as W  # noqa: E402
+
+METRIC = "spinor-steps/s"
+N_SAMPLES = 8
+# FP32 lanes per SM and SMs of a GB300; nominal FP64 rate 1.25 TFLOP/s.
+SMS = 152
+FP32_LANES_PER_SM = 128
+FP64_NOMINAL_FLOPS = 1.25e12
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--grid", type=int, default=2048)
+    ap.add_argument("--time-steps", type=int, default=100_000)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 leg")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-warmup", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# helpers
+# ------------------------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------------------------------
+# FP32-mixed instruction count per spinor-step (the kernel's formulation, EXACT scheme):
+#   P = p + A (hi and lo)            4
+#   theta^2 with the lo correction   5
+#   cos - 1 (degree D Horner)        D
+#   sin/theta (degree D Horner)      D
+#   valley sign                      1
+#   q = sinc * (P_y + i P_x)         4
+#   (U - I) psi + lo                 12
+#   Fast2Sum of the 4 components     12
+# FP64 per spinor-step: 2 + 2 + (D + 1) + D + 1 + 2 + 12.
+# ------------------------------------------------------------------------------------------
+
+def ops_mixed(D):
+    return 38 + 2 * D
+
+
+def ops_fp64(D):
+    return 20 + 2 * D
+
+
+def degree_for(theta_max, fp64):
+    """Mirrors the library's degree choice to report the instruction count."""
+    import math
+    x = theta_max * theta_max
+    tol = 2.0 ** -54 if fp64 else 2.0 ** -26
+    for D in ((5, 8, 13) if fp64 else (3, 5, 9)):
+        ec = 2.0 * x ** D / math.factorial(2 * D + 2)
+        es = x ** (D + 1) / math.factorial(2 * D + 3)
+        if ec < tol and es < tol:
+            return D
+    return 13 if fp64 else 9
+
+
+def theta_max_of(cfg, a_mid, dt):
+    g = cfg["grid"]
+    cx = np.array(g["px"])[:, None]
+    cy = np.array(g["py"])[:, None]
+    m = 0.0
+    for x in cx:
+        for y in cy:
+            m = max(m, float(np.hypot(x + a_mid[:, 0], y + a_mid[:, 1]).max()))
+    return dt * m
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1607_03062_gb300 import binding as B
+    from paper_1607_03062_gb300 import build as Bd
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        Bd.build()
+    if world > 1:
+        dist.barrier()
+    B.lib()
+
+    n = args.grid
+    nsteps = args.time_steps
+    cfgs = [W.config_lzs_2048(s, n=n, steps=nsteps) for s in range(N_SAMPLES)]
+    tables = [B.sample_pulse(c["pulse"], nsteps) for c in cfgs]
+    g0 = cfgs[0]["grid"]
+    stream = torch.cuda.current_stream()
+    st_ptr = stream.cuda_stream
+
+    def make(prec):
+        nbytes = B.state_bytes(n, n, prec)
+        state = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+        mdt = torch.float64 if prec == "fp64" else torch.float32
+        mp = torch.empty((n, n), dtype=mdt, device="cuda")
+        h = B.create_grid(n, n, g0["px"], g0["py"], prec, "exact", 1, st_ptr, state.data_ptr(),
+                          nbytes)
+        return h, state, mp
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed_solves(prec, warm, steps, sample_offset):
+        h, state, mp = make(prec)
+        dens = []
+        times = []
+        for k in range(warm + steps):
+            s = (sample_offset + k * world + rank) % N_SAMPLES
+            a_mid, a_in, a_out, dt = tables[s]
+            B.set_pulse(h, a_mid, dt, a_in, a_out)
+            flush.fill_(float(k))  # evict the previous solve from L2
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.solve(h, mp.data_ptr(), want_density=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= warm:
+                times.append(e0.elapsed_time(e1) / 1e3)
+                dens.append(B.reduce_density(h))
+        B.destroy_grid(h)
+        del state, mp
+        return times, dens
+
+    sampler = ClockSampler(local)
+    # ---- FP32-mixed (headline) ----
+    sampler.start()
+    t_mixed, d_mixed = timed_solves("fp32_mixed", args.warmup, args.steps, 0)
+    clocks = sampler.stop()
+    tot = sum(t_mixed)
+    if world > 1:
+        t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    work_per_solve = float(n) * n * nsteps
+    value = work_per_solve * args.steps * world / tot
+
+    # ---- FP64 ----
+    fp64 = None
+    if not args.no_fp64:
+        # offset so the FP64 leg's timed samples are the FP32-mixed leg's first ones
+        t64, d64 = timed_solves("fp64", args.fp64_warmup, args.fp64_steps,
+                                (args.warmup - args.fp64_warmup) * world)
+        tt = sum(t64)
+        if world > 1:
+            t = torch.tensor([tt], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tt = float(t.item())
+        fp64 = {"value": work_per_solve * args.fp64_steps * world / tt, "unit": METRIC,
+                "ms_per_step": 1e3 * tt / args.fp64_steps, "steps": args.fp64_steps,
+                "warmup": args.fp64_warmup}
+        # density of the same samples in both precisions (sample k*world+rank)
+        rels = [abs(a - b) / b for a, b in zip(d_mixed, d64) if b > 0]
+        fp64["density_rel_diff_vs_fp32_mixed"] = max(rels) if rels else None
+
+    # ---- end to end through the host-buffer entry point ----
+    e2e = None
+    h = B.create_grid(n, n, g0["px"], g0["py"], "fp32_mixed", "exact", 1, st_ptr)
+    host_map = np.empty((n, n), dtype=np.float32)
+    e2e_t = []
+    for k in range(1 + args.steps):
+        s = (k * world + rank) % N_SAMPLES
+        a_mid, a_in, a_out, dt = tables[s]
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.solve_host(h, a_mid, dt, a_in, a_out, host_map)
+        t1 = time.perf_counter()
+        if k >= 1:
+            e2e_t.append(t1 - t0)
+    B.destroy_grid(h)
+    e2e_tot = sum(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_tot], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    e2e = {"value": work_per_solve * args.steps * world / e2e_tot, "unit": METRIC,
+           "h2d_bytes_per_step": 16 * nsteps + 2 * 16,
+           "d2h_bytes_per_step": 4 * n * n + 16,
+           "note": "dsp_solve_host: host midpoint table in, host |c+|^2 map and density out"}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the evolve kernel (FP32 pipe) ----
+    peaks = load_peaks()
+    th = max(theta_max_of(c, t[0], t[3]) for c, t in zip(cfgs, tables))
+    D = degree_for(th, False)
+    ops_step = ops_mixed(D)
+    launch_s = statistics.mean(t_mixed)
+    achieved = ops_step * work_per_solve / launch_s / 1e12
+    sm_max = SM_MAX_MHZ_NOMINAL
+    peak = SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "Tinst/s (FP32 lane instructions)", "frac": achieved / peak,
+            "traffic": None, "kernel": "evolve_mixed_kernel",
+            "ops_per_spinor_step": ops_step, "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz"}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (SMS * FP32_LANES_PER_SM *
+                                                     clocks["sm_mhz"] * 1e6 / 1e12)
+    if fp64:
+        D64 = degree_for(th, True)
+        a64 = ops_fp64(D64) * fp64["value"] / world / 1e12
+        fp64["roofline"] = {"bound": "alu", "achieved": a64,
+                            "peak": FP64_NOMINAL_FLOPS / 2 / 1e12,
+                            "unit": "T FP64 inst/s", "frac": a64 / (FP64_NOMINAL_FLOPS / 2 / 1e12),
+                            "ops_per_spinor_step": ops_fp64(D64),
+                            "peak_basis": "nominal 1.25 TFLOP/s FP64 = 0.625 T DFMA/s"}
+
+    # ---- CPU baseline: the oracle on a bounded sample ----
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfgs[0], args.cpu_seconds, nsteps)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (compensated hi/lo; FP64 set-up)",
+        "data": "synthetic (seeded pulses; no dataset)",
+        "config": {"workload": f"lzs_scan_{n}x{n}_{nsteps}_steps_fp32_mixed",
+                   "grid": [n, n], "p_range_eV": [-10, 10], "time_steps": nsteps,
+                   "pulse": "20-cycle sin^2, x-linear, (omega, E0) ~ U[0.5,3] x U[0.2,6], seed 1607",
+                   "samples_rotated": N_SAMPLES, "scheme": "exact midpoint exponential",
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world} (independent samples per rank)"},
+        "density_first_step": d_mixed[0] if d_mixed else None,
+        "fp64": fp64, "e2e": e2e, "gpu_launches": 2 * args.steps,
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+        "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ------------------------------------------------------------------------------------------
+
+def oracle_rate(cfg, n_points, nsteps, seed=5):
+    from oracle import oracle
+    g = cfg["grid"]
+    a_mid, a_in, a_out, dt = oracle.pulse_table(cfg["pulse"], nsteps)
+    idx = W.sample_points(g["nx"], g["ny"], n_points, seed=seed)
+    xs = oracle.grid_nodes(*g["px"], g["nx"])
+    ys = oracle.grid_nodes(*g["py"], g["ny"])
+    t0 = time.perf_counter()
+    oracle.solve_points(xs[idx % g["nx"]], ys[idx // g["nx"]], a_mid, dt, a_in, a_out)
+    el = time.perf_counter() - t0
+    return n_points * nsteps / el, el
+
+
+def cpu_baseline(cfg, seconds, nsteps):
+    from oracle import oracle
+    cores = oracle.max_threads()
+    rate, _ = oracle_rate(cfg, 256, nsteps)
+    pts = int(max(256, min(cfg["grid"]["nx"] ** 2, rate * seconds / nsteps)))
+    rate, el = oracle_rate(cfg, pts, nsteps)
+    return {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{pts} seeded points of the {cfg['grid']['nx']}^2 grid x {nsteps} steps "
+                      f"(sample 0), {el:.1f} s, FP64, OpenMP over points"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    n, nsteps = args.grid, args.time_steps
+    cfg = W.config_lzs_2048(0, n=n, steps=nsteps)
+    from oracle import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    per_step_s = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    rate, _ = oracle_rate(cfg, 256, nsteps)
+    pts = int(max(64, min(n * n, rate * per_step_s / nsteps)))
+    times = []
+    for k in range(args.warmup + args.steps):
+        r, el = oracle_rate(cfg, pts, nsteps, seed=100 + k)
+        if k >= args.warmup:
+            times.append(el)
+    tot = sum(times)
+    value = pts * nsteps * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded pulses; no dataset)",
+            "config": {"workload": f"lzs_scan_{n}x{n}_{nsteps}_steps_fp32_mixed", "grid": [n, n],
+                       "time_steps": nsteps},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                             "sample": f"{pts} seeded points x {nsteps} steps per step"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

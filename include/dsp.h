@@ -1,0 +1,242 @@
+/*
+ * dsp.h -- C ABI of the GB300 split-operator solver for pair production in
+ * graphene (massless Dirac equation in momentum space, arXiv 1607.03062).
+ *
+ * Units: hbar = v_F = e = 1; momenta and energies in eV, time in hbar/eV.
+ *
+ * What the library computes (the paper's method, Sec. II and III):
+ *   every grid momentum p carries an independent two-component spinor psi(p).
+ *   It starts as the negative-energy free spinor v(p + A_in) (Sec. II, Eq.
+ *   (free_spin1..4), normalised to 1) and is stepped N times by the midpoint
+ *   exponential of Sec. III, Eq. (approx_time) in its closed form
+ *       U_n = I cos(dt |P_n|) - i (valley sigma.P_n / |P_n|) sin(dt |P_n|),
+ *       P_n = p + A(t_i + (n + 1/2) dt).
+ *   The result is projected on the positive-energy spinor u(p + A_out),
+ *   |c+(p)|^2 = |u^dag psi(t_f)|^2, and reduced to the pair density of Sec. II
+ *   Eq. (pair_prod_homo) with degeneracy 4 (spin x valley):
+ *       n = 4/(2 pi)^2 * hx * hy * sum_p |c+(p)|^2        [eV^2].
+ *
+ * Grid: nx by ny cell-centred nodes, p_x(i) = px_min + (i + 1/2)(px_max - px_min)/nx,
+ * same for y; arrays are row-major [ny][nx] with x fastest.
+ *
+ * Conventions for every entry point:
+ *   - returns a dsp_status and never aborts or traps; inputs are validated
+ *     before anything is launched;
+ *   - host arrays passed in are copied before the call returns and never kept;
+ *   - device pointers passed in are owned by the caller and must stay valid
+ *     until the work queued on the grid's stream has finished;
+ *   - work is queued on the grid's CUDA stream (the stream given at creation;
+ *     NULL means the legacy default stream); only dsp_reduce_density, dsp_solve,
+ *     dsp_solve_host and the server's step synchronise with the host;
+ *   - a CUDA error is latched in the handle: that call and every later call on
+ *     the handle return DSP_E_CUDA (destroy still frees what it can);
+ *   - handles are not thread safe: one host thread per handle at a time.
+ */
+#ifndef DSP_H
+#define DSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t dsp_status;
+#define DSP_OK 0
+#define DSP_E_INVALID (-1) /* a bad argument (NaN, size, enum, NULL ...)          */
+#define DSP_E_NOMEM (-2)   /* device or host allocation failed, or over budget    */
+#define DSP_E_CUDA (-3)    /* a CUDA call failed (latched in the handle)          */
+#define DSP_E_STATE (-4)   /* call out of order (no pulse, steps past the end ...) */
+#define DSP_E_CFL (-5)     /* dt * max|p + A| > pi: the step condition of Sec. III */
+#define DSP_E_TIMEOUT (-6) /* a bounded device-side wait gave up (error flag set) */
+
+/* Arithmetic of the evolution. */
+#define DSP_FP64 0       /* everything in FP64                                      */
+#define DSP_FP32_MIXED 1 /* spinor in compensated FP32 (hi + lo), momentum P = p + A
+                            as exact FP32 hi/lo pairs, cos/sin of the phase argument
+                            dt|P| in FP32; initial state and projection in FP64     */
+
+/* Time-step scheme. */
+#define DSP_SCHEME_EXACT 0     /* the paper's closed-form exponential (Sec. III)    */
+#define DSP_SCHEME_STRANG_XY 1 /* e^{-i dt Px sx/2} e^{-i dt Py sy} e^{-i dt Px sx/2},
+                                  a sigma_x / sigma_y split (not in the paper)      */
+
+typedef struct dsp_grid dsp_grid;
+
+/* Bytes of device state one grid needs: 32 bytes per point for both
+ * precisions (FP64: two complex doubles; FP32_MIXED: hi and lo float4 planes).
+ * Returns -1 on invalid sizes or precision. */
+int64_t dsp_state_bytes(int32_t nx, int32_t ny, int32_t precision);
+
+/* Creates a grid.  nx, ny >= 1 and nx*ny <= 2^31 - 1; px_min < px_max and
+ * py_min < py_max, all finite; precision DSP_FP64 or DSP_FP32_MIXED; scheme
+ * DSP_SCHEME_*; valley +1 (K+) or -1 (K-, H = -sigma.P, Sec. II Eq.
+ * (dirac_eq_mom)).  cuda_stream is a cudaStream_t (NULL: legacy stream).
+ * state_dev: NULL lets the library allocate the spinor state; otherwise a
+ * caller-owned device buffer of at least dsp_state_bytes() bytes, 16-byte
+ * aligned, kept alive until dsp_destroy_grid.  On success *out is the handle.
+ * Defined by Sec. II (grid of independent momenta, Eq. (pair_prod_homo)). */
+dsp_status dsp_create_grid(int32_t nx, int32_t ny, double px_min, double px_max, double py_min,
+                           double py_max, int32_t precision, int32_t scheme, int32_t valley,
+                           void *cuda_stream, void *state_dev, int64_t state_dev_bytes,
+                           dsp_grid **out);
+
+/* Sets the pulse: a_mid is a host array [n_steps][2] of (A_x, A_y) sampled at
+ * the step midpoints t_i + (n + 1/2) dt (Sec. III, Eq. (approx_time)); a_in and
+ * a_out are the asymptotic potentials A^in, A^out of Sec. II (host, 2 doubles
+ * each).  All values finite, dt > 0 (dt >= 0 when n_steps == 0), n_steps >= 0.
+ * Copies and converts the table to the device, resets the state to
+ * v(p + A_in) and the step cursor to 0.  Returns DSP_E_CFL when
+ * dt * max_{n, p in box} |p + A_n| > pi (the step condition of Sec. III).
+ * Not ordered against work already queued that still reads the old table:
+ * the library orders it on the grid's stream. */
+dsp_status dsp_set_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, double dt,
+                         const double a_in[2], const double a_out[2]);
+
+/* Advances every point by `steps` time steps (Sec. III, Eq. (ev_op_dt)) from
+ * the cursor; steps >= 0 and cursor + steps <= n_steps, else DSP_E_STATE.
+ * The spinors stay on the device; evolving in pieces gives bitwise the same
+ * state as evolving at once.  Asynchronous. */
+dsp_status dsp_evolve(dsp_grid *g, int64_t steps);
+
+/* Projects psi(t_f) on u(p + A_out) (Sec. II, Eq. (pair_prod_homo)) and writes
+ * the |c+|^2 map, [ny][nx] row-major, to the caller's device buffer map_dev:
+ * double for DSP_FP64, float for DSP_FP32_MIXED.  Needs cursor == n_steps
+ * (DSP_E_STATE otherwise).  Also leaves per-tile FP64 partial sums for
+ * dsp_reduce_density.  Points with |p + A_out| == 0 get |c+|^2 = 0.
+ * Asynchronous. */
+dsp_status dsp_project(dsp_grid *g, void *map_dev);
+
+/* Reduces the last projection to the pair density n (eV^2) with a fixed-order
+ * FP64 tree (deterministic: bitwise the same on every run), times
+ * 4/(2 pi)^2 * hx * hy (Sec. II, Eq. (pair_prod_homo), degeneracy 4).  Needs a
+ * projection since the last dsp_set_pulse (DSP_E_STATE otherwise).  Writes
+ * *n_host; synchronises the grid's stream. */
+dsp_status dsp_reduce_density(dsp_grid *g, double *n_host);
+
+/* The whole hot path in one call: evolves the remaining steps with the
+ * projection fused into the same kernel, writes map_dev (may be NULL: then an
+ * internal map is used) and the density to *n_host (may be NULL).
+ * Synchronises when n_host is not NULL. */
+dsp_status dsp_solve(dsp_grid *g, void *map_dev, double *n_host);
+
+/* End to end with host buffers: copies the host pulse table in (as
+ * dsp_set_pulse), runs dsp_solve, and copies the |c+|^2 map (double or float
+ * by precision, nx*ny values) back to map_host (may be NULL) and the density
+ * to *n_host.  Synchronises. */
+dsp_status dsp_solve_host(dsp_grid *g, const double *a_mid, int64_t n_steps, double dt,
+                          const double a_in[2], const double a_out[2], void *map_host,
+                          double *n_host);
+
+/* One launch that advances several grids (each by steps[i], same rules as
+ * dsp_evolve).  All grids must share one CUDA stream; work goes on that
+ * stream.  Results are bitwise identical to advancing each grid alone. */
+dsp_status dsp_evolve_batch(dsp_grid *const *grids, const int64_t *steps, int32_t count);
+
+/* Cursor and pulse length of a grid. */
+dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps);
+
+/* Copies the raw spinor state (dsp_state_bytes bytes) to the host, or back
+ * from the host, with the step cursor, for checkpoint / resume.  Synchronise. */
+dsp_status dsp_save_state(dsp_grid *g, void *host_buf, int64_t bytes, int64_t *cursor);
+dsp_status dsp_load_state(dsp_grid *g, const void *host_buf, int64_t bytes, int64_t cursor);
+
+/* Frees the grid (and the state if the library allocated it).  NULL is OK. */
+dsp_status dsp_destroy_grid(dsp_grid *g);
+
+/* Static string for a status code. */
+const char *dsp_status_string(dsp_status s);
+
+/* ------------------------------------------------------------------------- */
+/* Pulse sampler (host).  Fills the midpoint table of a pulse model so callers
+ * need not write their own; any other A(t) can be passed to dsp_set_pulse.   */
+/* ------------------------------------------------------------------------- */
+
+#define DSP_PULSE_ZERO 0        /* A = 0                                            */
+#define DSP_PULSE_SIN2 1        /* (E0/w) sin^2(pi t/T) (sin wt, eps cos wt)         */
+#define DSP_PULSE_GAUSS 2       /* (E0/w) exp(-(t-t0)^2/tau^2) (sin wt, eps cos wt)  */
+#define DSP_PULSE_TWO_COLOUR 3  /* sin^2(pi t/T) sum_{k=1,2} (E0/(k w))
+                                   (sin(k w t + ph_k), eps cos(k w t + ph_k)),
+                                   ph_1 = 0, ph_2 = phase2                           */
+#define DSP_PULSE_CONST_FIELD 4 /* A_x = -E0 (t - T/2): constant field E_x = E0      */
+#define DSP_PULSE_PAPER 5       /* Sec. IV, Eq. (elec_field): E_x = E0 env(t)
+                                   cos(w t + phi), sin^2 rise over pi/(2 Omega_rise),
+                                   flat, cos^2 fall over pi/(2 Omega_fall) ending at
+                                   T; A_x = -int_0^t E_x                             */
+
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    double E0, omega, T, tau, t0, eps, phase2, Omega_rise, Omega_fall, phi;
+} dsp_pulse_spec;
+
+/* t_i = 0, t_f = T, dt = T/n_steps.  a_mid: host [n_steps][2] at
+ * (n + 1/2) dt; a_in = A(0); a_out = A(T); *dt_out = dt.  n_steps >= 1. */
+dsp_status dsp_sample_pulse(const dsp_pulse_spec *spec, int64_t n_steps, double *a_mid,
+                            double *a_in, double *a_out, double *dt_out);
+
+/* ------------------------------------------------------------------------- */
+/* Serving: a continuous-batching request loop (not in the paper).  Requests
+ * (each a whole solve) are queued on submit and admitted FIFO while the device
+ * footprint fits the budget and a slot is free; every dsp_server_step advances
+ * all admitted requests by up to chunk_steps in ONE batched launch, retires
+ * the ones that finished (projection fused, density reduced, map copied to
+ * the server's host buffer) and admits more.  A request's result is bitwise
+ * the same alone or in any mix.                                              */
+/* ------------------------------------------------------------------------- */
+
+typedef struct dsp_server dsp_server;
+
+typedef struct {
+    int32_t nx, ny;
+    double px_min, px_max, py_min, py_max;
+    int32_t precision, scheme, valley;
+    int32_t keep_map; /* 1: copy the |c+|^2 map back to host memory at the end */
+    int64_t n_steps;
+    double dt;
+    double a_in[2], a_out[2];
+} dsp_request;
+
+#define DSP_REQ_QUEUED 0
+#define DSP_REQ_ACTIVE 1
+#define DSP_REQ_DONE 2
+#define DSP_REQ_FAILED 3
+#define DSP_REQ_CANCELLED 4
+
+/* hbm_budget_bytes > 0: admission limit on the sum of device footprints
+ * (state + table + map + partial sums) of the active requests; max_active
+ * >= 1; chunk_steps >= 1: steps per batched launch.  cuda_stream as above. */
+dsp_status dsp_server_create(int64_t hbm_budget_bytes, int32_t max_active, int64_t chunk_steps,
+                             void *cuda_stream, dsp_server **out);
+
+/* Queues a request; a_mid is its host midpoint table [n_steps][2] (copied).
+ * Validation as dsp_create_grid + dsp_set_pulse (DSP_E_CFL included); a
+ * request whose footprint alone exceeds the budget is refused (DSP_E_NOMEM).
+ * *id receives its id (0, 1, 2, ... in submit order). */
+dsp_status dsp_server_submit(dsp_server *s, const dsp_request *req, const double *a_mid,
+                             int64_t *id);
+
+/* One scheduling iteration (see above).  Synchronises.  Outputs may be NULL:
+ * number active after the iteration, number still queued, number that
+ * finished in this iteration. */
+dsp_status dsp_server_step(dsp_server *s, int32_t *n_active, int32_t *n_queued,
+                           int32_t *n_finished);
+
+/* State of a request (DSP_REQ_*), its density once DONE, and (if keep_map)
+ * its map copied into map_host (nx*ny doubles or floats by precision; may be
+ * NULL).  Steps done so far in *steps_done (may be NULL). */
+dsp_status dsp_server_query(dsp_server *s, int64_t id, int32_t *state, double *density,
+                            void *map_host, int64_t *steps_done);
+
+/* Cancels a queued or active request; its device memory is freed at the next
+ * step.  Other requests are unaffected. */
+dsp_status dsp_server_cancel(dsp_server *s, int64_t id);
+
+/* Frees everything.  NULL is OK. */
+dsp_status dsp_server_destroy(dsp_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSP_H */

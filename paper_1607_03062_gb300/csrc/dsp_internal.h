@@ -1,0 +1,78 @@
+// dsp_internal.h -- shared between the kernels and the host API (not installed).
+//
+// Launch descriptors are passed BY VALUE as __grid_constant__ kernel parameters,
+// so queueing a launch needs no host-to-device copy and no allocation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dsp {
+
+// Points per CTA, and per FP64 partial sum of |c+|^2 (the reduction tile).
+constexpr int kTilePoints = 1024;
+// Spinors per thread (independent momenta advanced together for ILP).
+constexpr int kSpinorsPerThread = 2;
+constexpr int kThreads = kTilePoints / kSpinorsPerThread;
+// A(t) entries per shared-memory buffer (16 bytes each; two buffers per CTA).
+constexpr int kChunkSteps = 1024;
+// Requests one evolve launch can carry in its parameter block.
+constexpr int kMaxReqPerLaunch = 48;
+// Device-side error bits (the launch's error word).
+constexpr int kErrTimeout = 1;
+// Bound on one mbarrier wait, in nanoseconds of %globaltimer.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+// Polynomial degrees (in x = theta^2) instantiated for cos(theta)-1 and
+// sin(theta)/theta; the host picks the smallest one accurate for the
+// request's largest phase step theta_max.
+constexpr int kDegF32[3] = {3, 5, 9};
+constexpr int kDegF64[3] = {5, 8, 13};
+
+struct ReqDesc {
+    const void *table;  // float4 (FP32_MIXED: dt*Ax hi, lo, dt*Ay hi, lo) or double2 (FP64: dt*A)
+    void *state;        // planes: FP32_MIXED float4 hi[n], float4 lo[n]; FP64 double2 a[n], double2 b[n]
+    void *map;          // |c+|^2 output (float or double), or nullptr
+    double *partials;   // one double per tile (written when projecting)
+    double px_min, py_min, hx, hy;
+    double dt;
+    double a_in[2], a_out[2];
+    double quant, inv_quant;  // 2^k and 2^-k: hi parts are multiples of 2^-k (FP32_MIXED)
+    int64_t n_points;
+    int64_t step_begin, step_end;  // table entries [step_begin, step_end) this launch
+    int32_t nx, ny;
+    int32_t scheme, valley, degree_idx;
+    int32_t fresh;    // 1: start from v(p + A_in) instead of reading the state
+    int32_t project;  // 1: project at the end (map + partials)
+    int32_t tile_begin;  // first CTA of this request in the launch
+    int32_t n_tiles;
+    int32_t pad;
+};
+
+struct EvolveArgs {
+    int32_t nreq;
+    int32_t total_tiles;
+    int *err;  // device error word (bits kErr*)
+    ReqDesc r[kMaxReqPerLaunch];
+};
+
+struct FinDesc {
+    const double *partials;
+    int32_t n_tiles;
+    int32_t pad;
+    double scale;  // 4/(2 pi)^2 * hx * hy
+    double *out;   // device double
+};
+
+constexpr int kMaxFinPerLaunch = 64;
+struct FinalizeArgs {
+    int32_t count;
+    int32_t pad;
+    FinDesc f[kMaxFinPerLaunch];
+};
+
+// precision: 0 = FP64, 1 = FP32_MIXED.  Every request in args must have that precision.
+cudaError_t launch_evolve(const EvolveArgs &args, int precision, cudaStream_t stream);
+cudaError_t launch_finalize(const FinalizeArgs &args, cudaStream_t stream);
+
+}  // namespace dsp

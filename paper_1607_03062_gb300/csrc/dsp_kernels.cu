@@ -1,0 +1,652 @@
+// dsp_kernels.cu -- sm_103a kernels of the split-operator massless-Dirac solver.
+//
+// Method (arXiv 1607.03062):
+//   Sec. II Eq. (free_spin1..4)  initial state v(p + A_in), normalised;
+//   Sec. III Eq. (ev_op_dt)      product of N one-step operators, in time order;
+//   Sec. III Eq. (approx_time)   step n uses P_n = p + A(t_i + (n + 1/2) dt);
+//   Sec. III closed form         U_n = cos(theta) I - i sin(theta) valley sigma.P/|P|,
+//                                theta = dt |P_n|;
+//   Sec. II Eq. (pair_prod_homo) |c+|^2 = |u(p + A_out)^dag psi|^2, summed to n.
+//
+// GB300 design (one CTA = one tile of 1024 momenta; 512 threads x 2 spinors):
+//   * the spinors stay in registers across all steps of a launch: one 16-byte
+//     read and one write per spinor plane per launch;
+//   * A(t) is staged in shared memory in chunks of 1024 steps by 1-D bulk
+//     copies (cp.async.bulk) completing on an mbarrier, double buffered, so the
+//     step loop reads it with one broadcast LDS.128 per step;
+//   * cos(theta) - 1 and sin(theta)/theta are evaluated as their Taylor series
+//     in x = theta^2 = |dt P|^2 (no square root, no sin/cos call): the degree is
+//     chosen per request on the host from theta_max so truncation stays below
+//     the working precision;
+//   * FP32_MIXED: dt*p and dt*A are split into hi + lo with every hi a multiple
+//     of 2^-k, so P_hi = p_hi + A_hi is exact in FP32 and the momentum is known
+//     to ~1e-16 relative; the spinor is stored as hi + lo and each step adds the
+//     increment (U - I) psi with a Fast2Sum, so the FP32 rounding of psi does
+//     not random-walk over 1e5 steps;
+//   * the projection and the per-tile partial sums of |c+|^2 are fused into the
+//     last launch; partial sums use a fixed pairwise tree, so the density is
+//     bitwise reproducible and independent of the batch a request ran in.
+// No tensor cores: the work is 2x2 complex arithmetic per momentum.
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dsp_internal.h"
+
+namespace dsp {
+namespace {
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk copy (inline PTX)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase with the given parity; gives up after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if (global_ns() - t0 > kWaitLimitNs)
+            return false;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Taylor series in x = theta^2 (written from the power series of cos and sin)
+//   cos(theta) - 1    = sum_{k>=1} (-x)^k / (2k)!
+//   sin(theta)/theta  = sum_{k>=0} (-x)^k / (2k+1)!
+// ---------------------------------------------------------------------------
+
+template <int N>
+__host__ __device__ constexpr double inv_factorial()
+{
+    if constexpr (N <= 1)
+        return 1.0;
+    else
+        return inv_factorial<N - 1>() / static_cast<double>(N);
+}
+
+// Horner tail sum_{k=K..D} c_k x^(k-K) with c_k = (-1)^k / (2k + ODD)!; every
+// coefficient is a compile-time constant rounded once to T.
+template <typename T, int D, int K, int ODD>
+__device__ __forceinline__ T horner(T x)
+{
+    constexpr T c = static_cast<T>(((K & 1) ? -1.0 : 1.0) * inv_factorial<2 * K + ODD>());
+    if constexpr (K == D)
+        return c;
+    else
+        return fma(horner<T, D, K + 1, ODD>(x), x, c);
+}
+
+template <int D>
+__device__ __forceinline__ float cosm1_f32(float x)
+{
+    return horner<float, D, 1, 0>(x) * x;
+}
+template <int D>
+__device__ __forceinline__ float sinc_f32(float x)
+{
+    return horner<float, D, 0, 1>(x);
+}
+template <int D>
+__device__ __forceinline__ double cosm1_f64(double x)
+{
+    return horner<double, D, 1, 0>(x) * x;
+}
+template <int D>
+__device__ __forceinline__ double sinc_f64(double x)
+{
+    return horner<double, D, 0, 1>(x);
+}
+
+// ---------------------------------------------------------------------------
+// Per-point set-up shared by both precisions (all FP64, once per launch)
+// ---------------------------------------------------------------------------
+
+// Cell-centred node p = p_min + (i + 1/2) h, without contraction.
+__device__ __forceinline__ double grid_node(double lo, double h, int64_t i)
+{
+    return __dadd_rn(lo, __dmul_rn(static_cast<double>(i) + 0.5, h));
+}
+
+// Negative-energy spinor v(P) of valley * sigma.P, normalised (Sec. II Eq.
+// (free_spin1..4)); at P = 0 the limit P -> (0+, 0).
+__device__ __forceinline__ void initial_spinor(double Px, double Py, double sgn, double &ar,
+                                               double &ai, double &br, double &bi)
+{
+    const double r = 0.70710678118654752440;
+    const double E = sqrt(Px * Px + Py * Py);
+    if (E > 0.0) {
+        ar = sgn * (-Px / E) * r;
+        ai = sgn * (Py / E) * r;
+    } else {
+        ar = -sgn * r;
+        ai = 0.0;
+    }
+    br = r;
+    bi = 0.0;
+}
+
+// |u(P_out)^dag psi|^2 with u = [1, valley (Px + i Py)/E]/sqrt(2); 0 at P_out = 0.
+__device__ __forceinline__ double project_point(double Px, double Py, double sgn, double ar,
+                                                double ai, double br, double bi)
+{
+    const double E = sqrt(Px * Px + Py * Py);
+    if (!(E > 0.0))
+        return 0.0;
+    const double wr = sgn * Px / E, wi = -sgn * Py / E;  // valley * conj(Px + i Py)/E
+    const double cr = ar + (wr * br - wi * bi);
+    const double ci = ai + (wr * bi + wi * br);
+    return 0.5 * (cr * cr + ci * ci);
+}
+
+// Fixed pairwise tree over kTilePoints doubles in shared memory (deterministic).
+__device__ __forceinline__ double tile_tree_sum(double *red)
+{
+    for (int s = kTilePoints / 2; s > 0; s >>= 1) {
+        for (int t = threadIdx.x; t < s; t += blockDim.x)
+            red[t] += red[t + s];
+        __syncthreads();
+    }
+    return red[0];
+}
+
+// Locates the request a CTA belongs to (requests are sorted by tile_begin).
+__device__ __forceinline__ int find_request(const EvolveArgs &a)
+{
+    int lo = 0, hi = a.nreq - 1;
+    const int b = static_cast<int>(blockIdx.x);
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.r[mid].tile_begin <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Table staging: chunk c of the launch goes to buffer c & 1.
+// ---------------------------------------------------------------------------
+
+template <typename E>
+struct Stager {
+    E (*buf)[kChunkSteps];
+    uint64_t *bars;
+    const E *table;  // entry step_begin is element 0 of chunk 0
+    int64_t nsteps;
+    int nchunks;
+
+    __device__ __forceinline__ int chunk_len(int c) const
+    {
+        const int64_t rem = nsteps - static_cast<int64_t>(c) * kChunkSteps;
+        return rem < kChunkSteps ? static_cast<int>(rem) : kChunkSteps;
+    }
+    __device__ __forceinline__ void issue(int c) const  // one thread
+    {
+        const uint32_t bytes = static_cast<uint32_t>(chunk_len(c)) * sizeof(E);
+        mbar_arrive_expect_tx(&bars[c & 1], bytes);
+        bulk_load(&buf[c & 1][0], table + static_cast<int64_t>(c) * kChunkSteps, bytes,
+                  &bars[c & 1]);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// FP32_MIXED step
+// ---------------------------------------------------------------------------
+
+struct MixedPoint {
+    float ar, ai, br, bi;      // hi parts of psi = (a, b)
+    float lar, lai, lbr, lbi;  // lo parts
+    float pxh, pxl, pyh, pyl;  // dt * p as hi + lo
+};
+
+// Coefficients of U - I = [[cm1, -q], [conj(q), cm1]] for the step with kinematic
+// momentum dt*P = (Pxh + Pxl, Pyh + Pyl).
+template <int SCHEME, int D>
+__device__ __forceinline__ void step_coeffs_f32(float Pxh, float Pxl, float Pyh, float Pyl,
+                                                float sgn, float &cm1, float &qr, float &qi)
+{
+    if constexpr (SCHEME == 0) {
+        // theta^2 = |dt P|^2 with the first-order lo correction
+        float x = fmaf(Pxh, Pxh, Pyh * Pyh);
+        x = fmaf(2.0f, fmaf(Pxh, Pxl, Pyh * Pyl), x);
+        cm1 = cosm1_f32<D>(x);
+        const float sn = sinc_f32<D>(x) * sgn;
+        qr = sn * (Pyh + Pyl);
+        qi = sn * (Pxh + Pxl);
+    } else {
+        // e^{-i a sx} e^{-i b sy} e^{-i a sx}, a = dt Px / 2, b = dt Py:
+        //   = [[cos b cos 2a, -(sin b + i cos b sin 2a)], [sin b - i cos b sin 2a, cos b cos 2a]]
+        const float xx = fmaf(Pxh, Pxh, 2.0f * Pxh * Pxl);
+        const float xy = fmaf(Pyh, Pyh, 2.0f * Pyh * Pyl);
+        const float cmx = cosm1_f32<D>(xx), cmy = cosm1_f32<D>(xy);
+        const float sx = (Pxh + Pxl) * sinc_f32<D>(xx) * sgn;
+        const float sy = (Pyh + Pyl) * sinc_f32<D>(xy) * sgn;
+        cm1 = cmx + cmy + cmx * cmy;
+        qr = sy;
+        qi = (1.0f + cmy) * sx;
+    }
+}
+
+// psi <- U psi as psi_hi + (U - I) psi_hi + psi_lo, the rounding error of the
+// hi update carried into lo (Fast2Sum).
+__device__ __forceinline__ void apply_f32(MixedPoint &s, float cm1, float qr, float qi)
+{
+    const float dar = fmaf(cm1, s.ar, fmaf(-qr, s.br, fmaf(qi, s.bi, s.lar)));
+    const float dai = fmaf(cm1, s.ai, fmaf(-qr, s.bi, fmaf(-qi, s.br, s.lai)));
+    const float dbr = fmaf(cm1, s.br, fmaf(qr, s.ar, fmaf(qi, s.ai, s.lbr)));
+    const float dbi = fmaf(cm1, s.bi, fmaf(qr, s.ai, fmaf(-qi, s.ar, s.lbi)));
+    float t;
+    t = s.ar + dar; s.lar = dar - (t - s.ar); s.ar = t;
+    t = s.ai + dai; s.lai = dai - (t - s.ai); s.ai = t;
+    t = s.br + dbr; s.lbr = dbr - (t - s.br); s.br = t;
+    t = s.bi + dbi; s.lbi = dbi - (t - s.bi); s.bi = t;
+}
+
+template <int SCHEME, int D>
+__device__ void body_mixed(const ReqDesc &R, int tile, float4 (*buf)[kChunkSteps], uint64_t *bars,
+                           int *err)
+{
+    constexpr int S = kSpinorsPerThread;
+    const int tid = threadIdx.x;
+    const int64_t base = static_cast<int64_t>(tile) * kTilePoints;
+    const float sgn = R.valley > 0 ? 1.0f : -1.0f;
+    float4 *hi_plane = static_cast<float4 *>(R.state);
+    float4 *lo_plane = hi_plane + R.n_points;
+
+    MixedPoint pt[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t idx = base + s * kThreads + tid;
+        const bool valid = idx < R.n_points;
+        double px = 0.0, py = 0.0;
+        if (valid) {
+            px = grid_node(R.px_min, R.hx, idx % R.nx);
+            py = grid_node(R.py_min, R.hy, idx / R.nx);
+        }
+        const double tx = R.dt * px, ty = R.dt * py;
+        const double hx = rint(tx * R.quant) * R.inv_quant, hy = rint(ty * R.quant) * R.inv_quant;
+        pt[s].pxh = static_cast<float>(hx);
+        pt[s].pxl = static_cast<float>(tx - hx);
+        pt[s].pyh = static_cast<float>(hy);
+        pt[s].pyl = static_cast<float>(ty - hy);
+        if (R.fresh || !valid) {
+            double ar, ai, br, bi;
+            initial_spinor(px + R.a_in[0], py + R.a_in[1], static_cast<double>(sgn), ar, ai, br, bi);
+            pt[s].ar = static_cast<float>(ar);
+            pt[s].lar = static_cast<float>(ar - static_cast<double>(pt[s].ar));
+            pt[s].ai = static_cast<float>(ai);
+            pt[s].lai = static_cast<float>(ai - static_cast<double>(pt[s].ai));
+            pt[s].br = static_cast<float>(br);
+            pt[s].lbr = static_cast<float>(br - static_cast<double>(pt[s].br));
+            pt[s].bi = static_cast<float>(bi);
+            pt[s].lbi = static_cast<float>(bi - static_cast<double>(pt[s].bi));
+        } else {
+            const float4 h = hi_plane[idx], l = lo_plane[idx];
+            pt[s].ar = h.x; pt[s].ai = h.y; pt[s].br = h.z; pt[s].bi = h.w;
+            pt[s].lar = l.x; pt[s].lai = l.y; pt[s].lbr = l.z; pt[s].lbi = l.w;
+        }
+    }
+
+    Stager<float4> st{buf, bars, static_cast<const float4 *>(R.table) + R.step_begin,
+                      R.step_end - R.step_begin, 0};
+    st.nchunks = static_cast<int>((st.nsteps + kChunkSteps - 1) / kChunkSteps);
+    if (tid == 0) {
+        if (st.nchunks > 0) st.issue(0);
+        if (st.nchunks > 1) st.issue(1);
+    }
+    bool failed = false;
+    for (int c = 0; c < st.nchunks; ++c) {
+        const bool ok = mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1);
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+        const float4 *tb = buf[c & 1];
+        const int len = st.chunk_len(c);
+#pragma unroll 2
+        for (int j = 0; j < len; ++j) {
+            const float4 a = tb[j];  // (dt Ax hi, lo, dt Ay hi, lo): shared-memory broadcast
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                float cm1, qr, qi;
+                step_coeffs_f32<SCHEME, D>(pt[s].pxh + a.x, pt[s].pxl + a.y, pt[s].pyh + a.z,
+                                           pt[s].pyl + a.w, sgn, cm1, qr, qi);
+                apply_f32(pt[s], cm1, qr, qi);
+            }
+        }
+        __syncthreads();  // everyone is done with buffer c & 1
+        if (tid == 0 && c + 2 < st.nchunks)
+            st.issue(c + 2);
+    }
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(err, kErrTimeout);
+            // give copies still in flight a bounded chance to land before exit
+            for (int c = 0; c < st.nchunks && c < 2; ++c)
+                (void)mbar_wait_bounded(&bars[c & 1], 0);
+        }
+        return;
+    }
+
+    double cp2[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t idx = base + s * kThreads + tid;
+        cp2[s] = 0.0;
+        if (idx < R.n_points) {
+            hi_plane[idx] = make_float4(pt[s].ar, pt[s].ai, pt[s].br, pt[s].bi);
+            lo_plane[idx] = make_float4(pt[s].lar, pt[s].lai, pt[s].lbr, pt[s].lbi);
+            if (R.project) {
+                const double px = grid_node(R.px_min, R.hx, idx % R.nx);
+                const double py = grid_node(R.py_min, R.hy, idx / R.nx);
+                const double ar = static_cast<double>(pt[s].ar) + pt[s].lar;
+                const double ai = static_cast<double>(pt[s].ai) + pt[s].lai;
+                const double br = static_cast<double>(pt[s].br) + pt[s].lbr;
+                const double bi = static_cast<double>(pt[s].bi) + pt[s].lbi;
+                cp2[s] = project_point(px + R.a_out[0], py + R.a_out[1], static_cast<double>(sgn),
+                                       ar, ai, br, bi);
+                if (R.map)
+                    static_cast<float *>(R.map)[idx] = static_cast<float>(cp2[s]);
+            }
+        }
+    }
+    if (R.project) {
+        double *red = reinterpret_cast<double *>(&buf[0][0]);  // table buffers are free now
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            red[s * kThreads + tid] = cp2[s];
+        __syncthreads();
+        const double sum = tile_tree_sum(red);
+        if (tid == 0)
+            R.partials[tile] = sum;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 step
+// ---------------------------------------------------------------------------
+
+struct F64Point {
+    double ar, ai, br, bi;
+    double tx, ty;  // dt * p
+};
+
+template <int SCHEME, int D>
+__device__ __forceinline__ void step_f64(F64Point &s, double2 a, double sgn)
+{
+    const double Px = s.tx + a.x, Py = s.ty + a.y;  // dt * P
+    double c, qr, qi;
+    if constexpr (SCHEME == 0) {
+        const double x = fma(Px, Px, Py * Py);
+        c = 1.0 + cosm1_f64<D>(x);
+        const double sn = sinc_f64<D>(x) * sgn;
+        qr = sn * Py;
+        qi = sn * Px;
+    } else {
+        const double xx = Px * Px, xy = Py * Py;
+        const double cy = 1.0 + cosm1_f64<D>(xy);
+        c = cy * (1.0 + cosm1_f64<D>(xx));
+        qr = Py * sinc_f64<D>(xy) * sgn;
+        qi = cy * Px * sinc_f64<D>(xx) * sgn;
+    }
+    // a' = c a - q b ; b' = conj(q) a + c b, q = qr + i qi
+    const double nar = fma(c, s.ar, fma(-qr, s.br, qi * s.bi));
+    const double nai = fma(c, s.ai, fma(-qr, s.bi, -(qi * s.br)));
+    const double nbr = fma(c, s.br, fma(qr, s.ar, qi * s.ai));
+    const double nbi = fma(c, s.bi, fma(qr, s.ai, -(qi * s.ar)));
+    s.ar = nar; s.ai = nai; s.br = nbr; s.bi = nbi;
+}
+
+template <int SCHEME, int D>
+__device__ void body_f64(const ReqDesc &R, int tile, double2 (*buf)[kChunkSteps], uint64_t *bars,
+                         int *err)
+{
+    constexpr int S = kSpinorsPerThread;
+    const int tid = threadIdx.x;
+    const int64_t base = static_cast<int64_t>(tile) * kTilePoints;
+    const double sgn = R.valley > 0 ? 1.0 : -1.0;
+    double2 *a_plane = static_cast<double2 *>(R.state);
+    double2 *b_plane = a_plane + R.n_points;
+
+    F64Point pt[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t idx = base + s * kThreads + tid;
+        const bool valid = idx < R.n_points;
+        double px = 0.0, py = 0.0;
+        if (valid) {
+            px = grid_node(R.px_min, R.hx, idx % R.nx);
+            py = grid_node(R.py_min, R.hy, idx / R.nx);
+        }
+        pt[s].tx = R.dt * px;
+        pt[s].ty = R.dt * py;
+        if (R.fresh || !valid) {
+            initial_spinor(px + R.a_in[0], py + R.a_in[1], sgn, pt[s].ar, pt[s].ai, pt[s].br,
+                           pt[s].bi);
+        } else {
+            const double2 a = a_plane[idx], b = b_plane[idx];
+            pt[s].ar = a.x; pt[s].ai = a.y; pt[s].br = b.x; pt[s].bi = b.y;
+        }
+    }
+
+    Stager<double2> st{buf, bars, static_cast<const double2 *>(R.table) + R.step_begin,
+                       R.step_end - R.step_begin, 0};
+    st.nchunks = static_cast<int>((st.nsteps + kChunkSteps - 1) / kChunkSteps);
+    if (tid == 0) {
+        if (st.nchunks > 0) st.issue(0);
+        if (st.nchunks > 1) st.issue(1);
+    }
+    bool failed = false;
+    for (int c = 0; c < st.nchunks; ++c) {
+        const bool ok = mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1);
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+        const double2 *tb = buf[c & 1];
+        const int len = st.chunk_len(c);
+#pragma unroll 2
+        for (int j = 0; j < len; ++j) {
+            const double2 a = tb[j];
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+                step_f64<SCHEME, D>(pt[s], a, sgn);
+        }
+        __syncthreads();
+        if (tid == 0 && c + 2 < st.nchunks)
+            st.issue(c + 2);
+    }
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(err, kErrTimeout);
+            for (int c = 0; c < st.nchunks && c < 2; ++c)
+                (void)mbar_wait_bounded(&bars[c & 1], 0);
+        }
+        return;
+    }
+
+    double cp2[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t idx = base + s * kThreads + tid;
+        cp2[s] = 0.0;
+        if (idx < R.n_points) {
+            a_plane[idx] = make_double2(pt[s].ar, pt[s].ai);
+            b_plane[idx] = make_double2(pt[s].br, pt[s].bi);
+            if (R.project) {
+                const double px = grid_node(R.px_min, R.hx, idx % R.nx);
+                const double py = grid_node(R.py_min, R.hy, idx / R.nx);
+                cp2[s] = project_point(px + R.a_out[0], py + R.a_out[1], sgn, pt[s].ar, pt[s].ai,
+                                       pt[s].br, pt[s].bi);
+                if (R.map)
+                    static_cast<double *>(R.map)[idx] = cp2[s];
+            }
+        }
+    }
+    if (R.project) {
+        double *red = reinterpret_cast<double *>(&buf[0][0]);
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            red[s * kThreads + tid] = cp2[s];
+        __syncthreads();
+        const double sum = tile_tree_sum(red);
+        if (tid == 0)
+            R.partials[tile] = sum;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads, 2)
+    evolve_mixed_kernel(const __grid_constant__ EvolveArgs args)
+{
+    __shared__ __align__(128) float4 buf[2][kChunkSteps];
+    __shared__ __align__(8) uint64_t bars[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int r = find_request(args);
+    const ReqDesc &R = args.r[r];
+    const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
+    switch (R.scheme * 4 + R.degree_idx) {
+    case 0: body_mixed<0, kDegF32[0]>(R, tile, buf, bars, args.err); break;
+    case 1: body_mixed<0, kDegF32[1]>(R, tile, buf, bars, args.err); break;
+    case 2: body_mixed<0, kDegF32[2]>(R, tile, buf, bars, args.err); break;
+    case 4: body_mixed<1, kDegF32[0]>(R, tile, buf, bars, args.err); break;
+    case 5: body_mixed<1, kDegF32[1]>(R, tile, buf, bars, args.err); break;
+    case 6: body_mixed<1, kDegF32[2]>(R, tile, buf, bars, args.err); break;
+    default: break;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    evolve_f64_kernel(const __grid_constant__ EvolveArgs args)
+{
+    __shared__ __align__(128) double2 buf[2][kChunkSteps];
+    __shared__ __align__(8) uint64_t bars[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int r = find_request(args);
+    const ReqDesc &R = args.r[r];
+    const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
+    switch (R.scheme * 4 + R.degree_idx) {
+    case 0: body_f64<0, kDegF64[0]>(R, tile, buf, bars, args.err); break;
+    case 1: body_f64<0, kDegF64[1]>(R, tile, buf, bars, args.err); break;
+    case 2: body_f64<0, kDegF64[2]>(R, tile, buf, bars, args.err); break;
+    case 4: body_f64<1, kDegF64[0]>(R, tile, buf, bars, args.err); break;
+    case 5: body_f64<1, kDegF64[1]>(R, tile, buf, bars, args.err); break;
+    case 6: body_f64<1, kDegF64[2]>(R, tile, buf, bars, args.err); break;
+    default: break;
+    }
+}
+
+// One CTA per density: fixed-order per-thread sums, then a pairwise tree.
+__global__ void __launch_bounds__(1024) finalize_kernel(const __grid_constant__ FinalizeArgs args)
+{
+    __shared__ double red[1024];
+    const FinDesc &f = args.f[blockIdx.x];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < f.n_tiles; i += blockDim.x)
+        acc += f.partials[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        *f.out = red[0] * f.scale;
+}
+
+}  // namespace
+
+cudaError_t launch_evolve(const EvolveArgs &args, int precision, cudaStream_t stream)
+{
+    if (args.nreq <= 0 || args.total_tiles <= 0)
+        return cudaSuccess;
+    if (precision == 1)
+        evolve_mixed_kernel<<<args.total_tiles, kThreads, 0, stream>>>(args);
+    else
+        evolve_f64_kernel<<<args.total_tiles, kThreads, 0, stream>>>(args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const FinalizeArgs &args, cudaStream_t stream)
+{
+    if (args.count <= 0)
+        return cudaSuccess;
+    finalize_kernel<<<args.count, 1024, 0, stream>>>(args);
+    return cudaGetLastError();
+}
+
+}  // namespace dsp

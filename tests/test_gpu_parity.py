@@ -1,0 +1,251 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (per point |c+|^2 absolute, density relative):
+  FP64        1e-9 and 1e-10 -- both sides are FP64; the difference is rounding
+              order and the series-vs-libm evaluation of cos/sin, O(1e-16) per
+              step, accumulated over <= 1e5 unitary steps.
+  FP32_MIXED  1e-5 and 1e-4 -- the accuracy target for the mixed path.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1607_03062_gb300 import binding as B
+from paper_1607_03062_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": (1e-9, 1e-10), "fp32_mixed": (1e-5, 1e-4)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1607_03062_gb300 import build
+    build.build()
+    B.lib()
+    torch.cuda.set_device(0)
+
+
+def run_gpu(grid, table, precision="fp32_mixed", scheme="exact", valley=1, pieces=None):
+    a_mid, a_in, a_out, dt = table
+    g = B.Grid(grid["nx"], grid["ny"], grid["px"], grid["py"], precision, scheme, valley)
+    g.set_pulse(a_mid, dt, a_in, a_out)
+    if pieces is None:
+        m, n = g.solve()
+    else:
+        for p in pieces:
+            g.evolve(p)
+        m = g.project()
+        n = g.density()
+    torch.cuda.synchronize()
+    out = m.double().cpu().numpy().copy()
+    g.close()
+    return out, n
+
+
+def run_oracle(orc, grid, table, scheme="exact", valley=1):
+    a_mid, a_in, a_out, dt = table
+    cp, _, _, n = orc.solve_grid(grid["nx"], grid["ny"], grid["px"], grid["py"], a_mid, dt, a_in,
+                                 a_out, scheme=scheme, valley=valley)
+    return cp, n
+
+
+def assert_close(prec, m, n, ref, nref):
+    tp, tn = TOL[prec]
+    err = np.abs(m - ref).max()
+    assert err <= tp, f"{prec}: max |c+|^2 error {err:.3e} > {tp}"
+    if nref > 0:
+        rel = abs(n - nref) / nref
+        assert rel <= tn, f"{prec}: density relative error {rel:.3e} > {tn}"
+    else:
+        assert abs(n) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_sin2_64_full_map(orc, prec):
+    """64x64 grid on [-4,4]^2, 5-cycle sin^2 pulse, 2000 steps: every point."""
+    cfg = W.config_sin2_64()
+    tab = orc.pulse_table(cfg["pulse"], cfg["steps"])
+    ref, nref = run_oracle(orc, cfg["grid"], tab)
+    m, n = run_gpu(cfg["grid"], B.sample_pulse(cfg["pulse"], cfg["steps"]), prec)
+    assert_close(prec, m, n, ref, nref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+@pytest.mark.parametrize("scheme,valley", [("exact", 1), ("exact", -1), ("strang_xy", 1),
+                                           ("strang_xy", -1)])
+def test_ragged_tiles_and_chunks(orc, prec, scheme, valley):
+    """67x45 points (3 tiles, ragged tail), asymmetric box, elliptical pulse,
+    1500 steps evolved in pieces that straddle the 1024-step table chunks."""
+    grid = {"nx": 67, "ny": 45, "px": (-3.0, 5.0), "py": (-2.5, 3.5)}
+    pulse = W.sin2_pulse(2.0, 1.2, 4.0, eps=0.6)
+    n_steps = 1500
+    ref, nref = run_oracle(orc, grid, orc.pulse_table(pulse, n_steps), scheme, valley)
+    m, n = run_gpu(grid, B.sample_pulse(pulse, n_steps), prec, scheme, valley,
+                   pieces=[700, 1, 799])
+    assert_close(prec, m, n, ref, nref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_pieces_equal_one_launch_bitwise(prec):
+    grid = {"nx": 100, "ny": 37, "px": (-4, 4), "py": (-4, 4)}
+    tab = B.sample_pulse(W.gauss_pulse(2.0, 1.55, 1.0), 3100)
+    m1, n1 = run_gpu(grid, tab, prec)
+    m2, n2 = run_gpu(grid, tab, prec, pieces=[1024, 1000, 1, 1075])
+    assert np.array_equal(m1, m2) and n1 == n2
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_runs_are_deterministic(prec):
+    grid = {"nx": 300, "ny": 200, "px": (-4, 4), "py": (-4, 4)}
+    tab = B.sample_pulse(W.sin2_pulse(1.0, 1.55, 5.0), 800)
+    m1, n1 = run_gpu(grid, tab, prec)
+    m2, n2 = run_gpu(grid, tab, prec)
+    assert np.array_equal(m1, m2) and n1 == n2
+
+
+def test_batch_equals_alone_bitwise():
+    """One launch over several grids (both precisions, different sizes, pulses and
+    step counts) gives bitwise the results of each grid alone."""
+    specs = [({"nx": 64, "ny": 64, "px": (-4, 4), "py": (-4, 4)}, W.sin2_pulse(1.0, 1.55, 5.0),
+              1200, "fp32_mixed"),
+             ({"nx": 130, "ny": 33, "px": (-6, 6), "py": (-3, 3)}, W.gauss_pulse(3.0, 1.1, 1.0),
+              900, "fp32_mixed"),
+             ({"nx": 50, "ny": 70, "px": (-2, 5), "py": (-4, 4)}, W.sin2_pulse(2.0, 0.9, 3.0, 0.3),
+              1500, "fp64")]
+    alone = []
+    for grid, pulse, n, prec in specs:
+        alone.append(run_gpu(grid, B.sample_pulse(pulse, n), prec))
+    gs = []
+    for grid, pulse, n, prec in specs:
+        g = B.Grid(grid["nx"], grid["ny"], grid["px"], grid["py"], prec)
+        a_mid, a_in, a_out, dt = B.sample_pulse(pulse, n)
+        g.set_pulse(a_mid, dt, a_in, a_out)
+        gs.append(g)
+    steps = [s[2] for s in specs]
+    B.evolve_batch([g.h for g in gs], [500, 500, 500])
+    B.evolve_batch([g.h for g in gs], [s - 500 for s in steps])
+    for g, (m_ref, n_ref) in zip(gs, alone):
+        m = g.project()
+        n = g.density()
+        torch.cuda.synchronize()
+        assert np.array_equal(m.double().cpu().numpy(), m_ref) and n == n_ref
+        g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_zero_steps_and_single_point(orc, prec):
+    """No steps: |c+|^2 = 0 when A_in = A_out.  A 1x1 grid is the point p = 0
+    (the P -> (0+, 0) limit of the spinors), here under a zero field."""
+    grid = {"nx": 5, "ny": 3, "px": (-1, 1), "py": (-1, 1)}
+    m, n = run_gpu(grid, (np.zeros((0, 2)), np.zeros(2), np.zeros(2), 0.0), prec)
+    assert np.abs(m).max() <= 1e-15 and abs(n) <= 1e-15
+    one = {"nx": 1, "ny": 1, "px": (-1, 1), "py": (-1, 1)}
+    tab = B.sample_pulse(W.sin2_pulse(0.5, 1.55, 2.0), 300)
+    ref, nref = run_oracle(orc, one, orc.pulse_table(W.sin2_pulse(0.5, 1.55, 2.0), 300))
+    m, n = run_gpu(one, tab, prec)
+    assert abs(m[0, 0] - ref[0, 0]) <= TOL[prec][0]
+
+
+def test_constant_field_landau_zener_on_gpu(orc):
+    """The LZ workload through the GPU, FP32-mixed, against the oracle (whose LZ
+    closed-form agreement is pinned on the CPU)."""
+    E0, T = 1.0, 60.0
+    pulse = W.const_field_pulse(E0, T)
+    grid = {"nx": 128, "ny": 40, "px": (-40.0, 40.0), "py": (-2.0, 2.0)}
+    n = 6000
+    ref, nref = run_oracle(orc, grid, orc.pulse_table(pulse, n))
+    m, dens = run_gpu(grid, B.sample_pulse(pulse, n), "fp32_mixed")
+    assert_close("fp32_mixed", m, dens, ref, nref)
+
+
+def test_argument_and_order_errors():
+    g = B.Grid(8, 8, (-1, 1), (-1, 1), "fp32_mixed")
+    with pytest.raises(B.DSPError) as e:  # no pulse yet
+        g.evolve(1)
+    assert e.value.code == -4
+    big = np.full((10, 2), 0.0)
+    with pytest.raises(B.DSPError) as e:  # dt * max|p + A| > pi
+        g.set_pulse(big, 3.0, [0, 0], [0, 0])
+    assert e.value.code == -5
+    bad = np.zeros((10, 2))
+    bad[3, 1] = np.nan
+    with pytest.raises(B.DSPError) as e:
+        g.set_pulse(bad, 0.01, [0, 0], [0, 0])
+    assert e.value.code == -1
+    g.set_pulse(np.zeros((10, 2)), 0.01, [0, 0], [0, 0])
+    with pytest.raises(B.DSPError) as e:  # past the end
+        g.evolve(11)
+    assert e.value.code == -4
+    g.evolve(4)
+    with pytest.raises(B.DSPError) as e:  # project before the end
+        g.project()
+    assert e.value.code == -4
+    with pytest.raises(B.DSPError) as e:  # no projection yet
+        g.density()
+    assert e.value.code == -4
+    g.evolve(6)
+    g.project()
+    assert abs(g.density()) < 1e-15
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_host_buffer_entry_point_matches_device_path(prec):
+    grid = {"nx": 96, "ny": 80, "px": (-4, 4), "py": (-4, 4)}
+    a_mid, a_in, a_out, dt = B.sample_pulse(W.sin2_pulse(1.0, 1.55, 5.0), 1000)
+    m_dev, n_dev = run_gpu(grid, (a_mid, a_in, a_out, dt), prec)
+    h = B.create_grid(96, 80, (-4, 4), (-4, 4), prec)
+    out = np.zeros((80, 96), dtype=np.float64 if prec == "fp64" else np.float32)
+    n = B.solve_host(h, a_mid, dt, a_in, a_out, out)
+    B.destroy_grid(h)
+    assert np.array_equal(out.astype(np.float64), m_dev) and n == n_dev
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_checkpoint_resume_bitwise(prec):
+    grid = {"nx": 70, "ny": 30, "px": (-4, 4), "py": (-4, 4)}
+    tab = B.sample_pulse(W.sin2_pulse(1.5, 1.55, 4.0), 1400)
+    m_ref, n_ref = run_gpu(grid, tab, prec)
+    a_mid, a_in, a_out, dt = tab
+    h1 = B.create_grid(70, 30, (-4, 4), (-4, 4), prec)
+    B.set_pulse(h1, a_mid, dt, a_in, a_out)
+    B.evolve(h1, 613)
+    buf = np.zeros(B.state_bytes(70, 30, prec), dtype=np.uint8)
+    cur = B.save_state(h1, buf)
+    B.destroy_grid(h1)
+    h2 = B.create_grid(70, 30, (-4, 4), (-4, 4), prec)
+    B.set_pulse(h2, a_mid, dt, a_in, a_out)
+    B.load_state(h2, buf, cur)
+    B.evolve(h2, 1400 - cur)
+    out = np.zeros((30, 70), dtype=np.float64 if prec == "fp64" else np.float32)
+    mp = torch.from_numpy(out).cuda()
+    B.project(h2, mp.data_ptr())
+    n = B.reduce_density(h2)
+    B.destroy_grid(h2)
+    assert np.array_equal(mp.cpu().numpy().astype(np.float64), m_ref) and n == n_ref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_lzs_2048_full_size_sampled(orc, prec):
+    """The 2048x2048, 1e5-step LZS workload (first seeded sample) in the launch
+    configuration the benchmark times; 384 seeded points checked one by one."""
+    cfg = W.config_lzs_2048(0)
+    g = cfg["grid"]
+    tab_o = orc.pulse_table(cfg["pulse"], cfg["steps"])
+    m, n = run_gpu(g, B.sample_pulse(cfg["pulse"], cfg["steps"]), prec)
+    idx = W.sample_points(g["nx"], g["ny"], 384, seed=11)
+    # points where pairs are likely: around p_y = 0 along the field
+    xs = orc.grid_nodes(*g["px"], g["nx"])
+    ys = orc.grid_nodes(*g["py"], g["ny"])
+    band = np.arange(g["nx"] // 2 - 8, g["nx"] // 2 + 8) * g["nx"] + np.arange(0, g["nx"], 128)[:, None]
+    idx = np.unique(np.concatenate([idx, band.ravel()]))
+    r = orc.solve_points(xs[idx % g["nx"]], ys[idx // g["nx"]], *tab_o[:1], tab_o[3], tab_o[1],
+                         tab_o[2])
+    err = np.abs(m.ravel()[idx] - r["cplus2"]).max()
+    assert r["cplus2"].max() > 0.05
+    assert err <= TOL[prec][0], f"{prec}: max sampled error {err:.3e}"
+    assert np.all(np.isfinite(m)) and m.min() >= 0.0 and m.max() <= 1.0 + 1e-6
+    assert n > 0

@@ -332,3 +332,13 @@ def test_paper_fig1_parameters_in_ev_units():
     assert p["Omega_rise"] == pytest.approx(vals["hbar_Omega_eV"], rel=1e-3)
     assert p["T"] == pytest.approx(vals["duration_hbar_per_eV"], rel=1e-3)
     assert W.VF_MPS == vals["v_F_m_per_s"]
+
+
+def test_zero_momentum_point_is_defined(orc):
+    """At P = 0 the free spinors are undefined; the oracle takes the limit
+    P -> (0+, 0): still orthonormal, and a zero-field run from p = 0 stays put."""
+    u, v = orc.spinors(0.0, 0.0, 1)
+    assert abs(np.vdot(u, v)) < 1e-15 and abs(np.vdot(v, v) - 1) < 1e-15
+    a_mid, a_in, a_out, dt = orc.pulse_table(W.zero_pulse(5.0), 100)
+    r = orc.solve_points(np.array([0.0]), np.array([0.0]), a_mid, dt, a_in, a_out)
+    assert r["cplus2"][0] == 0.0 and abs(r["norm2"][0] - 1) < 1e-15
