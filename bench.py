@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-loop leg")
+    ap.add_argument("--serving-requests", type=int, default=256)
+    ap.add_argument("--serving-load", type=float, default=0.8,
+                    help="offered load as a fraction of the measured solve throughput")
+    ap.add_argument("--serving-chunk", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -300,6 +305,11 @@ def run_gpu(args):
            "d2h_bytes_per_step": 4 * n * n + 16,
            "note": "dsp_solve_host: host midpoint table in, host |c+|^2 map and density out"}
 
+    # ---- serving: continuous batching vs one request at a time ----
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = serving_leg(args, value / world, st_ptr)
+
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -348,7 +358,7 @@ def run_gpu(args):
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world} (independent samples per rank)"},
         "density_first_step": d_mixed[0] if d_mixed else None,
-        "fp64": fp64, "e2e": e2e, "gpu_launches": 2 * args.steps,
+        "fp64": fp64, "e2e": e2e, "serving": serving, "gpu_launches": 2 * args.steps,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
     }
@@ -356,6 +366,40 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------
+# Serving leg
+# ------------------------------------------------------------------------------------------
+
+def serving_leg(args, solve_rate, stream):
+    """256 seeded Poisson requests through the library's continuous-batching server
+    vs the same requests one at a time (FIFO, each alone); at an offered load of
+    args.serving_load x the measured solve throughput (latency), and with every
+    request submitted at t = 0 (throughput at saturation)."""
+    from paper_1607_03062_gb300 import serve
+
+    probe = W.serving_requests(count=args.serving_requests, seed=1607, rate_hz=1.0)
+    mean_work = float(np.mean([r["grid"]["nx"] * r["grid"]["ny"] * r["steps"] for r in probe]))
+    rate = args.serving_load * solve_rate / mean_work
+    reqs = serve.prepare(W.serving_requests(count=args.serving_requests, seed=1607, rate_hz=rate))
+    budget = 64 << 30
+    out = {"requests": len(reqs), "rate_hz": rate, "offered_load": args.serving_load,
+           "chunk_steps": args.serving_chunk, "hbm_budget_bytes": budget,
+           "workload": "N in {128,256,512,1024}, eps~U[0,1], omega~U[0.8,2.5], E0~U[0.5,4], "
+                       "steps~U{1e3..1e5}, 5-cycle sin^2, [-8,8]^2, FP32-mixed, seed 1607"}
+    legs = {"batched": dict(max_active=48, chunk_steps=args.serving_chunk),
+            "one_at_a_time": dict(max_active=1, chunk_steps=1 << 40)}
+    for name, kw in legs.items():
+        for mode, realtime in (("poisson", True), ("saturated", False)):
+            r = serve.run(reqs, hbm_budget_bytes=budget, stream=stream, realtime=realtime, **kw)
+            out[f"{name}_{mode}"] = {"p50_s": r["p50_s"], "p99_s": r["p99_s"],
+                                     "throughput": r["throughput"], "wall_s": r["wall_s"],
+                                     "iterations": r["iterations"],
+                                     "max_active": r["max_active_seen"]}
+    out["throughput_ratio_saturated"] = (out["batched_saturated"]["throughput"] /
+                                         out["one_at_a_time_saturated"]["throughput"])
+    return out
 
 
 # ------------------------------------------------------------------------------------------
