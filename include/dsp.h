@@ -114,6 +114,32 @@ dsp_status dsp_project(dsp_grid *g, void *map_dev);
  * *n_host; synchronises the grid's stream. */
 dsp_status dsp_reduce_density(dsp_grid *g, double *n_host);
 
+/* Pair density of a |c+|^2 map that ALLOCATES NOTHING.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc -- a host
+ * application or framework that already owns the device memory through its
+ * own allocator, or a latency-critical loop where cudaMalloc/cudaFree (which
+ * can synchronise the device) are not allowed.
+ *   map_dev: the caller's device map, nx*ny values row-major [ny][nx], double
+ *     for DSP_FP64 or float for DSP_FP32_MIXED (as written by dsp_project);
+ *   the box and nx, ny give hx = (px_max - px_min)/nx, hy likewise, and
+ *   *n_host receives 4/(2 pi)^2 * hx * hy * sum |c+|^2 (Sec. II, Eq.
+ *   (pair_prod_homo)), summed in the same fixed order as dsp_reduce_density
+ *   (bitwise equal to it for an FP64 map).
+ * Scratch: a static device array inside the library sized for at most
+ * DSP_NOALLOC_MAX_POINTS points (about 512 KB, held on every GPU that loads
+ * the library until the process exits); larger maps are refused with
+ * DSP_E_INVALID before anything is queued.  The first call made with a given
+ * device current looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call overwrites the
+ * whole scratch it reads, so no state leaks between calls, but all calls
+ * share the one array: calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  Work is queued on
+ * cuda_stream (NULL: legacy stream), which the call synchronises. */
+#define DSP_NOALLOC_MAX_POINTS 67108864
+dsp_status dsp_density_noalloc(const void *map_dev, int32_t precision, int32_t nx, int32_t ny,
+                               double px_min, double px_max, double py_min, double py_max,
+                               void *cuda_stream, double *n_host);
+
 /* The whole hot path in one call: evolves the remaining steps with the
  * projection fused into the same kernel, writes map_dev (may be NULL: then an
  * internal map is used) and the density to *n_host (may be NULL).

@@ -37,7 +37,7 @@ EXPORTS = (
     "dsp_reduce_density", "dsp_solve", "dsp_solve_host", "dsp_evolve_batch", "dsp_get_cursor",
     "dsp_save_state", "dsp_load_state", "dsp_destroy_grid", "dsp_status_string",
     "dsp_sample_pulse", "dsp_server_create", "dsp_server_submit", "dsp_server_step",
-    "dsp_server_query", "dsp_server_cancel", "dsp_server_destroy",
+    "dsp_server_query", "dsp_server_cancel", "dsp_server_destroy", "dsp_density_noalloc",
 )
 
 
@@ -104,6 +104,7 @@ def lib() -> ctypes.CDLL:
                 "dsp_server_query": (i32, [p, i64, pi32, pd, p, pi64]),
                 "dsp_server_cancel": (i32, [p, i64]),
                 "dsp_server_destroy": (i32, [p]),
+                "dsp_density_noalloc": (i32, [p, i32, i32, i32, d, d, d, d, p, pd]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -217,6 +218,19 @@ def load_state(h: int, buf: np.ndarray, cursor: int):
 
 def destroy_grid(h: int):
     _check(lib().dsp_destroy_grid(ctypes.c_void_p(h)), "destroy_grid")
+
+
+def density_noalloc(map_ptr: int, precision, nx: int, ny: int, px_range, py_range,
+                    stream=0) -> float:
+    """Pair density of a device |c+|^2 map without any device allocation (the
+    scratch is a static array inside the library; see include/dsp.h)."""
+    n = ctypes.c_double()
+    _check(lib().dsp_density_noalloc(ctypes.c_void_p(int(map_ptr)), _enum(precision, PRECISIONS),
+                                     int(nx), int(ny), float(px_range[0]), float(px_range[1]),
+                                     float(py_range[0]), float(py_range[1]),
+                                     ctypes.c_void_p(int(stream)), ctypes.byref(n)),
+           "density_noalloc")
+    return n.value
 
 
 def status_string(code: int) -> str:

@@ -29,7 +29,7 @@ def _nvcc() -> str:
 
 
 def sources() -> list[str]:
-    return [os.path.join(CSRC, f) for f in ("dsp_kernels.cu", "dsp_api.cpp")]
+    return [os.path.join(CSRC, f) for f in ("dsp_kernels.cu", "dsp_api.cpp", "dsp_noalloc.cu")]
 
 
 def _stale() -> bool:
