@@ -129,6 +129,29 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture, with the
+# SHA-256 of the kernel source the counters were taken on; a different source
+# means the counters are stale and the traffic is reported as null.
+KERNEL_TRAFFIC = {
+    "evolve_mixed_kernel": {"bytes": 90.39e6, "source_sha256": "20baa4b392a40c84484c4950a5abef528a793333ec0a148577b8fb72b35e7c7a",
+                            "profile": "profiles/evolve_kernels_lzs2048_2000steps_full.md"},
+}
+
+
+def kernel_source_sha256():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1607_03062_gb300", "csrc", "dsp_kernels.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def kernel_traffic(name):
+    rec = KERNEL_TRAFFIC.get(name)
+    if not rec or rec["bytes"] is None or rec["source_sha256"] != kernel_source_sha256():
+        return None
+    return rec["bytes"]
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -139,48 +162,25 @@ def load_peaks():
 
 
 # ------------------------------------------------------------------------------------------
-# FP32-mixed instruction count per spinor-step (the kernel's formulation, EXACT scheme):
-#   P = p + A (hi and lo)            4
-#   theta^2 with the lo correction   5
-#   cos - 1 (degree D Horner)        D
-#   sin/theta (degree D Horner)      D
-#   valley sign                      1
-#   q = sinc * (P_y + i P_x)         4
-#   (U - I) psi + lo                 12
-#   Fast2Sum of the 4 components     12
-# FP64 per spinor-step: 2 + 2 + (D + 1) + D + 1 + 2 + 12.
+# FP32 lane instructions per spinor-step of the FP32-mixed EXACT step, with series
+# degrees dc (cos) and ds (sin/theta) as the library reports them:
+#   P_h = p_h + A_h, P_l = p_l + A_l, P = P_h + P_l (x and y)   6
+#   theta^2 = fma(Px, Px, Py*Py)                               2
+#   cos(theta) - 1 (Horner, dc - 1 FMA + 1 MUL)                dc
+#   sin(theta)/theta (Horner)                                  ds
+#   q = sinc * (P_y + i P_x)                                   2
+#   (U - I) psi_hi + psi_lo                                    12
+#   Fast2Sum of the 4 components                               12
+# FP64 instructions per spinor-step of the FP64 EXACT step:
+#   P (2) + theta^2 (2) + cos (dc) + sinc (ds) + q (2) + U psi (12)
 # ------------------------------------------------------------------------------------------
 
-def ops_mixed(D):
-    return 38 + 2 * D
+def ops_mixed(dc, ds):
+    return 34 + dc + ds
 
 
-def ops_fp64(D):
-    return 20 + 2 * D
-
-
-def degree_for(theta_max, fp64):
-    """Mirrors the library's degree choice to report the instruction count."""
-    import math
-    x = theta_max * theta_max
-    tol = 2.0 ** -54 if fp64 else 2.0 ** -26
-    for D in ((5, 8, 13) if fp64 else (3, 5, 9)):
-        ec = 2.0 * x ** D / math.factorial(2 * D + 2)
-        es = x ** (D + 1) / math.factorial(2 * D + 3)
-        if ec < tol and es < tol:
-            return D
-    return 13 if fp64 else 9
-
-
-def theta_max_of(cfg, a_mid, dt):
-    g = cfg["grid"]
-    cx = np.array(g["px"])[:, None]
-    cy = np.array(g["py"])[:, None]
-    m = 0.0
-    for x in cx:
-        for y in cy:
-            m = max(m, float(np.hypot(x + a_mid[:, 0], y + a_mid[:, 1]).max()))
-    return dt * m
+def ops_fp64(dc, ds):
+    return 18 + dc + ds
 
 
 # ------------------------------------------------------------------------------------------
@@ -227,6 +227,7 @@ def run_gpu(args):
         h, state, mp = make(prec)
         dens = []
         times = []
+        ops = []
         for k in range(warm + steps):
             s = (sample_offset + k * world + rank) % N_SAMPLES
             a_mid, a_in, a_out, dt = tables[s]
@@ -244,14 +245,17 @@ def run_gpu(args):
             if k >= warm:
                 times.append(e0.elapsed_time(e1) / 1e3)
                 dens.append(B.reduce_density(h))
+                info = B.get_info(h)
+                f = ops_fp64 if prec == "fp64" else ops_mixed
+                ops.append(f(info["cos_degree"], info["sinc_degree"]))
         B.destroy_grid(h)
         del state, mp
-        return times, dens
+        return times, dens, ops
 
     sampler = ClockSampler(local)
     # ---- FP32-mixed (headline) ----
     sampler.start()
-    t_mixed, d_mixed = timed_solves("fp32_mixed", args.warmup, args.steps, 0)
+    t_mixed, d_mixed, o_mixed = timed_solves("fp32_mixed", args.warmup, args.steps, 0)
     clocks = sampler.stop()
     tot = sum(t_mixed)
     if world > 1:
@@ -265,8 +269,8 @@ def run_gpu(args):
     fp64 = None
     if not args.no_fp64:
         # offset so the FP64 leg's timed samples are the FP32-mixed leg's first ones
-        t64, d64 = timed_solves("fp64", args.fp64_warmup, args.fp64_steps,
-                                (args.warmup - args.fp64_warmup) * world)
+        t64, d64, o64 = timed_solves("fp64", args.fp64_warmup, args.fp64_steps,
+                                     (args.warmup - args.fp64_warmup) * world)
         tt = sum(t64)
         if world > 1:
             t = torch.tensor([tt], dtype=torch.float64, device="cuda")
@@ -318,27 +322,23 @@ def run_gpu(args):
 
     # ---- roofline of the evolve kernel (FP32 pipe) ----
     peaks = load_peaks()
-    th = max(theta_max_of(c, t[0], t[3]) for c, t in zip(cfgs, tables))
-    D = degree_for(th, False)
-    ops_step = ops_mixed(D)
-    launch_s = statistics.mean(t_mixed)
-    achieved = ops_step * work_per_solve / launch_s / 1e12
-    sm_max = SM_MAX_MHZ_NOMINAL
-    peak = SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    # achieved = algorithmic FP32 instructions of each timed launch / its event time
+    achieved = statistics.mean(o * work_per_solve / t for o, t in zip(o_mixed, t_mixed)) / 1e12
+    peak = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "Tinst/s (FP32 lane instructions)", "frac": achieved / peak,
-            "traffic": None, "kernel": "evolve_mixed_kernel",
-            "ops_per_spinor_step": ops_step, "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz"}
+            "traffic": kernel_traffic("evolve_mixed_kernel"), "kernel": "evolve_mixed_kernel",
+            "ops_per_spinor_step": o_mixed,
+            "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts x max SM clock)"}
     if clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (SMS * FP32_LANES_PER_SM *
                                                      clocks["sm_mhz"] * 1e6 / 1e12)
     if fp64:
-        D64 = degree_for(th, True)
-        a64 = ops_fp64(D64) * fp64["value"] / world / 1e12
+        a64 = statistics.mean(o * work_per_solve / t for o, t in zip(o64, t64)) / 1e12
         fp64["roofline"] = {"bound": "alu", "achieved": a64,
                             "peak": FP64_NOMINAL_FLOPS / 2 / 1e12,
                             "unit": "T FP64 inst/s", "frac": a64 / (FP64_NOMINAL_FLOPS / 2 / 1e12),
-                            "ops_per_spinor_step": ops_fp64(D64),
+                            "ops_per_spinor_step": o64,
                             "peak_basis": "nominal 1.25 TFLOP/s FP64 = 0.625 T DFMA/s"}
 
     # ---- CPU baseline: the oracle on a bounded sample ----

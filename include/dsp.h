@@ -162,6 +162,20 @@ dsp_status dsp_evolve_batch(dsp_grid *const *grids, const int64_t *steps, int32_
 /* Cursor and pulse length of a grid. */
 dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps);
 
+/* What the library chose for the current pulse: the degrees (in theta^2) of
+ * the cos(theta) and sin(theta)/theta series used per step (picked so their
+ * truncation error over all n_steps stays below 2e-8 in FP32_MIXED, 1e-16 in
+ * FP64), theta_max = dt * max|p + A_n| over the box, the hi/lo grid 2^k of the
+ * FP32_MIXED momentum split, and the tile count. */
+typedef struct {
+    int32_t nx, ny, precision, scheme, valley;
+    int32_t cos_degree, sinc_degree;
+    int32_t n_tiles;
+    int64_t n_steps, cursor;
+    double dt, theta_max, quant;
+} dsp_grid_info;
+dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info);
+
 /* Copies the raw spinor state (dsp_state_bytes bytes) to the host, or back
  * from the host, with the step cursor, for checkpoint / resume.  Synchronise. */
 dsp_status dsp_save_state(dsp_grid *g, void *host_buf, int64_t bytes, int64_t *cursor);

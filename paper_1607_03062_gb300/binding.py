@@ -38,6 +38,7 @@ EXPORTS = (
     "dsp_save_state", "dsp_load_state", "dsp_destroy_grid", "dsp_status_string",
     "dsp_sample_pulse", "dsp_server_create", "dsp_server_submit", "dsp_server_step",
     "dsp_server_query", "dsp_server_cancel", "dsp_server_destroy", "dsp_density_noalloc",
+    "dsp_get_info",
 )
 
 
@@ -51,6 +52,13 @@ class PulseSpec(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32)] + [
         (n, ctypes.c_double) for n in ("E0", "omega", "T", "tau", "t0", "eps", "phase2",
                                        "Omega_rise", "Omega_fall", "phi")]
+
+
+class GridInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("nx", "ny", "precision", "scheme", "valley",
+                                              "cos_degree", "sinc_degree", "n_tiles")] + [
+        ("n_steps", ctypes.c_int64), ("cursor", ctypes.c_int64), ("dt", ctypes.c_double),
+        ("theta_max", ctypes.c_double), ("quant", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -105,6 +113,7 @@ def lib() -> ctypes.CDLL:
                 "dsp_server_cancel": (i32, [p, i64]),
                 "dsp_server_destroy": (i32, [p]),
                 "dsp_density_noalloc": (i32, [p, i32, i32, i32, d, d, d, d, p, pd]),
+                "dsp_get_info": (i32, [p, ctypes.POINTER(GridInfo)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -202,6 +211,13 @@ def get_cursor(h: int):
     _check(lib().dsp_get_cursor(ctypes.c_void_p(h), ctypes.byref(c), ctypes.byref(n)),
            "get_cursor")
     return c.value, n.value
+
+
+def get_info(h: int) -> dict:
+    """Series degrees, theta_max, hi/lo grid and tile count chosen for the current pulse."""
+    info = GridInfo()
+    _check(lib().dsp_get_info(ctypes.c_void_p(h), ctypes.byref(info)), "get_info")
+    return {n: getattr(info, n) for n, _ in GridInfo._fields_}
 
 
 def save_state(h: int, buf: np.ndarray) -> int:

@@ -55,7 +55,8 @@ struct dsp_grid {
     int64_t n_steps = 0, cursor = 0;
     double dt = 0, a_in[2] = {0, 0}, a_out[2] = {0, 0};
     double quant = 1, inv_quant = 1;
-    int32_t degree_idx = 0;
+    int32_t level = 0;
+    double theta_max = 0.0;
     bool fresh = true;      // state not yet written on the device
     bool projected = false;  // partial sums valid for the current pulse
     dsp_status latched = DSP_OK;
@@ -76,27 +77,33 @@ dsp_status latch_cuda(dsp_grid *g, cudaError_t e)
 
 size_t map_elem_bytes(int32_t precision) { return precision == DSP_FP64 ? 8 : 4; }
 
-// Smallest instantiated polynomial degree whose truncation error is below the
-// working precision for every theta <= theta_max (x = theta^2):
-//   cos(theta) - 1: next term relative to x/2 is 2 x^D / (2D+2)!
-//   sin(theta)/theta: next term x^(D+1) / (2D+3)!
-int32_t choose_degree(int32_t precision, double theta_max)
+// Lowest series level whose truncation error stays inside a fixed budget over
+// the whole run.  Truncating cos(theta) after x^dc leaves dc_err ~ x^(dc+1)/(2dc+2)!,
+// truncating sin(theta)/theta after x^ds leaves ds_err ~ x^(ds+1)/(2ds+3)!
+// (x = theta^2; alternating series, so the first omitted term bounds the error).
+// Both errors have a fixed sign, so they add up over steps: per step they
+// perturb the norm by ~2 dc_err + 2 x ds_err and the rotation angle by
+// ~theta ds_err.  The budget over n_steps steps is 2e-8 (FP32_MIXED, well below
+// its 1e-5 target) or 1e-16 (FP64).
+int32_t choose_level(int32_t precision, double theta, int64_t n_steps)
 {
-    const double x = theta_max * theta_max;
-    const double tol = precision == DSP_FP64 ? std::ldexp(1.0, -54) : std::ldexp(1.0, -26);
-    const int *degs = precision == DSP_FP64 ? dsp::kDegF64 : dsp::kDegF32;
-    for (int i = 0; i < 3; ++i) {
-        const int D = degs[i];
-        double f2 = 1.0, f3 = 1.0;  // (2D+2)!, (2D+3)!
-        for (int k = 2; k <= 2 * D + 2; ++k)
-            f2 *= k;
-        f3 = f2 * (2 * D + 3);
-        const double ec = 2.0 * std::pow(x, D) / f2;
-        const double es = std::pow(x, D + 1) / f3;
-        if (ec < tol && es < tol)
+    const double x = theta * theta;
+    const double budget =
+        (precision == DSP_FP64 ? 1e-16 : 2e-8) / static_cast<double>(std::max<int64_t>(n_steps, 1));
+    const dsp::SeriesLevel *lv = precision == DSP_FP64 ? dsp::kLevelsF64 : dsp::kLevelsF32;
+    for (int i = 0; i < dsp::kNumLevels; ++i) {
+        double fc = 1.0, fs = 1.0;  // (2dc+2)!, (2ds+3)!
+        for (int k = 2; k <= 2 * lv[i].dc + 2; ++k)
+            fc *= k;
+        for (int k = 2; k <= 2 * lv[i].ds + 3; ++k)
+            fs *= k;
+        const double dc_err = std::pow(x, lv[i].dc + 1) / fc;
+        const double ds_err = std::pow(x, lv[i].ds + 1) / fs;
+        const double err = std::max(2.0 * dc_err + 2.0 * x * ds_err, theta * ds_err);
+        if (err <= budget)
             return i;
     }
-    return 2;
+    return dsp::kNumLevels - 1;
 }
 
 double box_abs_max(const dsp_grid *g)
@@ -166,7 +173,7 @@ ReqDesc make_desc(const dsp_grid *g, int64_t begin, int64_t end, bool project, v
     r.ny = g->ny;
     r.scheme = g->scheme;
     r.valley = g->valley;
-    r.degree_idx = g->degree_idx;
+    r.level = g->level;
     r.fresh = g->fresh ? 1 : 0;
     r.project = project ? 1 : 0;
     r.n_tiles = g->n_tiles;
@@ -293,17 +300,19 @@ void build_table(const dsp_grid *g, const double *a_mid, int64_t n, double dt, d
                  double inv_quant, std::vector<unsigned char> &out)
 {
     out.resize(static_cast<size_t>(n) * 16);
+    // valley K- is stepped as K+ on -P, so its table holds -dt*A
+    const double vs = g->valley > 0 ? 1.0 : -1.0;
     if (g->precision == DSP_FP64) {
         double *t = reinterpret_cast<double *>(out.data());
         for (int64_t k = 0; k < n; ++k) {
-            t[2 * k] = dt * a_mid[2 * k];
-            t[2 * k + 1] = dt * a_mid[2 * k + 1];
+            t[2 * k] = vs * (dt * a_mid[2 * k]);
+            t[2 * k + 1] = vs * (dt * a_mid[2 * k + 1]);
         }
     } else {
         float *t = reinterpret_cast<float *>(out.data());
         for (int64_t k = 0; k < n; ++k) {
             for (int c = 0; c < 2; ++c) {
-                const double v = dt * a_mid[2 * k + c];
+                const double v = vs * (dt * a_mid[2 * k + c]);
                 const double hi = std::rint(v * quant) * inv_quant;
                 t[4 * k + 2 * c] = static_cast<float>(hi);
                 t[4 * k + 2 * c + 1] = static_cast<float>(v - hi);
@@ -426,7 +435,8 @@ dsp_status set_pulse_impl(dsp_grid *g, const double *a_mid, int64_t n_steps, dou
     g->a_out[1] = a_out[1];
     g->quant = quant;
     g->inv_quant = 1.0 / quant;
-    g->degree_idx = choose_degree(g->precision, tmax);
+    g->theta_max = tmax;
+    g->level = choose_level(g->precision, tmax, n_steps);
     g->fresh = true;
     g->projected = false;
     return DSP_OK;
@@ -644,6 +654,29 @@ dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps)
         return DSP_E_INVALID;
     *cursor = g->cursor;
     *n_steps = g->n_steps;
+    return DSP_OK;
+}
+
+dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info)
+{
+    if (!g || !info)
+        return DSP_E_INVALID;
+    std::memset(info, 0, sizeof(*info));
+    info->nx = g->nx;
+    info->ny = g->ny;
+    info->precision = g->precision;
+    info->scheme = g->scheme;
+    info->valley = g->valley;
+    const dsp::SeriesLevel lv =
+        (g->precision == DSP_FP64 ? dsp::kLevelsF64 : dsp::kLevelsF32)[g->level];
+    info->cos_degree = lv.dc;
+    info->sinc_degree = lv.ds;
+    info->n_steps = g->n_steps;
+    info->cursor = g->cursor;
+    info->n_tiles = g->n_tiles;
+    info->dt = g->dt;
+    info->theta_max = g->theta_max;
+    info->quant = g->quant;
     return DSP_OK;
 }
 

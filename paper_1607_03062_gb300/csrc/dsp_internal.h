@@ -23,14 +23,23 @@ constexpr int kErrTimeout = 1;
 // Bound on one mbarrier wait, in nanoseconds of %globaltimer.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
-// Polynomial degrees (in x = theta^2) instantiated for cos(theta)-1 and
-// sin(theta)/theta; the host picks the smallest one accurate for the
-// request's largest phase step theta_max.
-constexpr int kDegF32[3] = {3, 5, 9};
-constexpr int kDegF64[3] = {5, 8, 13};
+// Series levels: (degree of cos(theta) in x = theta^2, degree of
+// sin(theta)/theta in x).  The host picks, per request, the lowest level whose
+// truncation error, accumulated over all the request's steps at its largest
+// phase step theta_max, stays below a fixed budget (see choose_level).
+struct SeriesLevel {
+    int dc, ds;
+};
+constexpr int kNumLevels = 8;
+constexpr SeriesLevel kLevelsF32[kNumLevels] = {{2, 1}, {2, 2}, {3, 2}, {3, 3},
+                                                 {4, 4}, {6, 6}, {9, 9}, {12, 12}};
+constexpr SeriesLevel kLevelsF64[kNumLevels] = {{3, 3}, {4, 3}, {4, 4}, {5, 5},
+                                                 {6, 6}, {8, 8}, {11, 11}, {16, 16}};
 
 struct ReqDesc {
-    const void *table;  // float4 (FP32_MIXED: dt*Ax hi, lo, dt*Ay hi, lo) or double2 (FP64: dt*A)
+    // float4 (FP32_MIXED: s*dt*Ax hi, lo, s*dt*Ay hi, lo) or double2 (FP64: s*dt*A),
+    // s = valley: valley K- steps as K+ on -P (its step operator is K+'s at -P).
+    const void *table;
     void *state;        // planes: FP32_MIXED float4 hi[n], float4 lo[n]; FP64 double2 a[n], double2 b[n]
     void *map;          // |c+|^2 output (float or double), or nullptr
     double *partials;   // one double per tile (written when projecting)
@@ -41,7 +50,7 @@ struct ReqDesc {
     int64_t n_points;
     int64_t step_begin, step_end;  // table entries [step_begin, step_end) this launch
     int32_t nx, ny;
-    int32_t scheme, valley, degree_idx;
+    int32_t scheme, valley, level;
     int32_t fresh;    // 1: start from v(p + A_in) instead of reading the state
     int32_t project;  // 1: project at the end (map + partials)
     int32_t tile_begin;  // first CTA of this request in the launch

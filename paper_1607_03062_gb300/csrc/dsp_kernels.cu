@@ -146,9 +146,9 @@ __device__ __forceinline__ float sinc_f32(float x)
     return horner<float, D, 0, 1>(x);
 }
 template <int D>
-__device__ __forceinline__ double cosm1_f64(double x)
+__device__ __forceinline__ double cos_f64(double x)
 {
-    return horner<double, D, 1, 0>(x) * x;
+    return horner<double, D, 0, 0>(x);
 }
 template <int D>
 __device__ __forceinline__ double sinc_f64(double x)
@@ -260,30 +260,29 @@ struct MixedPoint {
 };
 
 // Coefficients of U - I = [[cm1, -q], [conj(q), cm1]] for the step with kinematic
-// momentum dt*P = (Pxh + Pxl, Pyh + Pyl).
-template <int SCHEME, int D>
+// momentum dt*P = (Pxh + Pxl, Pyh + Pyl).  P_h = p_h + A_h is exact (common 2^-k
+// grid), so P = fl(P_h + P_l) carries only its own final rounding, which varies
+// from step to step with A; no fixed (systematic) momentum error remains.
+template <int SCHEME, int DC, int DS>
 __device__ __forceinline__ void step_coeffs_f32(float Pxh, float Pxl, float Pyh, float Pyl,
-                                                float sgn, float &cm1, float &qr, float &qi)
+                                                float &cm1, float &qr, float &qi)
 {
+    const float Px = Pxh + Pxl, Py = Pyh + Pyl;
     if constexpr (SCHEME == 0) {
-        // theta^2 = |dt P|^2 with the first-order lo correction
-        float x = fmaf(Pxh, Pxh, Pyh * Pyh);
-        x = fmaf(2.0f, fmaf(Pxh, Pxl, Pyh * Pyl), x);
-        cm1 = cosm1_f32<D>(x);
-        const float sn = sinc_f32<D>(x) * sgn;
-        qr = sn * (Pyh + Pyl);
-        qi = sn * (Pxh + Pxl);
+        const float x = fmaf(Px, Px, Py * Py);  // theta^2
+        cm1 = cosm1_f32<DC>(x);
+        const float sn = sinc_f32<DS>(x);
+        qr = sn * Py;
+        qi = sn * Px;
     } else {
         // e^{-i a sx} e^{-i b sy} e^{-i a sx}, a = dt Px / 2, b = dt Py:
         //   = [[cos b cos 2a, -(sin b + i cos b sin 2a)], [sin b - i cos b sin 2a, cos b cos 2a]]
-        const float xx = fmaf(Pxh, Pxh, 2.0f * Pxh * Pxl);
-        const float xy = fmaf(Pyh, Pyh, 2.0f * Pyh * Pyl);
-        const float cmx = cosm1_f32<D>(xx), cmy = cosm1_f32<D>(xy);
-        const float sx = (Pxh + Pxl) * sinc_f32<D>(xx) * sgn;
-        const float sy = (Pyh + Pyl) * sinc_f32<D>(xy) * sgn;
-        cm1 = cmx + cmy + cmx * cmy;
-        qr = sy;
-        qi = (1.0f + cmy) * sx;
+        const float xx = Px * Px, xy = Py * Py;
+        const float cmx = cosm1_f32<DC>(xx), cmy = cosm1_f32<DC>(xy);
+        const float sx = Px * sinc_f32<DS>(xx);
+        cm1 = fmaf(cmx, cmy, cmx) + cmy;
+        qr = Py * sinc_f32<DS>(xy);
+        qi = fmaf(cmy, sx, sx);
     }
 }
 
@@ -302,14 +301,14 @@ __device__ __forceinline__ void apply_f32(MixedPoint &s, float cm1, float qr, fl
     t = s.bi + dbi; s.lbi = dbi - (t - s.bi); s.bi = t;
 }
 
-template <int SCHEME, int D>
+template <int SCHEME, int DC, int DS>
 __device__ void body_mixed(const ReqDesc &R, int tile, float4 (*buf)[kChunkSteps], uint64_t *bars,
                            int *err)
 {
     constexpr int S = kSpinorsPerThread;
     const int tid = threadIdx.x;
     const int64_t base = static_cast<int64_t>(tile) * kTilePoints;
-    const float sgn = R.valley > 0 ? 1.0f : -1.0f;
+    const double vs = R.valley > 0 ? 1.0 : -1.0;
     float4 *hi_plane = static_cast<float4 *>(R.state);
     float4 *lo_plane = hi_plane + R.n_points;
 
@@ -323,7 +322,8 @@ __device__ void body_mixed(const ReqDesc &R, int tile, float4 (*buf)[kChunkSteps
             px = grid_node(R.px_min, R.hx, idx % R.nx);
             py = grid_node(R.py_min, R.hy, idx / R.nx);
         }
-        const double tx = R.dt * px, ty = R.dt * py;
+        // valley K- is stepped as K+ on -P: the table holds -dt*A, here -dt*p
+        const double tx = vs * (R.dt * px), ty = vs * (R.dt * py);
         const double hx = rint(tx * R.quant) * R.inv_quant, hy = rint(ty * R.quant) * R.inv_quant;
         pt[s].pxh = static_cast<float>(hx);
         pt[s].pxl = static_cast<float>(tx - hx);
@@ -331,7 +331,7 @@ __device__ void body_mixed(const ReqDesc &R, int tile, float4 (*buf)[kChunkSteps
         pt[s].pyl = static_cast<float>(ty - hy);
         if (R.fresh || !valid) {
             double ar, ai, br, bi;
-            initial_spinor(px + R.a_in[0], py + R.a_in[1], static_cast<double>(sgn), ar, ai, br, bi);
+            initial_spinor(px + R.a_in[0], py + R.a_in[1], vs, ar, ai, br, bi);
             pt[s].ar = static_cast<float>(ar);
             pt[s].lar = static_cast<float>(ar - static_cast<double>(pt[s].ar));
             pt[s].ai = static_cast<float>(ai);
@@ -369,8 +369,8 @@ __device__ void body_mixed(const ReqDesc &R, int tile, float4 (*buf)[kChunkSteps
 #pragma unroll
             for (int s = 0; s < S; ++s) {
                 float cm1, qr, qi;
-                step_coeffs_f32<SCHEME, D>(pt[s].pxh + a.x, pt[s].pxl + a.y, pt[s].pyh + a.z,
-                                           pt[s].pyl + a.w, sgn, cm1, qr, qi);
+                step_coeffs_f32<SCHEME, DC, DS>(pt[s].pxh + a.x, pt[s].pxl + a.y, pt[s].pyh + a.z,
+                                                pt[s].pyl + a.w, cm1, qr, qi);
                 apply_f32(pt[s], cm1, qr, qi);
             }
         }
@@ -403,8 +403,7 @@ __device__ void body_mixed(const ReqDesc &R, int tile, float4 (*buf)[kChunkSteps
                 const double ai = static_cast<double>(pt[s].ai) + pt[s].lai;
                 const double br = static_cast<double>(pt[s].br) + pt[s].lbr;
                 const double bi = static_cast<double>(pt[s].bi) + pt[s].lbi;
-                cp2[s] = project_point(px + R.a_out[0], py + R.a_out[1], static_cast<double>(sgn),
-                                       ar, ai, br, bi);
+                cp2[s] = project_point(px + R.a_out[0], py + R.a_out[1], vs, ar, ai, br, bi);
                 if (R.map)
                     static_cast<float *>(R.map)[idx] = static_cast<float>(cp2[s]);
             }
@@ -431,23 +430,23 @@ struct F64Point {
     double tx, ty;  // dt * p
 };
 
-template <int SCHEME, int D>
-__device__ __forceinline__ void step_f64(F64Point &s, double2 a, double sgn)
+template <int SCHEME, int DC, int DS>
+__device__ __forceinline__ void step_f64(F64Point &s, double2 a)
 {
-    const double Px = s.tx + a.x, Py = s.ty + a.y;  // dt * P
+    const double Px = s.tx + a.x, Py = s.ty + a.y;  // dt * P (times the valley sign)
     double c, qr, qi;
     if constexpr (SCHEME == 0) {
         const double x = fma(Px, Px, Py * Py);
-        c = 1.0 + cosm1_f64<D>(x);
-        const double sn = sinc_f64<D>(x) * sgn;
+        c = cos_f64<DC>(x);
+        const double sn = sinc_f64<DS>(x);
         qr = sn * Py;
         qi = sn * Px;
     } else {
         const double xx = Px * Px, xy = Py * Py;
-        const double cy = 1.0 + cosm1_f64<D>(xy);
-        c = cy * (1.0 + cosm1_f64<D>(xx));
-        qr = Py * sinc_f64<D>(xy) * sgn;
-        qi = cy * Px * sinc_f64<D>(xx) * sgn;
+        const double cy = cos_f64<DC>(xy);
+        c = cy * cos_f64<DC>(xx);
+        qr = Py * sinc_f64<DS>(xy);
+        qi = cy * (Px * sinc_f64<DS>(xx));
     }
     // a' = c a - q b ; b' = conj(q) a + c b, q = qr + i qi
     const double nar = fma(c, s.ar, fma(-qr, s.br, qi * s.bi));
@@ -457,14 +456,14 @@ __device__ __forceinline__ void step_f64(F64Point &s, double2 a, double sgn)
     s.ar = nar; s.ai = nai; s.br = nbr; s.bi = nbi;
 }
 
-template <int SCHEME, int D>
+template <int SCHEME, int DC, int DS>
 __device__ void body_f64(const ReqDesc &R, int tile, double2 (*buf)[kChunkSteps], uint64_t *bars,
                          int *err)
 {
     constexpr int S = kSpinorsPerThread;
     const int tid = threadIdx.x;
     const int64_t base = static_cast<int64_t>(tile) * kTilePoints;
-    const double sgn = R.valley > 0 ? 1.0 : -1.0;
+    const double vs = R.valley > 0 ? 1.0 : -1.0;
     double2 *a_plane = static_cast<double2 *>(R.state);
     double2 *b_plane = a_plane + R.n_points;
 
@@ -478,10 +477,10 @@ __device__ void body_f64(const ReqDesc &R, int tile, double2 (*buf)[kChunkSteps]
             px = grid_node(R.px_min, R.hx, idx % R.nx);
             py = grid_node(R.py_min, R.hy, idx / R.nx);
         }
-        pt[s].tx = R.dt * px;
-        pt[s].ty = R.dt * py;
+        pt[s].tx = vs * (R.dt * px);  // valley K- is stepped as K+ on -P
+        pt[s].ty = vs * (R.dt * py);
         if (R.fresh || !valid) {
-            initial_spinor(px + R.a_in[0], py + R.a_in[1], sgn, pt[s].ar, pt[s].ai, pt[s].br,
+            initial_spinor(px + R.a_in[0], py + R.a_in[1], vs, pt[s].ar, pt[s].ai, pt[s].br,
                            pt[s].bi);
         } else {
             const double2 a = a_plane[idx], b = b_plane[idx];
@@ -510,7 +509,7 @@ __device__ void body_f64(const ReqDesc &R, int tile, double2 (*buf)[kChunkSteps]
             const double2 a = tb[j];
 #pragma unroll
             for (int s = 0; s < S; ++s)
-                step_f64<SCHEME, D>(pt[s], a, sgn);
+                step_f64<SCHEME, DC, DS>(pt[s], a);
         }
         __syncthreads();
         if (tid == 0 && c + 2 < st.nchunks)
@@ -536,7 +535,7 @@ __device__ void body_f64(const ReqDesc &R, int tile, double2 (*buf)[kChunkSteps]
             if (R.project) {
                 const double px = grid_node(R.px_min, R.hx, idx % R.nx);
                 const double py = grid_node(R.py_min, R.hy, idx / R.nx);
-                cp2[s] = project_point(px + R.a_out[0], py + R.a_out[1], sgn, pt[s].ar, pt[s].ai,
+                cp2[s] = project_point(px + R.a_out[0], py + R.a_out[1], vs, pt[s].ar, pt[s].ai,
                                        pt[s].br, pt[s].bi);
                 if (R.map)
                     static_cast<double *>(R.map)[idx] = cp2[s];
@@ -553,6 +552,28 @@ __device__ void body_f64(const ReqDesc &R, int tile, double2 (*buf)[kChunkSteps]
         if (tid == 0)
             R.partials[tile] = sum;
     }
+}
+
+// Block-uniform dispatch on the request's series level (compile-time degrees).
+template <int SCHEME, int L>
+__device__ __forceinline__ void dispatch_mixed(const ReqDesc &R, int tile,
+                                               float4 (*buf)[kChunkSteps], uint64_t *bars,
+                                               int *err)
+{
+    if (R.level == L || L + 1 == kNumLevels)
+        body_mixed<SCHEME, kLevelsF32[L].dc, kLevelsF32[L].ds>(R, tile, buf, bars, err);
+    else if constexpr (L + 1 < kNumLevels)
+        dispatch_mixed<SCHEME, L + 1>(R, tile, buf, bars, err);
+}
+
+template <int SCHEME, int L>
+__device__ __forceinline__ void dispatch_f64(const ReqDesc &R, int tile,
+                                             double2 (*buf)[kChunkSteps], uint64_t *bars, int *err)
+{
+    if (R.level == L || L + 1 == kNumLevels)
+        body_f64<SCHEME, kLevelsF64[L].dc, kLevelsF64[L].ds>(R, tile, buf, bars, err);
+    else if constexpr (L + 1 < kNumLevels)
+        dispatch_f64<SCHEME, L + 1>(R, tile, buf, bars, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -573,15 +594,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int r = find_request(args);
     const ReqDesc &R = args.r[r];
     const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
-    switch (R.scheme * 4 + R.degree_idx) {
-    case 0: body_mixed<0, kDegF32[0]>(R, tile, buf, bars, args.err); break;
-    case 1: body_mixed<0, kDegF32[1]>(R, tile, buf, bars, args.err); break;
-    case 2: body_mixed<0, kDegF32[2]>(R, tile, buf, bars, args.err); break;
-    case 4: body_mixed<1, kDegF32[0]>(R, tile, buf, bars, args.err); break;
-    case 5: body_mixed<1, kDegF32[1]>(R, tile, buf, bars, args.err); break;
-    case 6: body_mixed<1, kDegF32[2]>(R, tile, buf, bars, args.err); break;
-    default: break;
-    }
+    if (R.scheme == 0)
+        dispatch_mixed<0, 0>(R, tile, buf, bars, args.err);
+    else
+        dispatch_mixed<1, 0>(R, tile, buf, bars, args.err);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -598,15 +614,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r = find_request(args);
     const ReqDesc &R = args.r[r];
     const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
-    switch (R.scheme * 4 + R.degree_idx) {
-    case 0: body_f64<0, kDegF64[0]>(R, tile, buf, bars, args.err); break;
-    case 1: body_f64<0, kDegF64[1]>(R, tile, buf, bars, args.err); break;
-    case 2: body_f64<0, kDegF64[2]>(R, tile, buf, bars, args.err); break;
-    case 4: body_f64<1, kDegF64[0]>(R, tile, buf, bars, args.err); break;
-    case 5: body_f64<1, kDegF64[1]>(R, tile, buf, bars, args.err); break;
-    case 6: body_f64<1, kDegF64[2]>(R, tile, buf, bars, args.err); break;
-    default: break;
-    }
+    if (R.scheme == 0)
+        dispatch_f64<0, 0>(R, tile, buf, bars, args.err);
+    else
+        dispatch_f64<1, 0>(R, tile, buf, bars, args.err);
 }
 
 // One CTA per density: fixed-order per-thread sums, then a pairwise tree.

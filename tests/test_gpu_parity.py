@@ -249,3 +249,50 @@ def test_lzs_2048_full_size_sampled(orc, prec):
     assert err <= TOL[prec][0], f"{prec}: max sampled error {err:.3e}"
     assert np.all(np.isfinite(m)) and m.min() >= 0.0 and m.max() <= 1.0 + 1e-6
     assert n > 0
+
+
+def _sampled_parity(orc, cfg, prec, n_sample=256, seed=5, band_rows=8):
+    """Full-size solve on the GPU; seeded points plus a band around p_y = 0
+    (where pairs are likely) recomputed one by one by the oracle."""
+    g = cfg["grid"]
+    m, n = run_gpu(g, B.sample_pulse(cfg["pulse"], cfg["steps"]), prec)
+    tab = orc.pulse_table(cfg["pulse"], cfg["steps"])
+    idx = W.sample_points(g["nx"], g["ny"], n_sample, seed=seed)
+    rows = np.arange(g["ny"] // 2 - band_rows // 2, g["ny"] // 2 + band_rows // 2)
+    cols = np.linspace(0, g["nx"] - 1, 24).astype(int)
+    idx = np.unique(np.concatenate([idx, (rows[:, None] * g["nx"] + cols[None, :]).ravel()]))
+    xs = orc.grid_nodes(*g["px"], g["nx"])
+    ys = orc.grid_nodes(*g["py"], g["ny"])
+    r = orc.solve_points(xs[idx % g["nx"]], ys[idx // g["nx"]], tab[0], tab[3], tab[1], tab[2])
+    err = np.abs(m.ravel()[idx] - r["cplus2"]).max()
+    assert err <= TOL[prec][0], f"{prec}: sampled max error {err:.3e}"
+    assert np.all(np.isfinite(m)) and m.min() >= 0.0 and m.max() <= 1.0 + 1e-6
+    return m, n, r
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+@pytest.mark.parametrize("E0", [0.5, 2.0, 5.0])
+def test_gauss_1024_full_size_sampled(orc, prec, E0):
+    """1024x1024 on [-8,8]^2, Gaussian pulse (tau = 4 cycles), 3e4 steps."""
+    _sampled_parity(orc, W.config_gauss_1024(E0), prec)
+
+
+def test_two_colour_4096_full_size_sampled(orc):
+    """4096x4096 on [-12,12]^2, two-colour elliptical pulse, 2e5 steps, FP32-mixed
+    (the FP64 solve of this size takes minutes and is left to the benchmark)."""
+    _sampled_parity(orc, W.config_two_colour_4096(), "fp32_mixed", n_sample=192, band_rows=4)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_paper_laser_pulse_map(orc, prec):
+    """Sec. IV pulse (Fig. 1 parameters in eV units): A_in = 0 and A_out != 0, so
+    the projection uses a shifted momentum.  Whole 64x64 map on [-0.5,0.5]^2."""
+    pulse = W.paper_pulse()
+    grid = {"nx": 64, "ny": 64, "px": (-0.5, 0.5), "py": (-0.5, 0.5)}
+    steps = 20000
+    tab_o = orc.pulse_table(pulse, steps)
+    assert abs(tab_o[2][0]) > 1e-3  # A_out != 0
+    ref, nref = run_oracle(orc, grid, tab_o)
+    m, n = run_gpu(grid, B.sample_pulse(pulse, steps), prec)
+    assert ref.max() > 1e-3
+    assert_close(prec, m, n, ref, nref)
