@@ -31,6 +31,14 @@
  * The "STRANG_XY" scheme is not in the paper: it splits sigma.P into its
  * sigma_x and sigma_y parts, e^{-i dt/2 Px sx} e^{-i dt Py sy} e^{-i dt/2 Px sx},
  * each factor a closed-form rotation.  Here it is applied unmerged.
+ *
+ * The "MAGNUS4" scheme is the higher-order decomposition Sec. III says the
+ * midpoint rule can be improved to: the fourth-order Magnus integrator with two
+ * Gauss points per step, t_n + (1/2 -/+ sqrt(3)/6) dt:
+ *   Omega = dt/2 (A1 + A2) - sqrt(3) dt^2 / 12 [A1, A2],  A_k = -i valley sigma.P_k,
+ *   U_n = exp(Omega).
+ * Here Omega is formed as a 2x2 matrix from that definition, and its
+ * exponential is taken in closed form (Omega is traceless anti-Hermitian).
  */
 #include <complex.h>
 #include <math.h>
@@ -204,6 +212,27 @@ int orc_pulse_table(const orc_pulse *s, int64_t n_steps, double *a_mid, double *
     return 0;
 }
 
+/* Two Gauss points per step for the MAGNUS4 scheme: a_gauss[4n .. 4n+3] =
+ * (A_x, A_y)(t_n + (1/2 - sqrt(3)/6) dt), (A_x, A_y)(t_n + (1/2 + sqrt(3)/6) dt). */
+int orc_pulse_table_gauss(const orc_pulse *s, int64_t n_steps, double *a_gauss, double *a_in,
+                          double *a_out, double *dt_out)
+{
+    int64_t n;
+    double dt;
+    const double c1 = 0.5 - sqrt(3.0) / 6.0, c2 = 0.5 + sqrt(3.0) / 6.0;
+    if (!s || n_steps < 0 || !(s->T > 0.0))
+        return -1;
+    dt = n_steps > 0 ? s->T / (double)n_steps : 0.0;
+    for (n = 0; n < n_steps; ++n) {
+        orc_pulse_A(s, ((double)n + c1) * dt, a_gauss + 4 * n);
+        orc_pulse_A(s, ((double)n + c2) * dt, a_gauss + 4 * n + 2);
+    }
+    orc_pulse_A(s, 0.0, a_in);
+    orc_pulse_A(s, s->T, a_out);
+    *dt_out = dt;
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Free spinors, Sec. II Eq. (free_spin1..4), divided by sqrt(2E) so |u|=|v|=1 */
 /* ------------------------------------------------------------------------- */
@@ -214,7 +243,8 @@ void orc_spinor_u(double Px, double Py, int valley, cplx u[2])
 {
     double E = sqrt(Px * Px + Py * Py);
     double r = 1.0 / sqrt(2.0);
-    cplx w = (Px + I * Py) / E;
+    /* At P = 0 the spinors are undefined; take the limit P -> (0+, 0). */
+    cplx w = E > 0.0 ? (Px + I * Py) / E : 1.0;
     u[0] = r;
     u[1] = (valley > 0 ? w : -w) * r;
 }
@@ -225,7 +255,7 @@ void orc_spinor_v(double Px, double Py, int valley, cplx v[2])
 {
     double E = sqrt(Px * Px + Py * Py);
     double r = 1.0 / sqrt(2.0);
-    cplx w = (-Px + I * Py) / E;
+    cplx w = E > 0.0 ? (-Px + I * Py) / E : -1.0; /* limit P -> (0+, 0) */
     v[0] = (valley > 0 ? w : -w) * r;
     v[1] = r;
 }
@@ -276,6 +306,56 @@ static void step_matrix(double Px, double Py, double dt, int scheme, int valley,
     }
 }
 
+/* MAGNUS4 step from the kinematic momenta at the two Gauss points. */
+static void step_matrix_magnus4(double P1x, double P1y, double P2x, double P2y, double dt,
+                                int valley, cplx m[4])
+{
+    double sg = valley > 0 ? 1.0 : -1.0;
+    cplx A1[4], A2[4], C[4], W[4];
+    double nx, ny, nz, nn, c, sn;
+    int k;
+    /* A_k = -i valley sigma.P_k = -i valley [[0, Px - i Py], [Px + i Py, 0]] */
+    A1[0] = 0.0;
+    A1[1] = -I * sg * (P1x - I * P1y);
+    A1[2] = -I * sg * (P1x + I * P1y);
+    A1[3] = 0.0;
+    A2[0] = 0.0;
+    A2[1] = -I * sg * (P2x - I * P2y);
+    A2[2] = -I * sg * (P2x + I * P2y);
+    A2[3] = 0.0;
+    /* C = [A1, A2] = A1 A2 - A2 A1 */
+    C[0] = A1[0] * A2[0] + A1[1] * A2[2] - (A2[0] * A1[0] + A2[1] * A1[2]);
+    C[1] = A1[0] * A2[1] + A1[1] * A2[3] - (A2[0] * A1[1] + A2[1] * A1[3]);
+    C[2] = A1[2] * A2[0] + A1[3] * A2[2] - (A2[2] * A1[0] + A2[3] * A1[2]);
+    C[3] = A1[2] * A2[1] + A1[3] * A2[3] - (A2[2] * A1[1] + A2[3] * A1[3]);
+    for (k = 0; k < 4; ++k)
+        W[k] = 0.5 * dt * (A1[k] + A2[k]) - sqrt(3.0) * dt * dt / 12.0 * C[k];
+    /* W = -i (nx sx + ny sy + nz sz): nz = i W00, nx - i ny = i W01 */
+    nz = creal(I * W[0]);
+    nx = creal(I * W[1]);
+    ny = -cimag(I * W[1]);
+    nn = sqrt(nx * nx + ny * ny + nz * nz);
+    c = cos(nn);
+    sn = nn > 0.0 ? sin(nn) / nn : 1.0;
+    /* exp(-i n.sigma) = cos|n| I - i sin|n| (n/|n|).sigma */
+    m[0] = c - I * sn * nz;
+    m[1] = -I * sn * (nx - I * ny);
+    m[2] = -I * sn * (nx + I * ny);
+    m[3] = c + I * sn * nz;
+}
+
+void orc_step_matrix_magnus4(double P1x, double P1y, double P2x, double P2y, double dt, int valley,
+                             double *out8)
+{
+    cplx m[4];
+    int k;
+    step_matrix_magnus4(P1x, P1y, P2x, P2y, dt, valley, m);
+    for (k = 0; k < 4; ++k) {
+        out8[2 * k] = creal(m[k]);
+        out8[2 * k + 1] = cimag(m[k]);
+    }
+}
+
 void orc_step_matrix(double Px, double Py, double dt, int scheme, int valley, double *out8)
 {
     cplx m[4];
@@ -309,9 +389,14 @@ static void solve_point(const solve_args *a, double px, double py, double *cp2, 
     int64_t n;
     orc_spinor_v(px + a->a_in[0], py + a->a_in[1], a->valley, psi);
     for (n = 0; n < a->n_steps; ++n) {
-        double Px = px + a->a_mid[2 * n];
-        double Py = py + a->a_mid[2 * n + 1];
-        step_matrix(Px, Py, a->dt, a->scheme, a->valley, m);
+        if (a->scheme == 2) {
+            const double *g = a->a_mid + 4 * n; /* two Gauss-point samples */
+            step_matrix_magnus4(px + g[0], py + g[1], px + g[2], py + g[3], a->dt, a->valley, m);
+        } else {
+            double Px = px + a->a_mid[2 * n];
+            double Py = py + a->a_mid[2 * n + 1];
+            step_matrix(Px, Py, a->dt, a->scheme, a->valley, m);
+        }
         t0 = m[0] * psi[0] + m[1] * psi[1];
         t1 = m[2] * psi[0] + m[3] * psi[1];
         psi[0] = t0;
@@ -319,7 +404,7 @@ static void solve_point(const solve_args *a, double px, double py, double *cp2, 
     }
     {
         double Px = px + a->a_out[0], Py = py + a->a_out[1];
-        if (sqrt(Px * Px + Py * Py) > 1e-300) {
+        if (sqrt(Px * Px + Py * Py) > 0.0) {
             orc_spinor_u(Px, Py, a->valley, u);
             orc_spinor_v(Px, Py, a->valley, v);
             cp = conj(u[0]) * psi[0] + conj(u[1]) * psi[1];
@@ -348,7 +433,7 @@ static int check_common(const double *a_mid, int64_t n_steps, double dt, int sch
 {
     if (n_steps < 0 || (n_steps > 0 && !a_mid))
         return -1;
-    if (!(dt >= 0.0) || (scheme != 0 && scheme != 1) || (valley != 1 && valley != -1))
+    if (!(dt >= 0.0) || scheme < 0 || scheme > 2 || (valley != 1 && valley != -1))
         return -1;
     return 0;
 }

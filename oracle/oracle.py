@@ -10,6 +10,9 @@ Paper passages each function follows:
                          Sec. II: asymptotic A_in, A_out.
   * ``spinors``       -- Sec. II Eq. (free_spin1..4), normalised to 1.
   * ``step_matrix``   -- Sec. III closed form I cos(dt E) - i sigma.P sin(dt E)/E.
+  * ``step_matrix_magnus4``, ``pulse_table_gauss`` -- the fourth-order Magnus
+                         decomposition (Sec. III: the midpoint rule "can be improved
+                         to higher order by other decompositions").
   * ``solve_points`` / ``solve_grid`` -- Sec. III Eq. (ev_op_dt) product of steps,
                          then the projection of Sec. II Eq. (pair_prod_homo).
   * ``density``       -- Sec. II Eq. (pair_prod_homo) with degeneracy 4.
@@ -35,7 +38,7 @@ _lock = threading.Lock()
 _lib = None
 
 PULSE_KINDS = {"zero": 0, "sin2": 1, "gauss": 2, "two_colour": 3, "const_field": 4, "paper": 5}
-SCHEMES = {"exact": 0, "strang_xy": 1}
+SCHEMES = {"exact": 0, "strang_xy": 1, "magnus4": 2}
 
 
 class _Pulse(ctypes.Structure):
@@ -76,6 +79,11 @@ def _load():
             d, i32, i64, p = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
             lib.orc_pulse_table.argtypes = [ctypes.POINTER(_Pulse), i64, p, p, p, ctypes.POINTER(d)]
             lib.orc_pulse_table.restype = ctypes.c_int
+            lib.orc_pulse_table_gauss.argtypes = [ctypes.POINTER(_Pulse), i64, p, p, p,
+                                                  ctypes.POINTER(d)]
+            lib.orc_pulse_table_gauss.restype = ctypes.c_int
+            lib.orc_step_matrix_magnus4.argtypes = [d, d, d, d, d, ctypes.c_int, p]
+            lib.orc_step_matrix_magnus4.restype = None
             lib.orc_pulse_A.argtypes = [ctypes.POINTER(_Pulse), d, p]
             lib.orc_pulse_A.restype = None
             lib.orc_step_matrix.argtypes = [d, d, d, ctypes.c_int, ctypes.c_int, p]
@@ -135,6 +143,35 @@ def pulse_table(spec: dict, n_steps: int):
     return a_mid, a_in, a_out, dt.value
 
 
+def pulse_table_gauss(spec: dict, n_steps: int):
+    """(a_gauss[n_steps, 4], a_in, a_out, dt): A at the two Gauss points of each
+    step, t_n + (1/2 -/+ sqrt(3)/6) dt, for the fourth-order Magnus scheme."""
+    a = np.zeros((max(n_steps, 0), 4))
+    a_in = np.zeros(2)
+    a_out = np.zeros(2)
+    dt = ctypes.c_double(0.0)
+    s = _pulse_struct(spec)
+    rc = _load().orc_pulse_table_gauss(ctypes.byref(s), int(n_steps), _ptr(a), _ptr(a_in),
+                                       _ptr(a_out), ctypes.byref(dt))
+    if rc != 0:
+        raise ValueError("bad pulse spec")
+    return a, a_in, a_out, dt.value
+
+
+def step_matrix_magnus4(P1, P2, dt: float, valley: int = 1):
+    out = np.zeros(8)
+    _load().orc_step_matrix_magnus4(float(P1[0]), float(P1[1]), float(P2[0]), float(P2[1]),
+                                    float(dt), int(valley), _ptr(out))
+    return (out[0::2] + 1j * out[1::2]).reshape(2, 2)
+
+
+def _table(a_mid, scheme):
+    """Steps of a table: [n, 2] midpoint samples, or [n, 4] Gauss pairs (magnus4)."""
+    w = 4 if scheme == "magnus4" else 2
+    a = np.ascontiguousarray(a_mid, dtype=np.float64).reshape(-1, w)
+    return a, a.shape[0]
+
+
 def step_matrix(Px: float, Py: float, dt: float, scheme: str = "exact", valley: int = 1):
     out = np.zeros(8)
     _load().orc_step_matrix(float(Px), float(Py), float(dt), SCHEMES[scheme], int(valley),
@@ -157,7 +194,7 @@ def solve_points(px, py, a_mid, dt, a_in, a_out, scheme="exact", valley=1, nthre
     """Evolve each point (px[k], py[k]); returns dict of |c+|^2, |c-|^2, |psi|^2 (and psi)."""
     px = np.ascontiguousarray(px, dtype=np.float64).ravel()
     py = np.ascontiguousarray(py, dtype=np.float64).ravel()
-    a_mid = np.ascontiguousarray(a_mid, dtype=np.float64).reshape(-1, 2)
+    a_mid, n_steps = _table(a_mid, scheme)
     a_in = np.ascontiguousarray(a_in, dtype=np.float64)
     a_out = np.ascontiguousarray(a_out, dtype=np.float64)
     n = px.size
@@ -166,7 +203,7 @@ def solve_points(px, py, a_mid, dt, a_in, a_out, scheme="exact", valley=1, nthre
     nr = np.zeros(n)
     psi = np.zeros((n, 4)) if want_psi else None
     rc = _load().orc_solve_points(n, _ptr(px), _ptr(py), SCHEMES[scheme], int(valley),
-                                  _ptr(a_mid), a_mid.shape[0], float(dt), _ptr(a_in),
+                                  _ptr(a_mid), n_steps, float(dt), _ptr(a_in),
                                   _ptr(a_out), _ptr(cp), _ptr(cm), _ptr(nr), _ptr(psi),
                                   int(nthreads))
     if rc != 0:
@@ -185,7 +222,7 @@ def grid_nodes(lo: float, hi: float, n: int) -> np.ndarray:
 def solve_grid(nx, ny, px_range, py_range, a_mid, dt, a_in, a_out, scheme="exact", valley=1,
                nthreads=0):
     """Whole cell-centred grid; returns (cplus2[ny, nx], cminus2, norm2, density)."""
-    a_mid = np.ascontiguousarray(a_mid, dtype=np.float64).reshape(-1, 2)
+    a_mid, n_steps = _table(a_mid, scheme)
     a_in = np.ascontiguousarray(a_in, dtype=np.float64)
     a_out = np.ascontiguousarray(a_out, dtype=np.float64)
     cp = np.zeros((ny, nx))
@@ -194,7 +231,7 @@ def solve_grid(nx, ny, px_range, py_range, a_mid, dt, a_in, a_out, scheme="exact
     dens = ctypes.c_double(0.0)
     rc = _load().orc_solve_grid(int(nx), int(ny), float(px_range[0]), float(px_range[1]),
                                 float(py_range[0]), float(py_range[1]), SCHEMES[scheme],
-                                int(valley), _ptr(a_mid), a_mid.shape[0], float(dt), _ptr(a_in),
+                                int(valley), _ptr(a_mid), n_steps, float(dt), _ptr(a_in),
                                 _ptr(a_out), _ptr(cp), _ptr(cm), _ptr(nr), ctypes.byref(dens),
                                 int(nthreads))
     if rc != 0:

@@ -342,3 +342,73 @@ def test_zero_momentum_point_is_defined(orc):
     a_mid, a_in, a_out, dt = orc.pulse_table(W.zero_pulse(5.0), 100)
     r = orc.solve_points(np.array([0.0]), np.array([0.0]), a_mid, dt, a_in, a_out)
     assert r["cplus2"][0] == 0.0 and abs(r["norm2"][0] - 1) < 1e-15
+
+
+# ----------------------------------------------------------------------------------------
+# Fourth-order Magnus scheme (the higher-order decomposition of Sec. III).
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("valley", [1, -1])
+def test_magnus4_step_equals_expm_of_its_definition(orc, valley):
+    """exp(dt/2 (A1 + A2) - sqrt(3) dt^2/12 [A1, A2]), A_k = -i valley sigma.P_k,
+    built here as matrices and exponentiated by scipy."""
+    rng = np.random.default_rng(21)
+    for _ in range(40):
+        P1 = rng.uniform(-8, 8, size=2)
+        P2 = P1 + rng.uniform(-0.5, 0.5, size=2)
+        dt = rng.uniform(1e-3, 0.1)
+        A1 = -1j * valley * (P1[0] * SX + P1[1] * SY)
+        A2 = -1j * valley * (P2[0] * SX + P2[1] * SY)
+        W_ = 0.5 * dt * (A1 + A2) - math.sqrt(3) * dt * dt / 12 * (A1 @ A2 - A2 @ A1)
+        ref = scipy.linalg.expm(W_)
+        got = orc.step_matrix_magnus4(P1, P2, dt, valley)
+        assert np.abs(got - ref).max() < 2e-14
+
+
+def test_magnus4_gauss_table_points(orc):
+    pulse = W.sin2_pulse(1.0, 1.55, 5.0)
+    a, a_in, a_out, dt = orc.pulse_table_gauss(pulse, 300)
+    c = (0.5 - math.sqrt(3) / 6, 0.5 + math.sqrt(3) / 6)
+    for n in (0, 17, 299):
+        assert np.allclose(a[n, 0:2], orc.pulse_A(pulse, (n + c[0]) * dt), atol=1e-16, rtol=0)
+        assert np.allclose(a[n, 2:4], orc.pulse_A(pulse, (n + c[1]) * dt), atol=1e-16, rtol=0)
+
+
+def test_magnus4_is_fourth_order_and_unitary(orc):
+    """Global error O(dt^4) (slope 4.0 +- 0.3) against a fine reference; the
+    midpoint scheme converges to the same solution at O(dt^2)."""
+    pulse = W.sin2_pulse(1.0, 1.55, 5.0)
+    rng = np.random.default_rng(22)
+    px, py = rng.uniform(-2, 2, size=(2, 12))
+
+    def psi(n, scheme):
+        if scheme == "magnus4":
+            a, a_in, a_out, dt = orc.pulse_table_gauss(pulse, n)
+        else:
+            a, a_in, a_out, dt = orc.pulse_table(pulse, n)
+        r = orc.solve_points(px, py, a, dt, a_in, a_out, scheme=scheme, want_psi=True)
+        assert np.abs(r["norm2"] - 1).max() < 1e-12
+        return r["psi"], dt
+
+    ref, _ = psi(16000, "magnus4")
+    errs, dts = [], []
+    for n in (250, 500, 1000):
+        p_, dt = psi(n, "magnus4")
+        errs.append(np.abs(p_ - ref).max())
+        dts.append(dt)
+    slope = np.polyfit(np.log(dts), np.log(errs), 1)[0]
+    assert abs(slope - 4.0) < 0.3
+    mid, _ = psi(64000, "exact")
+    assert np.abs(mid - ref).max() < 1e-6
+
+
+def test_magnus4_valleys_and_zero_field(orc):
+    a, a_in, a_out, dt = orc.pulse_table_gauss(W.zero_pulse(10.0), 500)
+    cp, _, _, _ = orc.solve_grid(9, 7, (-3, 3), (-2, 2), a, dt, a_in, a_out, scheme="magnus4")
+    assert cp.max() < 1e-28
+    a, a_in, a_out, dt = orc.pulse_table_gauss(W.sin2_pulse(1.5, 1.2, 4.0, eps=0.4), 800)
+    rng = np.random.default_rng(23)
+    px, py = rng.uniform(-3, 3, size=(2, 40))
+    kp = orc.solve_points(px, py, a, dt, a_in, a_out, scheme="magnus4", valley=1)
+    km = orc.solve_points(px, py, a, dt, a_in, a_out, scheme="magnus4", valley=-1)
+    assert np.abs(kp["cplus2"] - km["cplus2"]).max() < 1e-12
