@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--serving-load", type=float, default=0.8,
                     help="offered load as a fraction of the measured solve throughput")
     ap.add_argument("--serving-chunk", type=int, default=2000)
+    ap.add_argument("--no-small-grid", action="store_true", help="skip the 64x64 latency leg")
+    ap.add_argument("--no-magnus4", action="store_true", help="skip the fourth-order leg")
     return ap.parse_args()
 
 
@@ -133,7 +135,7 @@ class ClockSampler:
 # SHA-256 of the kernel source the counters were taken on; a different source
 # means the counters are stale and the traffic is reported as null.
 KERNEL_TRAFFIC = {
-    "evolve_mixed_kernel": {"bytes": 90.39e6, "source_sha256": "20baa4b392a40c84484c4950a5abef528a793333ec0a148577b8fb72b35e7c7a",
+    "evolve_mixed_kernel": {"bytes": 90.98e6, "source_sha256": "ada8cc2fdf5c767ae38d81b10519efdcbfc43b213e1e97fee44209421a7661b8",
                             "profile": "profiles/evolve_kernels_lzs2048_2000steps_full.md"},
 }
 
@@ -309,6 +311,16 @@ def run_gpu(args):
            "d2h_bytes_per_step": 4 * n * n + 16,
            "note": "dsp_solve_host: host midpoint table in, host |c+|^2 map and density out"}
 
+    # ---- fourth-order Magnus scheme on the same workload ----
+    magnus = None
+    if not args.no_magnus4:
+        magnus = magnus4_leg(args, cfgs, st_ptr, world, rank)
+
+    # ---- small grid: sequential vs time-parallel solve latency ----
+    small = None
+    if not args.no_small_grid and rank == 0:
+        small = small_grid_leg(st_ptr)
+
     # ---- serving: continuous batching vs one request at a time ----
     serving = None
     if not args.no_serving and rank == 0:
@@ -358,7 +370,8 @@ def run_gpu(args):
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world} (independent samples per rank)"},
         "density_first_step": d_mixed[0] if d_mixed else None,
-        "fp64": fp64, "e2e": e2e, "serving": serving, "gpu_launches": 2 * args.steps,
+        "fp64": fp64, "e2e": e2e, "magnus4": magnus, "serving": serving, "small_grid": small,
+        "gpu_launches": 2 * args.steps,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
     }
@@ -366,6 +379,94 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------
+# Fourth-order Magnus leg
+# ------------------------------------------------------------------------------------------
+
+def magnus4_leg(args, cfgs, stream, world, rank, warm=1, reps=2):
+    """The same 2048^2 x 1e5-step solves with the fourth-order Magnus step
+    (two Gauss-point samples per step), FP32-mixed.  Its instructions per
+    spinor-step: 6 (Pbar) + 2 (n_z) + 3 (|n|^2) + dc + ds + 3 (q, q_z) + 16
+    ((U - I) psi + lo) + 12 (Fast2Sum) = 42 + dc + ds."""
+    import torch
+
+    from paper_1607_03062_gb300 import binding as B
+
+    n = args.grid
+    g0 = cfgs[0]["grid"]
+    nbytes = B.state_bytes(n, n, "fp32_mixed")
+    state = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    mp = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    h = B.create_grid(n, n, g0["px"], g0["py"], "fp32_mixed", "magnus4", 1, stream,
+                      state.data_ptr(), nbytes)
+    times, ops = [], []
+    for k in range(warm + reps):
+        c = cfgs[(k * world + rank) % len(cfgs)]
+        a, a_in, a_out, dt = B.sample_pulse_gauss(c["pulse"], args.time_steps)
+        B.set_pulse(h, a, dt, a_in, a_out)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.solve(h, mp.data_ptr(), want_density=False)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= warm:
+            times.append(e0.elapsed_time(e1) / 1e3)
+            info = B.get_info(h)
+            ops.append(42 + info["cos_degree"] + info["sinc_degree"])
+    B.destroy_grid(h)
+    work = float(n) * n * args.time_steps
+    achieved = statistics.mean(o * work / t for o, t in zip(ops, times)) / 1e12
+    peak = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    return {"value": work * reps / sum(times), "unit": METRIC, "ms_per_step": 1e3 * statistics.mean(times),
+            "steps": reps, "warmup": warm, "scheme": "magnus4 (fourth order, 2 Gauss points/step)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                         "unit": "Tinst/s (FP32 lane instructions)", "ops_per_spinor_step": ops}}
+
+
+# ------------------------------------------------------------------------------------------
+# Small-grid leg
+# ------------------------------------------------------------------------------------------
+
+def small_grid_leg(stream, reps=5, warm=3):
+    """64x64 on [-4,4]^2, 5-cycle sin^2 pulse, 2000 steps: four 1024-point tiles,
+    far too few to fill the GPU.  Latency of one solve, sequential (dsp_solve) vs
+    time-parallel (dsp_solve_segmented, automatic segment count), CUDA events."""
+    import torch
+
+    from paper_1607_03062_gb300 import binding as B
+
+    cfg = W.config_sin2_64()
+    g = cfg["grid"]
+    a_mid, a_in, a_out, dt = B.sample_pulse(cfg["pulse"], cfg["steps"])
+    out = {"workload": "sin2_64x64_2000_steps", "spinor_steps": 64 * 64 * cfg["steps"]}
+    for prec in ("fp64", "fp32_mixed"):
+        grid = B.Grid(g["nx"], g["ny"], g["px"], g["py"], prec)
+        res = {}
+        for mode in ("sequential", "segmented"):
+            times = []
+            for k in range(warm + reps):
+                grid.set_pulse(a_mid, dt, a_in, a_out)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                if mode == "sequential":
+                    B.solve(grid.h, grid.map.data_ptr(), want_density=False)
+                else:
+                    B.solve_segmented(grid.h, 0, grid.map.data_ptr(), want_density=False)
+                e1.record()
+                torch.cuda.synchronize()
+                if k >= warm:
+                    times.append(e0.elapsed_time(e1))
+            res[mode + "_ms"] = statistics.median(times)
+        res["speedup"] = res["sequential_ms"] / res["segmented_ms"]
+        out[prec] = res
+        grid.close()
+    return out
 
 
 # ------------------------------------------------------------------------------------------

@@ -60,6 +60,12 @@ typedef int32_t dsp_status;
 #define DSP_SCHEME_EXACT 0     /* the paper's closed-form exponential (Sec. III)    */
 #define DSP_SCHEME_STRANG_XY 1 /* e^{-i dt Px sx/2} e^{-i dt Py sy} e^{-i dt Px sx/2},
                                   a sigma_x / sigma_y split (not in the paper)      */
+#define DSP_SCHEME_MAGNUS4 2   /* fourth-order Magnus with two Gauss points per step,
+                                  exp(dt/2 (A1 + A2) - sqrt(3) dt^2/12 [A1, A2]),
+                                  A_k = -i valley sigma.P(t_n + (1/2 -/+ sqrt(3)/6) dt):
+                                  the higher-order decomposition Sec. III mentions.
+                                  Its pulse tables hold TWO samples per step (the
+                                  Gauss points): [n_steps][2][2]                    */
 
 typedef struct dsp_grid dsp_grid;
 
@@ -82,7 +88,10 @@ dsp_status dsp_create_grid(int32_t nx, int32_t ny, double px_min, double px_max,
                            dsp_grid **out);
 
 /* Sets the pulse: a_mid is a host array [n_steps][2] of (A_x, A_y) sampled at
- * the step midpoints t_i + (n + 1/2) dt (Sec. III, Eq. (approx_time)); a_in and
+ * the step midpoints t_i + (n + 1/2) dt (Sec. III, Eq. (approx_time)) -- for
+ * DSP_SCHEME_MAGNUS4 it is [n_steps][2][2], (A_x, A_y) at t_i + (n + 1/2 -
+ * sqrt(3)/6) dt then at t_i + (n + 1/2 + sqrt(3)/6) dt (dsp_sample_pulse_gauss
+ * fills it); the same holds for dsp_solve_host and dsp_server_submit; a_in and
  * a_out are the asymptotic potentials A^in, A^out of Sec. II (host, 2 doubles
  * each).  All values finite, dt > 0 (dt >= 0 when n_steps == 0), n_steps >= 0.
  * Copies and converts the table to the device, resets the state to
@@ -145,6 +154,20 @@ dsp_status dsp_density_noalloc(const void *map_dev, int32_t precision, int32_t n
  * internal map is used) and the density to *n_host (may be NULL).
  * Synchronises when n_host is not NULL. */
 dsp_status dsp_solve(dsp_grid *g, void *map_dev, double *n_host);
+
+/* The whole hot path with the time axis split into `segments` pieces that run
+ * in parallel (for grids too small to fill the GPU).  The evolution operator
+ * is the time-ordered product of the step operators (Sec. III, Eq. (ev_op_dt));
+ * the product is associative, so each segment's product is formed on its own
+ * (as its first column: every step operator is SU(2), [[a, -conj(b)], [b,
+ * conj(a)]], so the column (a, b) determines it), then the segments are
+ * multiplied onto v(p + A_in) in time order in FP64.  Same steps, same results
+ * as dsp_solve up to rounding (not bitwise).  segments = 0 picks enough to put
+ * two CTAs on every SM (at least 16 steps per segment); needs cursor == 0
+ * (DSP_E_STATE otherwise).  Scratch: segments * 32 bytes per point, allocated
+ * by the library (at most 16 GB, else DSP_E_INVALID).  map_dev and n_host as
+ * in dsp_solve. */
+dsp_status dsp_solve_segmented(dsp_grid *g, int32_t segments, void *map_dev, double *n_host);
 
 /* End to end with host buffers: copies the host pulse table in (as
  * dsp_set_pulse), runs dsp_solve, and copies the |c+|^2 map (double or float
@@ -215,6 +238,11 @@ typedef struct {
 dsp_status dsp_sample_pulse(const dsp_pulse_spec *spec, int64_t n_steps, double *a_mid,
                             double *a_in, double *a_out, double *dt_out);
 
+/* The same for DSP_SCHEME_MAGNUS4: a_gauss host [n_steps][2][2], A at
+ * (n + 1/2 - sqrt(3)/6) dt and (n + 1/2 + sqrt(3)/6) dt. */
+dsp_status dsp_sample_pulse_gauss(const dsp_pulse_spec *spec, int64_t n_steps, double *a_gauss,
+                                  double *a_in, double *a_out, double *dt_out);
+
 /* ------------------------------------------------------------------------- */
 /* Serving: a continuous-batching request loop (not in the paper).  Requests
  * (each a whole solve) are queued on submit and admitted FIFO while the device
@@ -256,9 +284,14 @@ dsp_status dsp_server_create(int64_t hbm_budget_bytes, int32_t max_active, int64
 dsp_status dsp_server_submit(dsp_server *s, const dsp_request *req, const double *a_mid,
                              int64_t *id);
 
-/* One scheduling iteration (see above).  Synchronises.  Outputs may be NULL:
- * number active after the iteration, number still queued, number that
- * finished in this iteration. */
+/* One scheduling iteration, pipelined: admits what fits, queues one batched
+ * launch that advances every admitted request by up to chunk_steps (with the
+ * projection, density and result copies of those whose last steps are in it),
+ * then waits only for the PREVIOUS iteration and retires the requests that
+ * finished there (so the device always has the next iteration queued).  Device
+ * memory comes from the stream-ordered pool; nothing blocks on an allocation.
+ * Outputs may be NULL: requests admitted and not yet retired, requests still
+ * queued, requests retired by this call. */
 dsp_status dsp_server_step(dsp_server *s, int32_t *n_active, int32_t *n_queued,
                            int32_t *n_finished);
 

@@ -24,7 +24,7 @@ _lib = None
 FP64 = 0
 FP32_MIXED = 1
 PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED}
-SCHEMES = {"exact": 0, "strang_xy": 1}
+SCHEMES = {"exact": 0, "strang_xy": 1, "magnus4": 2}
 PULSE_KINDS = {"zero": 0, "sin2": 1, "gauss": 2, "two_colour": 3, "const_field": 4, "paper": 5}
 REQ_STATES = {0: "queued", 1: "active", 2: "done", 3: "failed", 4: "cancelled"}
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory or over budget", -3: "CUDA error",
@@ -38,7 +38,7 @@ EXPORTS = (
     "dsp_save_state", "dsp_load_state", "dsp_destroy_grid", "dsp_status_string",
     "dsp_sample_pulse", "dsp_server_create", "dsp_server_submit", "dsp_server_step",
     "dsp_server_query", "dsp_server_cancel", "dsp_server_destroy", "dsp_density_noalloc",
-    "dsp_get_info",
+    "dsp_get_info", "dsp_solve_segmented", "dsp_sample_pulse_gauss",
 )
 
 
@@ -114,6 +114,8 @@ def lib() -> ctypes.CDLL:
                 "dsp_server_destroy": (i32, [p]),
                 "dsp_density_noalloc": (i32, [p, i32, i32, i32, d, d, d, d, p, pd]),
                 "dsp_get_info": (i32, [p, ctypes.POINTER(GridInfo)]),
+                "dsp_solve_segmented": (i32, [p, i32, p, pd]),
+                "dsp_sample_pulse_gauss": (i32, [ctypes.POINTER(PulseSpec), i64, p, p, p, pd]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -160,10 +162,20 @@ def create_grid(nx, ny, px_range, py_range, precision="fp32_mixed", scheme="exac
     return h.value
 
 
+def _steps(a_mid):
+    """A table and its step count: [n, 2] midpoint samples or [n, 4] Gauss pairs."""
+    a = _f64(a_mid)
+    w = a.shape[-1] if a.ndim == 2 else 2
+    if w not in (2, 4):
+        raise ValueError("pulse table must be [n, 2] (midpoints) or [n, 4] (Gauss pairs)")
+    a = a.reshape(-1, w)
+    return a, a.shape[0]
+
+
 def set_pulse(h: int, a_mid, dt: float, a_in, a_out):
-    a = _f64(a_mid).reshape(-1, 2)
+    a, n = _steps(a_mid)
     ai, ao = _f64(a_in), _f64(a_out)
-    _check(lib().dsp_set_pulse(ctypes.c_void_p(h), _ptr(a), a.shape[0], float(dt), _ptr(ai),
+    _check(lib().dsp_set_pulse(ctypes.c_void_p(h), _ptr(a), n, float(dt), _ptr(ai),
                                _ptr(ao)), "set_pulse")
 
 
@@ -189,12 +201,21 @@ def solve(h: int, map_ptr: int = 0, want_density: bool = True):
     return n.value if want_density else None
 
 
+def solve_segmented(h: int, segments: int = 0, map_ptr: int = 0, want_density: bool = True):
+    """Whole solve with the time axis split into segments run in parallel."""
+    n = ctypes.c_double()
+    rc = lib().dsp_solve_segmented(ctypes.c_void_p(h), int(segments), ctypes.c_void_p(int(map_ptr)),
+                                   ctypes.byref(n) if want_density else None)
+    _check(rc, "solve_segmented")
+    return n.value if want_density else None
+
+
 def solve_host(h: int, a_mid, dt: float, a_in, a_out, map_out: np.ndarray | None) -> float:
-    a = _f64(a_mid).reshape(-1, 2)
+    a, steps = _steps(a_mid)
     ai, ao = _f64(a_in), _f64(a_out)
     n = ctypes.c_double()
     mp = None if map_out is None else _ptr(map_out)
-    _check(lib().dsp_solve_host(ctypes.c_void_p(h), _ptr(a), a.shape[0], float(dt), _ptr(ai),
+    _check(lib().dsp_solve_host(ctypes.c_void_p(h), _ptr(a), steps, float(dt), _ptr(ai),
                                 _ptr(ao), mp, ctypes.byref(n)), "solve_host")
     return n.value
 
@@ -276,6 +297,18 @@ def sample_pulse(spec: dict, n_steps: int):
     return a_mid, a_in, a_out, dt.value
 
 
+def sample_pulse_gauss(spec: dict, n_steps: int):
+    """(a_gauss[n_steps, 4], a_in[2], a_out[2], dt): A at the two Gauss points of
+    each step, for the fourth-order Magnus scheme."""
+    a = np.zeros((int(n_steps), 4))
+    a_in, a_out = np.zeros(2), np.zeros(2)
+    dt = ctypes.c_double()
+    s = pulse_spec(spec)
+    _check(lib().dsp_sample_pulse_gauss(ctypes.byref(s), int(n_steps), _ptr(a), _ptr(a_in),
+                                        _ptr(a_out), ctypes.byref(dt)), "sample_pulse_gauss")
+    return a, a_in, a_out, dt.value
+
+
 # ------------------------------------------------------------------------------------------
 # Server
 # ------------------------------------------------------------------------------------------
@@ -305,7 +338,7 @@ def make_request(grid: dict, n_steps: int, dt: float, a_in, a_out, precision="fp
 
 
 def server_submit(s: int, req: Request, a_mid) -> int:
-    a = _f64(a_mid).reshape(-1, 2)
+    a, _ = _steps(a_mid)
     rid = ctypes.c_int64()
     _check(lib().dsp_server_submit(ctypes.c_void_p(s), ctypes.byref(req), _ptr(a),
                                    ctypes.byref(rid)), "server_submit")
@@ -373,6 +406,10 @@ class Grid:
 
     def solve(self):
         n = solve(self.h, self.map.data_ptr())
+        return self.map, n
+
+    def solve_segmented(self, segments=0):
+        n = solve_segmented(self.h, segments, self.map.data_ptr())
         return self.map, n
 
     def close(self):

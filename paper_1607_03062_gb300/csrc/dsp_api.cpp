@@ -50,6 +50,8 @@ struct dsp_grid {
     double *partials = nullptr;
     DeviceScalars *scal = nullptr;
     void *own_map = nullptr;  // used by dsp_solve when the caller passes no map
+    void *seg_buf = nullptr;  // time-segment columns for dsp_solve_segmented
+    size_t seg_cap = 0;
 
     bool has_pulse = false;
     int64_t n_steps = 0, cursor = 0;
@@ -271,7 +273,8 @@ dsp_status validate_grid_args(int32_t nx, int32_t ny, double px_min, double px_m
         return DSP_E_INVALID;
     if (precision != DSP_FP64 && precision != DSP_FP32_MIXED)
         return DSP_E_INVALID;
-    if (scheme != DSP_SCHEME_EXACT && scheme != DSP_SCHEME_STRANG_XY)
+    if (scheme != DSP_SCHEME_EXACT && scheme != DSP_SCHEME_STRANG_XY &&
+        scheme != DSP_SCHEME_MAGNUS4)
         return DSP_E_INVALID;
     if (valley != 1 && valley != -1)
         return DSP_E_INVALID;
@@ -295,13 +298,51 @@ dsp_status validate_pulse_args(const dsp_grid *g, const double *a_mid, int64_t n
     return DSP_OK;
 }
 
+// A(t) samples per step in the caller's table: one (A_x, A_y) at the midpoint,
+// or two (at the Gauss points) for MAGNUS4.
+int samples_per_step(int32_t scheme) { return scheme == DSP_SCHEME_MAGNUS4 ? 2 : 1; }
+
+// Bytes per step of the device table.
+size_t entry_bytes(int32_t scheme) { return 16 * static_cast<size_t>(samples_per_step(scheme)); }
+
 // Fills the table layout the kernels read (see ReqDesc::table).
 void build_table(const dsp_grid *g, const double *a_mid, int64_t n, double dt, double quant,
                  double inv_quant, std::vector<unsigned char> &out)
 {
-    out.resize(static_cast<size_t>(n) * 16);
+    out.resize(static_cast<size_t>(n) * entry_bytes(g->scheme));
     // valley K- is stepped as K+ on -P, so its table holds -dt*A
     const double vs = g->valley > 0 ? 1.0 : -1.0;
+    if (g->scheme == DSP_SCHEME_MAGNUS4) {
+        // (Abar, D): Abar = (A1 + A2)/2, D = -(sqrt(3)/6) (A2 - A1), both times s*dt
+        const double kappa = -std::sqrt(3.0) / 6.0;
+        for (int64_t k = 0; k < n; ++k) {
+            const double *a = a_mid + 4 * k;
+            const double bx = vs * (dt * (0.5 * (a[0] + a[2])));
+            const double by = vs * (dt * (0.5 * (a[1] + a[3])));
+            const double dx = kappa * (vs * (dt * (a[2] - a[0])));
+            const double dy = kappa * (vs * (dt * (a[3] - a[1])));
+            if (g->precision == DSP_FP64) {
+                double *t = reinterpret_cast<double *>(out.data()) + 4 * k;
+                t[0] = bx;
+                t[1] = by;
+                t[2] = dx;
+                t[3] = dy;
+            } else {
+                float *t = reinterpret_cast<float *>(out.data()) + 8 * k;
+                const double hx = std::rint(bx * quant) * inv_quant;
+                const double hy = std::rint(by * quant) * inv_quant;
+                t[0] = static_cast<float>(hx);
+                t[1] = static_cast<float>(bx - hx);
+                t[2] = static_cast<float>(hy);
+                t[3] = static_cast<float>(by - hy);
+                t[4] = static_cast<float>(dx);
+                t[5] = static_cast<float>(dy);
+                t[6] = 0.0f;
+                t[7] = 0.0f;
+            }
+        }
+        return;
+    }
     if (g->precision == DSP_FP64) {
         double *t = reinterpret_cast<double *>(out.data());
         for (int64_t k = 0; k < n; ++k) {
@@ -333,9 +374,34 @@ void free_grid_memory(dsp_grid *g)
         cudaFree(g->scal);
     if (g->own_map)
         cudaFree(g->own_map);
+    if (g->seg_buf)
+        cudaFree(g->seg_buf);
+    g->seg_buf = nullptr;
+    g->seg_cap = 0;
     g->state = g->table = g->own_map = nullptr;
     g->partials = nullptr;
     g->scal = nullptr;
+}
+
+// Geometry and arithmetic fields of a grid (no allocation).
+void fill_grid(dsp_grid *g, int32_t nx, int32_t ny, double px_min, double px_max, double py_min,
+               double py_max, int32_t precision, int32_t scheme, int32_t valley,
+               cudaStream_t stream)
+{
+    g->nx = nx;
+    g->ny = ny;
+    g->precision = precision;
+    g->scheme = scheme;
+    g->valley = valley;
+    g->px_min = px_min;
+    g->px_max = px_max;
+    g->py_min = py_min;
+    g->py_max = py_max;
+    g->hx = (px_max - px_min) / nx;
+    g->hy = (py_max - py_min) / ny;
+    g->n_points = static_cast<int64_t>(nx) * ny;
+    g->n_tiles = static_cast<int32_t>((g->n_points + dsp::kTilePoints - 1) / dsp::kTilePoints);
+    g->stream = stream;
 }
 
 dsp_status create_grid_impl(int32_t nx, int32_t ny, double px_min, double px_max, double py_min,
@@ -356,20 +422,7 @@ dsp_status create_grid_impl(int32_t nx, int32_t ny, double px_min, double px_max
     dsp_grid *g = new (std::nothrow) dsp_grid();
     if (!g)
         return DSP_E_NOMEM;
-    g->nx = nx;
-    g->ny = ny;
-    g->precision = precision;
-    g->scheme = scheme;
-    g->valley = valley;
-    g->px_min = px_min;
-    g->px_max = px_max;
-    g->py_min = py_min;
-    g->py_max = py_max;
-    g->hx = (px_max - px_min) / nx;
-    g->hy = (py_max - py_min) / ny;
-    g->n_points = static_cast<int64_t>(nx) * ny;
-    g->n_tiles = static_cast<int32_t>((g->n_points + dsp::kTilePoints - 1) / dsp::kTilePoints);
-    g->stream = stream;
+    fill_grid(g, nx, ny, px_min, px_max, py_min, py_max, precision, scheme, valley, stream);
     cudaError_t e = cudaSuccess;
     if (state_dev) {
         g->state = state_dev;
@@ -393,38 +446,20 @@ dsp_status create_grid_impl(int32_t nx, int32_t ny, double px_min, double px_max
     return DSP_OK;
 }
 
-dsp_status set_pulse_impl(dsp_grid *g, const double *a_mid, int64_t n_steps, double dt,
-                          const double a_in[2], const double a_out[2])
+// Host part of setting a pulse: validates, fills the grid's pulse fields and
+// lays out the device table in `host` (n_steps * 16 bytes).  Nothing is queued.
+dsp_status prepare_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, double dt,
+                         const double a_in[2], const double a_out[2],
+                         std::vector<unsigned char> &host)
 {
-    dsp_status s = validate_pulse_args(g, a_mid, n_steps, dt, a_in, a_out);
+    // every (A_x, A_y) sample of the table, whatever the samples per step
+    const int64_t n_samples = n_steps * samples_per_step(g->scheme);
+    dsp_status s = validate_pulse_args(g, a_mid, n_samples, dt, a_in, a_out);
     if (s != DSP_OK)
         return s;
-    const double tmax = n_steps > 0 ? theta_max(g, a_mid, n_steps, dt) : 0.0;
-    const double quant = n_steps > 0 ? choose_quant(g, a_mid, n_steps, dt) : 1.0;
-    std::vector<unsigned char> host;
+    const double tmax = n_steps > 0 ? theta_max(g, a_mid, n_samples, dt) : 0.0;
+    const double quant = n_steps > 0 ? choose_quant(g, a_mid, n_samples, dt) : 1.0;
     build_table(g, a_mid, n_steps, dt, quant, 1.0 / quant, host);
-    cudaError_t e = cudaSuccess;
-    if (n_steps > g->table_cap) {
-        if (g->table) {
-            e = cudaStreamSynchronize(g->stream);  // old table may still be read
-            if (e == cudaSuccess)
-                e = cudaFree(g->table);
-            g->table = nullptr;
-            g->table_cap = 0;
-        }
-        if (e == cudaSuccess)
-            e = cudaMalloc(&g->table, static_cast<size_t>(n_steps) * 16);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return e == cudaErrorMemoryAllocation ? DSP_E_NOMEM : latch_cuda(g, e);
-        }
-        g->table_cap = n_steps;
-    }
-    if (n_steps > 0) {
-        e = cudaMemcpyAsync(g->table, host.data(), host.size(), cudaMemcpyHostToDevice, g->stream);
-        if (e != cudaSuccess)
-            return latch_cuda(g, e);
-    }
     g->has_pulse = true;
     g->n_steps = n_steps;
     g->cursor = 0;
@@ -439,6 +474,42 @@ dsp_status set_pulse_impl(dsp_grid *g, const double *a_mid, int64_t n_steps, dou
     g->level = choose_level(g->precision, tmax, n_steps);
     g->fresh = true;
     g->projected = false;
+    return DSP_OK;
+}
+
+dsp_status set_pulse_impl(dsp_grid *g, const double *a_mid, int64_t n_steps, double dt,
+                          const double a_in[2], const double a_out[2])
+{
+    dsp_grid staged = *g;
+    std::vector<unsigned char> host;
+    dsp_status s = prepare_pulse(&staged, a_mid, n_steps, dt, a_in, a_out, host);
+    if (s != DSP_OK)
+        return s;
+    cudaError_t e = cudaSuccess;
+    if (n_steps > g->table_cap) {
+        if (g->table) {
+            e = cudaStreamSynchronize(g->stream);  // old table may still be read
+            if (e == cudaSuccess)
+                e = cudaFree(g->table);
+            g->table = nullptr;
+            g->table_cap = 0;
+        }
+        if (e == cudaSuccess)
+            e = cudaMalloc(&g->table, static_cast<size_t>(n_steps) * entry_bytes(g->scheme));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? DSP_E_NOMEM : latch_cuda(g, e);
+        }
+        g->table_cap = n_steps;
+    }
+    if (n_steps > 0) {
+        e = cudaMemcpyAsync(g->table, host.data(), host.size(), cudaMemcpyHostToDevice, g->stream);
+        if (e != cudaSuccess)
+            return latch_cuda(g, e);
+    }
+    staged.table = g->table;
+    staged.table_cap = g->table_cap;
+    *g = staged;
     return DSP_OK;
 }
 
@@ -567,6 +638,107 @@ dsp_status dsp_solve(dsp_grid *g, void *map_dev, double *n_host)
         return s;
     std::vector<dsp::FinDesc> f(1, fin_desc(g));
     cudaError_t e = launch_finalizes(f, g->stream);
+    if (e != cudaSuccess)
+        return latch_cuda(g, e);
+    if (n_host)
+        return read_scalars(g, n_host);
+    return DSP_OK;
+}
+
+dsp_status dsp_solve_segmented(dsp_grid *g, int32_t segments, void *map_dev, double *n_host)
+{
+    dsp_status s = check_usable(g);
+    if (s != DSP_OK)
+        return s;
+    if (segments < 0)
+        return DSP_E_INVALID;
+    if (!g->has_pulse || g->cursor != 0)
+        return DSP_E_STATE;
+    if (g->n_steps == 0)
+        return dsp_solve(g, map_dev, n_host);
+    int64_t S = segments;
+    if (S == 0) {  // enough CTAs for two of them on every SM, >= 16 steps a segment
+        static int sms = 0;
+        if (sms == 0) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                cudaGetLastError();
+                sms = 152;
+            }
+        }
+        S = (2 * static_cast<int64_t>(sms) + g->n_tiles - 1) / g->n_tiles;
+        S = std::min<int64_t>(S, g->n_steps / 16);
+    }
+    S = std::max<int64_t>(1, std::min<int64_t>(S, g->n_steps));
+    const size_t slab = 32 * static_cast<size_t>(g->n_points);
+    if (S > 65536 || static_cast<double>(S) * static_cast<double>(slab) > 16.0e9)
+        return DSP_E_INVALID;  // segment columns above 16 GB
+    const size_t need = static_cast<size_t>(S) * slab;
+    cudaError_t e = cudaSuccess;
+    if (need > g->seg_cap) {
+        if (g->seg_buf) {
+            e = cudaStreamSynchronize(g->stream);
+            if (e == cudaSuccess)
+                e = cudaFree(g->seg_buf);
+            g->seg_buf = nullptr;
+            g->seg_cap = 0;
+        }
+        if (e == cudaSuccess)
+            e = cudaMalloc(&g->seg_buf, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            g->seg_buf = nullptr;
+            return e == cudaErrorMemoryAllocation ? DSP_E_NOMEM : latch_cuda(g, e);
+        }
+        g->seg_cap = need;
+    }
+    if (!map_dev) {
+        s = ensure_own_map(g);
+        if (s != DSP_OK)
+            return s;
+        map_dev = g->own_map;
+    }
+    // 1. every segment's operator product, as its first column, in one batched pass
+    std::vector<ReqDesc> descs;
+    descs.reserve(static_cast<size_t>(S));
+    for (int64_t k = 0; k < S; ++k) {
+        const int64_t b = k * g->n_steps / S, e_ = (k + 1) * g->n_steps / S;
+        ReqDesc d = make_desc(g, b, e_, false, nullptr);
+        d.state = static_cast<unsigned char *>(g->seg_buf) + static_cast<size_t>(k) * slab;
+        d.fresh = 1;
+        d.init_identity = 1;
+        descs.push_back(d);
+    }
+    e = launch_requests(descs, g->precision, &g->scal->err, g->stream);
+    // 2. psi = M_{S-1} ... M_0 v(p + A_in)
+    if (e == cudaSuccess) {
+        dsp::CombineArgs c;
+        std::memset(&c, 0, sizeof(c));
+        c.segs = g->seg_buf;
+        c.state = g->state;
+        c.n_points = g->n_points;
+        c.n_segments = static_cast<int32_t>(S);
+        c.nx = g->nx;
+        c.px_min = g->px_min;
+        c.py_min = g->py_min;
+        c.hx = g->hx;
+        c.hy = g->hy;
+        c.a_in[0] = g->a_in[0];
+        c.a_in[1] = g->a_in[1];
+        c.valley = g->valley;
+        e = dsp::launch_combine(c, g->precision, g->stream);
+    }
+    if (e != cudaSuccess)
+        return latch_cuda(g, e);
+    g->fresh = false;
+    g->cursor = g->n_steps;
+    // 3. projection + tile sums (a zero-step launch), then the density
+    s = run_one(g, g->n_steps, true, map_dev);
+    if (s != DSP_OK)
+        return s;
+    std::vector<dsp::FinDesc> f(1, fin_desc(g));
+    e = launch_finalizes(f, g->stream);
     if (e != cudaSuccess)
         return latch_cuda(g, e);
     if (n_host)
@@ -876,6 +1048,24 @@ bool spec_ok(const dsp_pulse_spec &s)
 
 }  // namespace
 
+extern "C" dsp_status dsp_sample_pulse_gauss(const dsp_pulse_spec *spec, int64_t n_steps,
+                                             double *a_gauss, double *a_in, double *a_out,
+                                             double *dt_out)
+{
+    if (!spec || n_steps < 1 || !a_gauss || !a_in || !a_out || !dt_out || !spec_ok(*spec))
+        return DSP_E_INVALID;
+    const double dt = spec->T / static_cast<double>(n_steps);
+    const double c1 = 0.5 - std::sqrt(3.0) / 6.0, c2 = 0.5 + std::sqrt(3.0) / 6.0;
+    for (int64_t n = 0; n < n_steps; ++n) {
+        pulse_at(*spec, (static_cast<double>(n) + c1) * dt, a_gauss + 4 * n);
+        pulse_at(*spec, (static_cast<double>(n) + c2) * dt, a_gauss + 4 * n + 2);
+    }
+    pulse_at(*spec, 0.0, a_in);
+    pulse_at(*spec, spec->T, a_out);
+    *dt_out = dt;
+    return DSP_OK;
+}
+
 extern "C" dsp_status dsp_sample_pulse(const dsp_pulse_spec *spec, int64_t n_steps,
                                        double *a_mid, double *a_in, double *a_out,
                                        double *dt_out)
@@ -893,6 +1083,17 @@ extern "C" dsp_status dsp_sample_pulse(const dsp_pulse_spec *spec, int64_t n_ste
 
 // ===========================================================================
 // Continuous-batching server
+//
+// Pipelined: dsp_server_step queues iteration k (admissions, one batched
+// launch over every admitted request, the finalize of the requests whose last
+// steps are in it, and the copies of their results to pinned host memory),
+// records an event, and only then waits for iteration k-1's event to retire
+// the requests that finished there.  The GPU therefore always has the next
+// iteration queued while the host does its bookkeeping.  Which requests finish
+// in an iteration is known on the host from the step counts, so no read-back
+// is needed to plan the next one.  Device memory comes from the stream-ordered
+// pool (cudaMallocAsync / cudaFreeAsync on the server stream), table uploads go
+// through pinned staging on a side stream, so no step blocks on an allocation.
 // ===========================================================================
 
 namespace {
@@ -902,20 +1103,28 @@ struct ServerReq {
     dsp_request p{};
     std::vector<double> a_mid;
     int32_t state = DSP_REQ_QUEUED;
-    dsp_grid *g = nullptr;
+    dsp_grid g{};             // pointers borrowed from `block`
+    void *block = nullptr;    // one pool allocation: state | table | partials | scalars | map
     void *map_dev = nullptr;
     int64_t footprint = 0;
-    std::vector<unsigned char> map_host;
+    int64_t finish_iter = -1;  // iteration whose launch holds the last steps
+    bool cancel_pending = false;
+    int32_t slot = -1;                   // index into the server's pinned result slots
+    void *map_host = nullptr;            // pinned, when keep_map
     double density = 0.0;
-    bool finishing = false;
 };
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 int64_t footprint_of(const dsp_request &p)
 {
     const int64_t pts = static_cast<int64_t>(p.nx) * p.ny;
     const int64_t tiles = (pts + dsp::kTilePoints - 1) / dsp::kTilePoints;
-    return 32 * pts + 16 * p.n_steps + static_cast<int64_t>(map_elem_bytes(p.precision)) * pts +
-           8 * tiles + static_cast<int64_t>(sizeof(DeviceScalars));
+    return static_cast<int64_t>(align256(32 * static_cast<size_t>(pts)) +
+                                align256(entry_bytes(p.scheme) * static_cast<size_t>(p.n_steps)) +
+                                align256(8 * static_cast<size_t>(tiles)) +
+                                align256(sizeof(DeviceScalars)) +
+                                align256(map_elem_bytes(p.precision) * static_cast<size_t>(pts)));
 }
 
 }  // namespace
@@ -924,54 +1133,108 @@ struct dsp_server {
     int64_t budget = 0, used = 0;
     int32_t max_active = 1;
     int64_t chunk = 1;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;       // compute (caller's)
+    cudaStream_t copy_stream = nullptr;  // table uploads
+    cudaEvent_t upload_done = nullptr;
+    cudaEvent_t iter_done[2] = {nullptr, nullptr};
+    int64_t iter = 0;                    // iterations queued so far
+    unsigned char *staging = nullptr;    // pinned table staging
+    size_t staging_cap = 0;
+    int *err = nullptr;                  // device error word of the batched launches
+    int *err_host = nullptr;             // pinned copy, refreshed every iteration
+    DeviceScalars *slots = nullptr;      // pinned, 2 * max_active: results of two iterations
     std::vector<std::unique_ptr<ServerReq>> reqs;  // by id
     std::deque<int64_t> queue;
-    std::vector<int64_t> active;
-    int *err = nullptr;  // device error word of the batched launches
+    std::vector<int64_t> active;         // admitted, not yet retired
     dsp_status latched = DSP_OK;
 };
 
 namespace {
 
+dsp_status server_fail(dsp_server *s, dsp_status st)
+{
+    cudaGetLastError();
+    if (s->latched == DSP_OK)
+        s->latched = st;
+    return st;
+}
+
 void server_release(dsp_server *s, ServerReq *r)
 {
-    if (r->g) {
-        dsp_destroy_grid(r->g);
-        r->g = nullptr;
+    if (r->block) {
+        cudaFreeAsync(r->block, s->stream);
+        r->block = nullptr;
     }
-    if (r->map_dev) {
-        cudaFree(r->map_dev);
-        r->map_dev = nullptr;
-    }
+    r->map_dev = nullptr;
     s->used -= r->footprint;
     r->footprint = 0;
 }
 
-// Allocates and uploads one request; false if the device refused memory.
+// Allocates from the pool and queues the table upload of one request.
 dsp_status server_admit(dsp_server *s, ServerReq *r)
 {
     const dsp_request &p = r->p;
-    dsp_status st = create_grid_impl(p.nx, p.ny, p.px_min, p.px_max, p.py_min, p.py_max,
-                                     p.precision, p.scheme, p.valley, s->stream, nullptr, 0, &r->g);
+    fill_grid(&r->g, p.nx, p.ny, p.px_min, p.px_max, p.py_min, p.py_max, p.precision, p.scheme,
+              p.valley, s->stream);
+    std::vector<unsigned char> host;
+    dsp_status st = prepare_pulse(&r->g, r->a_mid.data(), p.n_steps, p.dt, p.a_in, p.a_out, host);
     if (st != DSP_OK)
         return st;
-    const size_t mb = static_cast<size_t>(r->g->n_points) * map_elem_bytes(p.precision);
-    if (cudaMalloc(&r->map_dev, mb) != cudaSuccess) {
+    const size_t pts = static_cast<size_t>(r->g.n_points);
+    const size_t o_table = align256(32 * pts);
+    const size_t o_part = o_table + align256(host.size());
+    const size_t o_scal = o_part + align256(8 * static_cast<size_t>(r->g.n_tiles));
+    const size_t o_map = o_scal + align256(sizeof(DeviceScalars));
+    const size_t total = o_map + align256(map_elem_bytes(p.precision) * pts);
+    // allocated in stream order on the copy stream, so the upload does not wait for
+    // the iteration in flight on the compute stream; the compute stream waits for
+    // the upload before its first use, and frees the block after its last use
+    void *block = nullptr;
+    if (cudaMallocAsync(&block, total, s->copy_stream) != cudaSuccess) {
         cudaGetLastError();
-        r->map_dev = nullptr;
-        dsp_destroy_grid(r->g);
-        r->g = nullptr;
         return DSP_E_NOMEM;
     }
-    st = set_pulse_impl(r->g, r->a_mid.data(), p.n_steps, p.dt, p.a_in, p.a_out);
-    if (st != DSP_OK) {
-        cudaFree(r->map_dev);
-        r->map_dev = nullptr;
-        dsp_destroy_grid(r->g);
-        r->g = nullptr;
-        return st;
+    unsigned char *b = static_cast<unsigned char *>(block);
+    r->block = block;
+    r->g.state = b;
+    r->g.table = b + o_table;
+    r->g.table_cap = p.n_steps;
+    r->g.partials = reinterpret_cast<double *>(b + o_part);
+    r->g.scal = reinterpret_cast<DeviceScalars *>(b + o_scal);
+    r->map_dev = b + o_map;
+    if (p.keep_map && !r->map_host) {
+        if (cudaMallocHost(&r->map_host, map_elem_bytes(p.precision) * pts) != cudaSuccess) {
+            cudaGetLastError();
+            r->map_host = nullptr;
+            cudaFreeAsync(block, s->copy_stream);
+            r->block = nullptr;
+            return DSP_E_NOMEM;
+        }
     }
+    // table: host -> pinned staging -> device on the copy stream; the compute
+    // stream waits for it before the first launch
+    if (!host.empty()) {
+        if (cudaEventSynchronize(s->upload_done) != cudaSuccess)  // staging free again
+            return server_fail(s, DSP_E_CUDA);
+        if (host.size() > s->staging_cap) {
+            if (s->staging)
+                cudaFreeHost(s->staging);
+            s->staging = nullptr;
+            s->staging_cap = 0;
+            if (cudaMallocHost(reinterpret_cast<void **>(&s->staging), host.size()) != cudaSuccess)
+                return server_fail(s, DSP_E_NOMEM);
+            s->staging_cap = host.size();
+        }
+        std::memcpy(s->staging, host.data(), host.size());
+        if (cudaMemcpyAsync(r->g.table, s->staging, host.size(), cudaMemcpyHostToDevice,
+                            s->copy_stream) != cudaSuccess ||
+            cudaEventRecord(s->upload_done, s->copy_stream) != cudaSuccess ||
+            cudaStreamWaitEvent(s->stream, s->upload_done, 0) != cudaSuccess)
+            return server_fail(s, DSP_E_CUDA);
+    }
+    if (host.empty() && (cudaEventRecord(s->upload_done, s->copy_stream) != cudaSuccess ||
+                         cudaStreamWaitEvent(s->stream, s->upload_done, 0) != cudaSuccess))
+        return server_fail(s, DSP_E_CUDA);
     r->footprint = footprint_of(p);
     s->used += r->footprint;
     r->state = DSP_REQ_ACTIVE;
@@ -998,16 +1261,41 @@ dsp_status dsp_server_create(int64_t hbm_budget_bytes, int32_t max_active, int64
     s->max_active = max_active;
     s->chunk = chunk_steps;
     s->stream = static_cast<cudaStream_t>(cuda_stream);
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&s->err), sizeof(int));
+    cudaError_t e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&s->upload_done, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&s->iter_done[0], cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&s->iter_done[1], cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void **>(&s->err), sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMallocHost(reinterpret_cast<void **>(&s->err_host), sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMallocHost(reinterpret_cast<void **>(&s->slots),
+                           sizeof(DeviceScalars) * 2 * static_cast<size_t>(max_active));
     if (e == cudaSuccess)
         e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(s->upload_done, s->copy_stream);
+    if (e == cudaSuccess) {
+        // keep freed pool memory in the pool (no return to the driver at syncs)
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (s->err)
-            cudaFree(s->err);
-        delete s;
-        return DSP_E_NOMEM;
+        dsp_server_destroy(s);
+        return DSP_E_CUDA;
     }
+    *s->err_host = 0;
     *out = s;
     return DSP_OK;
 }
@@ -1031,7 +1319,8 @@ dsp_status dsp_server_submit(dsp_server *s, const dsp_request *req, const double
     probe.px_max = p.px_max;
     probe.py_min = p.py_min;
     probe.py_max = p.py_max;
-    st = validate_pulse_args(&probe, a_mid, p.n_steps, p.dt, p.a_in, p.a_out);
+    const int64_t n_samples = p.n_steps * samples_per_step(p.scheme);
+    st = validate_pulse_args(&probe, a_mid, n_samples, p.dt, p.a_in, p.a_out);
     if (st != DSP_OK)
         return st;
     if (footprint_of(p) > s->budget)
@@ -1042,7 +1331,7 @@ dsp_status dsp_server_submit(dsp_server *s, const dsp_request *req, const double
     r->id = static_cast<int64_t>(s->reqs.size());
     r->p = p;
     try {
-        r->a_mid.assign(a_mid, a_mid + 2 * p.n_steps);
+        r->a_mid.assign(a_mid, a_mid + 2 * n_samples);
     } catch (...) {
         return DSP_E_NOMEM;
     }
@@ -1059,18 +1348,11 @@ dsp_status dsp_server_step(dsp_server *s, int32_t *n_active, int32_t *n_queued,
         return DSP_E_INVALID;
     if (s->latched != DSP_OK)
         return s->latched;
+    const int64_t k = s->iter;
     int32_t finished = 0;
-    // 1. drop cancelled requests
+    // 1. drop cancelled queued requests; cancelled active ones stop being
+    //    launched and are released below once their last iteration is done
     {
-        std::vector<int64_t> keep;
-        for (int64_t id : s->active) {
-            ServerReq *r = s->reqs[id].get();
-            if (r->state == DSP_REQ_CANCELLED)
-                server_release(s, r);
-            else
-                keep.push_back(id);
-        }
-        s->active.swap(keep);
         std::deque<int64_t> q;
         for (int64_t id : s->queue)
             if (s->reqs[id]->state == DSP_REQ_QUEUED)
@@ -1084,89 +1366,81 @@ dsp_status dsp_server_step(dsp_server *s, int32_t *n_active, int32_t *n_queued,
             break;
         s->queue.pop_front();
         dsp_status st = server_admit(s, r);
+        if (s->latched != DSP_OK)
+            return s->latched;
         if (st != DSP_OK) {
             r->state = DSP_REQ_FAILED;
+            std::vector<double>().swap(r->a_mid);
             continue;
         }
         s->active.push_back(r->id);
     }
-    // 3. one batched launch per precision over every active request
-    if (!s->active.empty()) {
-        std::vector<dsp::FinDesc> fins;
-        for (int prec = 0; prec < 2; ++prec) {
-            std::vector<ReqDesc> descs;
-            for (int64_t id : s->active) {
-                ServerReq *r = s->reqs[id].get();
-                dsp_grid *g = r->g;
-                if (g->precision != prec)
-                    continue;
-                const int64_t end = std::min(g->n_steps, g->cursor + s->chunk);
-                r->finishing = (end == g->n_steps);
-                descs.push_back(make_desc(g, g->cursor, end, r->finishing, r->map_dev));
-                if (r->finishing)
-                    fins.push_back(fin_desc(g));
-            }
-            if (descs.empty())
-                continue;
-            cudaError_t e = launch_requests(descs, prec, s->err, s->stream);
-            if (e != cudaSuccess) {
-                s->latched = DSP_E_CUDA;
-                return DSP_E_CUDA;
-            }
-        }
-        cudaError_t e = launch_finalizes(fins, s->stream);
-        // 4. copy results of the finishing requests back
-        std::vector<DeviceScalars> hs(s->active.size());
-        size_t k = 0;
+    // 3. iteration k: one batched launch per precision over the running requests
+    bool queued_any = false;
+    std::vector<dsp::FinDesc> fins;
+    std::vector<ServerReq *> finishing;
+    for (int prec = 0; prec < 2; ++prec) {
+        std::vector<ReqDesc> descs;
         for (int64_t id : s->active) {
             ServerReq *r = s->reqs[id].get();
-            dsp_grid *g = r->g;
-            const int64_t end = std::min(g->n_steps, g->cursor + s->chunk);
-            g->cursor = end;
-            g->fresh = false;
-            if (!r->finishing || e != cudaSuccess) {
-                ++k;
+            dsp_grid &g = r->g;
+            if (r->finish_iter >= 0 || r->state != DSP_REQ_ACTIVE || g.precision != prec)
                 continue;
+            const int64_t end = std::min(g.n_steps, g.cursor + s->chunk);
+            const bool fin = (end == g.n_steps);
+            descs.push_back(make_desc(&g, g.cursor, end, fin, r->map_dev));
+            g.cursor = end;
+            g.fresh = false;
+            if (fin) {
+                r->finish_iter = k;
+                fins.push_back(fin_desc(&g));
+                finishing.push_back(r);
             }
-            g->projected = true;
-            e = cudaMemcpyAsync(&hs[k], g->scal, sizeof(DeviceScalars), cudaMemcpyDeviceToHost,
-                                s->stream);
-            if (e == cudaSuccess && r->p.keep_map) {
-                const size_t mb = static_cast<size_t>(g->n_points) * map_elem_bytes(g->precision);
-                try {
-                    r->map_host.resize(mb);
-                } catch (...) {
-                    r->state = DSP_REQ_FAILED;
-                }
-                if (r->state != DSP_REQ_FAILED)
-                    e = cudaMemcpyAsync(r->map_host.data(), r->map_dev, mb, cudaMemcpyDeviceToHost,
-                                        s->stream);
-            }
-            ++k;
         }
-        int herr = 0;
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&herr, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess)
-            e = cudaStreamSynchronize(s->stream);
-        if (e != cudaSuccess) {
-            s->latched = DSP_E_CUDA;
-            return DSP_E_CUDA;
-        }
-        if (herr & dsp::kErrTimeout) {
-            s->latched = DSP_E_TIMEOUT;
-            return DSP_E_TIMEOUT;
-        }
-        // 5. retire
+        if (descs.empty())
+            continue;
+        queued_any = true;
+        if (launch_requests(descs, prec, s->err, s->stream) != cudaSuccess)
+            return server_fail(s, DSP_E_CUDA);
+    }
+    if (launch_finalizes(fins, s->stream) != cudaSuccess)
+        return server_fail(s, DSP_E_CUDA);
+    // results land in pinned slots [(k & 1) * max_active, ...): read when iteration
+    // k is retired, at the latest in step k + 1, before step k + 2 reuses them
+    int32_t next_slot = static_cast<int32_t>(k & 1) * s->max_active;
+    for (ServerReq *r : finishing) {
+        r->slot = next_slot++;
+        cudaError_t e = cudaMemcpyAsync(&s->slots[r->slot], r->g.scal, sizeof(DeviceScalars),
+                                        cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess && r->p.keep_map)
+            e = cudaMemcpyAsync(r->map_host, r->map_dev,
+                                static_cast<size_t>(r->g.n_points) * map_elem_bytes(r->p.precision),
+                                cudaMemcpyDeviceToHost, s->stream);
+        if (e != cudaSuccess)
+            return server_fail(s, DSP_E_CUDA);
+    }
+    if (cudaMemcpyAsync(s->err_host, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream) !=
+            cudaSuccess ||
+        cudaEventRecord(s->iter_done[k & 1], s->stream) != cudaSuccess)
+        return server_fail(s, DSP_E_CUDA);
+    s->iter = k + 1;
+    (void)queued_any;
+    // 4. wait for iteration k-1 (k itself when nothing new was queued, so the
+    //    loop always makes progress) and retire what finished by then
+    const int64_t done_iter = queued_any ? k - 1 : k;
+    if (done_iter >= 0) {
+        if (cudaEventSynchronize(s->iter_done[done_iter & 1]) != cudaSuccess)
+            return server_fail(s, DSP_E_CUDA);
+        if (*s->err_host & dsp::kErrTimeout)
+            return server_fail(s, DSP_E_TIMEOUT);
         std::vector<int64_t> keep;
-        k = 0;
         for (int64_t id : s->active) {
             ServerReq *r = s->reqs[id].get();
-            if (r->finishing) {
-                if (hs[k].err & dsp::kErrTimeout) {
-                    r->state = DSP_REQ_FAILED;
-                } else if (r->state != DSP_REQ_FAILED) {
-                    r->density = hs[k].density;
+            const bool launched_out = r->finish_iter >= 0 && r->finish_iter <= done_iter;
+            const bool cancelled = r->state == DSP_REQ_CANCELLED;
+            if (launched_out || cancelled) {
+                if (launched_out && !cancelled) {
+                    r->density = s->slots[r->slot].density;
                     r->state = DSP_REQ_DONE;
                 }
                 server_release(s, r);
@@ -1174,7 +1448,6 @@ dsp_status dsp_server_step(dsp_server *s, int32_t *n_active, int32_t *n_queued,
             } else {
                 keep.push_back(id);
             }
-            ++k;
         }
         s->active.swap(keep);
     }
@@ -1195,12 +1468,13 @@ dsp_status dsp_server_query(dsp_server *s, int64_t id, int32_t *state, double *d
     ServerReq *r = s->reqs[id].get();
     *state = r->state;
     if (steps_done)
-        *steps_done = r->state == DSP_REQ_DONE ? r->p.n_steps : (r->g ? r->g->cursor : 0);
+        *steps_done = r->state == DSP_REQ_DONE ? r->p.n_steps : r->g.cursor;
     if (r->state == DSP_REQ_DONE) {
         if (density)
             *density = r->density;
-        if (map_host && !r->map_host.empty())
-            std::memcpy(map_host, r->map_host.data(), r->map_host.size());
+        if (map_host && r->map_host)
+            std::memcpy(map_host, r->map_host,
+                        static_cast<size_t>(r->p.nx) * r->p.ny * map_elem_bytes(r->p.precision));
     }
     return DSP_OK;
 }
@@ -1224,11 +1498,29 @@ dsp_status dsp_server_destroy(dsp_server *s)
         return DSP_OK;
     if (s->latched != DSP_E_CUDA)
         cudaStreamSynchronize(s->stream);
-    for (auto &r : s->reqs)
-        if (r->g || r->map_dev)
+    for (auto &r : s->reqs) {
+        if (r->block)
             server_release(s, r.get());
+        if (r->map_host)
+            cudaFreeHost(r->map_host);
+    }
+    if (s->latched != DSP_E_CUDA)
+        cudaStreamSynchronize(s->stream);
+    if (s->copy_stream) {
+        cudaStreamSynchronize(s->copy_stream);
+        cudaStreamDestroy(s->copy_stream);
+    }
+    for (cudaEvent_t ev : {s->upload_done, s->iter_done[0], s->iter_done[1]})
+        if (ev)
+            cudaEventDestroy(ev);
+    if (s->staging)
+        cudaFreeHost(s->staging);
     if (s->err)
         cudaFree(s->err);
+    if (s->err_host)
+        cudaFreeHost(s->err_host);
+    if (s->slots)
+        cudaFreeHost(s->slots);
     delete s;
     return DSP_OK;
 }

@@ -14,8 +14,6 @@ constexpr int kTilePoints = 1024;
 // Spinors per thread (independent momenta advanced together for ILP).
 constexpr int kSpinorsPerThread = 2;
 constexpr int kThreads = kTilePoints / kSpinorsPerThread;
-// A(t) entries per shared-memory buffer (16 bytes each; two buffers per CTA).
-constexpr int kChunkSteps = 1024;
 // Requests one evolve launch can carry in its parameter block.
 constexpr int kMaxReqPerLaunch = 48;
 // Device-side error bits (the launch's error word).
@@ -37,8 +35,11 @@ constexpr SeriesLevel kLevelsF64[kNumLevels] = {{3, 3}, {4, 3}, {4, 4}, {5, 5},
                                                  {6, 6}, {8, 8}, {11, 11}, {16, 16}};
 
 struct ReqDesc {
-    // float4 (FP32_MIXED: s*dt*Ax hi, lo, s*dt*Ay hi, lo) or double2 (FP64: s*dt*A),
-    // s = valley: valley K- steps as K+ on -P (its step operator is K+'s at -P).
+    // Per step, s = valley (valley K- steps as K+ on -P: its operator is K+'s at -P):
+    //   EXACT, STRANG_XY: float4 (FP32_MIXED: s*dt*Ax hi, lo, s*dt*Ay hi, lo) or
+    //     double2 (FP64: s*dt*A), A at the step midpoint;
+    //   MAGNUS4: that for Abar = (A1 + A2)/2, followed by D = -(sqrt(3)/6) s*dt*(A2 - A1)
+    //     as float4 (D_x, D_y, 0, 0) or double2, A1, A2 at the two Gauss points.
     const void *table;
     void *state;        // planes: FP32_MIXED float4 hi[n], float4 lo[n]; FP64 double2 a[n], double2 b[n]
     void *map;          // |c+|^2 output (float or double), or nullptr
@@ -55,7 +56,9 @@ struct ReqDesc {
     int32_t project;  // 1: project at the end (map + partials)
     int32_t tile_begin;  // first CTA of this request in the launch
     int32_t n_tiles;
-    int32_t pad;
+    int32_t init_identity;  // with fresh: start from the column (1, 0) of the identity
+                            // (the launch then computes the first column of the
+                            // product of its steps' operators)
 };
 
 struct EvolveArgs {
@@ -80,8 +83,25 @@ struct FinalizeArgs {
     FinDesc f[kMaxFinPerLaunch];
 };
 
+// Combines time segments: psi = M_{S-1} ... M_0 v(p + A_in) per point, where M_s
+// is the SU(2) matrix [[alpha, -conj(beta)], [beta, conj(alpha)]] whose first
+// column (alpha, beta) segment s left in its slab of `segs`; writes psi into
+// `state` in the grid's layout.  FP64 arithmetic for both precisions.
+struct CombineArgs {
+    const void *segs;  // S slabs of 32 * n_points bytes, in the state layout
+    void *state;
+    int64_t n_points;
+    int32_t n_segments;
+    int32_t nx;
+    double px_min, py_min, hx, hy;
+    double a_in[2];
+    int32_t valley;
+    int32_t pad;
+};
+
 // precision: 0 = FP64, 1 = FP32_MIXED.  Every request in args must have that precision.
 cudaError_t launch_evolve(const EvolveArgs &args, int precision, cudaStream_t stream);
 cudaError_t launch_finalize(const FinalizeArgs &args, cudaStream_t stream);
+cudaError_t launch_combine(const CombineArgs &args, int precision, cudaStream_t stream);
 
 }  // namespace dsp

@@ -224,30 +224,85 @@ __device__ __forceinline__ int find_request(const EvolveArgs &a)
 }
 
 // ---------------------------------------------------------------------------
-// Table staging: chunk c of the launch goes to buffer c & 1.
+// Table staging: chunk c of the launch goes to stage c & 1 of shared memory.
 // ---------------------------------------------------------------------------
+
+constexpr int kStageBytes = 16384;  // per stage; two stages per CTA
+
+// MAGNUS4 table entries: the Gauss-point mean (dt*Abar, valley-signed) and the
+// commutator factor D = -(sqrt(3)/6) dt (A2 - A1) (valley-signed).
+struct MixedG2 {
+    float4 a;  // (Abar_x hi, lo, Abar_y hi, lo)
+    float4 d;  // (D_x, D_y, 0, 0)
+};
+struct F64G2 {
+    double2 a;  // Abar
+    double2 d;  // D
+};
 
 template <typename E>
 struct Stager {
-    E (*buf)[kChunkSteps];
+    unsigned char *smem;
     uint64_t *bars;
     const E *table;  // entry step_begin is element 0 of chunk 0
     int64_t nsteps;
     int nchunks;
+    static constexpr int kCh = kStageBytes / static_cast<int>(sizeof(E));
 
+    __device__ __forceinline__ const E *stage(int c) const
+    {
+        return reinterpret_cast<const E *>(smem + (c & 1) * kStageBytes);
+    }
     __device__ __forceinline__ int chunk_len(int c) const
     {
-        const int64_t rem = nsteps - static_cast<int64_t>(c) * kChunkSteps;
-        return rem < kChunkSteps ? static_cast<int>(rem) : kChunkSteps;
+        const int64_t rem = nsteps - static_cast<int64_t>(c) * kCh;
+        return rem < kCh ? static_cast<int>(rem) : kCh;
     }
     __device__ __forceinline__ void issue(int c) const  // one thread
     {
         const uint32_t bytes = static_cast<uint32_t>(chunk_len(c)) * sizeof(E);
         mbar_arrive_expect_tx(&bars[c & 1], bytes);
-        bulk_load(&buf[c & 1][0], table + static_cast<int64_t>(c) * kChunkSteps, bytes,
+        bulk_load(smem + (c & 1) * kStageBytes, table + static_cast<int64_t>(c) * kCh, bytes,
                   &bars[c & 1]);
     }
 };
+
+// Runs the launch's steps with the table streamed through shared memory; STEP
+// is called as step(entry) for every step in order.  Returns false (and flags
+// err) if a staging wait timed out.
+template <typename E, typename StepFn>
+__device__ __forceinline__ bool run_steps(const ReqDesc &R, unsigned char *smem, uint64_t *bars,
+                                          int *err, StepFn step)
+{
+    Stager<E> st{smem, bars, static_cast<const E *>(R.table) + R.step_begin,
+                 R.step_end - R.step_begin, 0};
+    st.nchunks = static_cast<int>((st.nsteps + Stager<E>::kCh - 1) / Stager<E>::kCh);
+    if (threadIdx.x == 0) {
+        if (st.nchunks > 0) st.issue(0);
+        if (st.nchunks > 1) st.issue(1);
+    }
+    for (int c = 0; c < st.nchunks; ++c) {
+        const bool ok = mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(err, kErrTimeout);
+                // give copies still in flight a bounded chance to land before exit
+                for (int k = 0; k < st.nchunks && k < 2; ++k)
+                    (void)mbar_wait_bounded(&bars[k & 1], 0);
+            }
+            return false;
+        }
+        const E *tb = st.stage(c);
+        const int len = st.chunk_len(c);
+#pragma unroll 2
+        for (int j = 0; j < len; ++j)
+            step(tb[j]);  // shared-memory broadcast
+        __syncthreads();  // everyone is done with stage c & 1
+        if (threadIdx.x == 0 && c + 2 < st.nchunks)
+            st.issue(c + 2);
+    }
+    return true;
+}
 
 // ---------------------------------------------------------------------------
 // FP32_MIXED step
@@ -259,13 +314,15 @@ struct MixedPoint {
     float pxh, pxl, pyh, pyl;  // dt * p as hi + lo
 };
 
-// Coefficients of U - I = [[cm1, -q], [conj(q), cm1]] for the step with kinematic
-// momentum dt*P = (Pxh + Pxl, Pyh + Pyl).  P_h = p_h + A_h is exact (common 2^-k
-// grid), so P = fl(P_h + P_l) carries only its own final rounding, which varies
-// from step to step with A; no fixed (systematic) momentum error remains.
+// Coefficients of U - I = [[cm1 - i qz, -q], [conj(q), cm1 + i qz]], q = qr + i qi,
+// for the step with kinematic momentum dt*P = (Pxh + Pxl, Pyh + Pyl).  P_h = p_h +
+// A_h is exact (common 2^-k grid), so P = fl(P_h + P_l) carries only its own final
+// rounding, which varies from step to step with A: no fixed momentum error.
+// EXACT and STRANG_XY have qz = 0.
 template <int SCHEME, int DC, int DS>
 __device__ __forceinline__ void step_coeffs_f32(float Pxh, float Pxl, float Pyh, float Pyl,
-                                                float &cm1, float &qr, float &qi)
+                                                float2 d, float &cm1, float &qr, float &qi,
+                                                float &qz)
 {
     const float Px = Pxh + Pxl, Py = Pyh + Pyl;
     if constexpr (SCHEME == 0) {
@@ -274,7 +331,8 @@ __device__ __forceinline__ void step_coeffs_f32(float Pxh, float Pxl, float Pyh,
         const float sn = sinc_f32<DS>(x);
         qr = sn * Py;
         qi = sn * Px;
-    } else {
+        qz = 0.0f;
+    } else if constexpr (SCHEME == 1) {
         // e^{-i a sx} e^{-i b sy} e^{-i a sx}, a = dt Px / 2, b = dt Py:
         //   = [[cos b cos 2a, -(sin b + i cos b sin 2a)], [sin b - i cos b sin 2a, cos b cos 2a]]
         const float xx = Px * Px, xy = Py * Py;
@@ -283,17 +341,38 @@ __device__ __forceinline__ void step_coeffs_f32(float Pxh, float Pxl, float Pyh,
         cm1 = fmaf(cmx, cmy, cmx) + cmy;
         qr = Py * sinc_f32<DS>(xy);
         qi = fmaf(cmy, sx, sx);
+        qz = 0.0f;
+    } else {
+        // MAGNUS4: exp(-i n.sigma), n = (dt Pbar, n_z), n_z = -(sqrt 3/6) (dt P1 x dt P2)_z
+        // = (dt Pbar x D')_z with D' = -(sqrt 3/6) dt (A2 - A1) from the table (the
+        // cross product of the two nearly parallel momenta is never formed).
+        const float nz = fmaf(Px, d.y, -(Py * d.x));
+        const float x = fmaf(Px, Px, fmaf(Py, Py, nz * nz));
+        cm1 = cosm1_f32<DC>(x);
+        const float sn = sinc_f32<DS>(x);
+        qr = sn * Py;
+        qi = sn * Px;
+        qz = sn * nz;
     }
 }
 
 // psi <- U psi as psi_hi + (U - I) psi_hi + psi_lo, the rounding error of the
 // hi update carried into lo (Fast2Sum).
-__device__ __forceinline__ void apply_f32(MixedPoint &s, float cm1, float qr, float qi)
+template <int SCHEME>
+__device__ __forceinline__ void apply_f32(MixedPoint &s, float cm1, float qr, float qi, float qz)
 {
-    const float dar = fmaf(cm1, s.ar, fmaf(-qr, s.br, fmaf(qi, s.bi, s.lar)));
-    const float dai = fmaf(cm1, s.ai, fmaf(-qr, s.bi, fmaf(-qi, s.br, s.lai)));
-    const float dbr = fmaf(cm1, s.br, fmaf(qr, s.ar, fmaf(qi, s.ai, s.lbr)));
-    const float dbi = fmaf(cm1, s.bi, fmaf(qr, s.ai, fmaf(-qi, s.ar, s.lbi)));
+    float dar, dai, dbr, dbi;
+    if constexpr (SCHEME == 2) {
+        dar = fmaf(cm1, s.ar, fmaf(qz, s.ai, fmaf(-qr, s.br, fmaf(qi, s.bi, s.lar))));
+        dai = fmaf(cm1, s.ai, fmaf(-qz, s.ar, fmaf(-qr, s.bi, fmaf(-qi, s.br, s.lai))));
+        dbr = fmaf(cm1, s.br, fmaf(-qz, s.bi, fmaf(qr, s.ar, fmaf(qi, s.ai, s.lbr))));
+        dbi = fmaf(cm1, s.bi, fmaf(qz, s.br, fmaf(qr, s.ai, fmaf(-qi, s.ar, s.lbi))));
+    } else {
+        dar = fmaf(cm1, s.ar, fmaf(-qr, s.br, fmaf(qi, s.bi, s.lar)));
+        dai = fmaf(cm1, s.ai, fmaf(-qr, s.bi, fmaf(-qi, s.br, s.lai)));
+        dbr = fmaf(cm1, s.br, fmaf(qr, s.ar, fmaf(qi, s.ai, s.lbr)));
+        dbi = fmaf(cm1, s.bi, fmaf(qr, s.ai, fmaf(-qi, s.ar, s.lbi)));
+    }
     float t;
     t = s.ar + dar; s.lar = dar - (t - s.ar); s.ar = t;
     t = s.ai + dai; s.lai = dai - (t - s.ai); s.ai = t;
@@ -302,7 +381,16 @@ __device__ __forceinline__ void apply_f32(MixedPoint &s, float cm1, float qr, fl
 }
 
 template <int SCHEME, int DC, int DS>
-__device__ void body_mixed(const ReqDesc &R, int tile, float4 (*buf)[kChunkSteps], uint64_t *bars,
+__device__ __forceinline__ void step_mixed(MixedPoint &p, const float4 &a, float2 d)
+{
+    float cm1, qr, qi, qz;
+    step_coeffs_f32<SCHEME, DC, DS>(p.pxh + a.x, p.pxl + a.y, p.pyh + a.z, p.pyl + a.w, d, cm1,
+                                    qr, qi, qz);
+    apply_f32<SCHEME>(p, cm1, qr, qi, qz);
+}
+
+template <int SCHEME, int DC, int DS>
+__device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint64_t *bars,
                            int *err)
 {
     constexpr int S = kSpinorsPerThread;
@@ -330,8 +418,9 @@ __device__ void body_mixed(const ReqDesc &R, int tile, float4 (*buf)[kChunkSteps
         pt[s].pyh = static_cast<float>(hy);
         pt[s].pyl = static_cast<float>(ty - hy);
         if (R.fresh || !valid) {
-            double ar, ai, br, bi;
-            initial_spinor(px + R.a_in[0], py + R.a_in[1], vs, ar, ai, br, bi);
+            double ar = 1.0, ai = 0.0, br = 0.0, bi = 0.0;  // identity column
+            if (!R.init_identity)
+                initial_spinor(px + R.a_in[0], py + R.a_in[1], vs, ar, ai, br, bi);
             pt[s].ar = static_cast<float>(ar);
             pt[s].lar = static_cast<float>(ar - static_cast<double>(pt[s].ar));
             pt[s].ai = static_cast<float>(ai);
@@ -347,46 +436,22 @@ __device__ void body_mixed(const ReqDesc &R, int tile, float4 (*buf)[kChunkSteps
         }
     }
 
-    Stager<float4> st{buf, bars, static_cast<const float4 *>(R.table) + R.step_begin,
-                      R.step_end - R.step_begin, 0};
-    st.nchunks = static_cast<int>((st.nsteps + kChunkSteps - 1) / kChunkSteps);
-    if (tid == 0) {
-        if (st.nchunks > 0) st.issue(0);
-        if (st.nchunks > 1) st.issue(1);
-    }
-    bool failed = false;
-    for (int c = 0; c < st.nchunks; ++c) {
-        const bool ok = mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1);
-        if (!__syncthreads_and(ok)) {
-            failed = true;
-            break;
-        }
-        const float4 *tb = buf[c & 1];
-        const int len = st.chunk_len(c);
-#pragma unroll 2
-        for (int j = 0; j < len; ++j) {
-            const float4 a = tb[j];  // (dt Ax hi, lo, dt Ay hi, lo): shared-memory broadcast
+    bool ok;
+    if constexpr (SCHEME == 2) {
+        ok = run_steps<MixedG2>(R, smem, bars, err, [&](const MixedG2 &e) {
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                float cm1, qr, qi;
-                step_coeffs_f32<SCHEME, DC, DS>(pt[s].pxh + a.x, pt[s].pxl + a.y, pt[s].pyh + a.z,
-                                                pt[s].pyl + a.w, cm1, qr, qi);
-                apply_f32(pt[s], cm1, qr, qi);
-            }
-        }
-        __syncthreads();  // everyone is done with buffer c & 1
-        if (tid == 0 && c + 2 < st.nchunks)
-            st.issue(c + 2);
+            for (int s = 0; s < S; ++s)
+                step_mixed<SCHEME, DC, DS>(pt[s], e.a, make_float2(e.d.x, e.d.y));
+        });
+    } else {
+        ok = run_steps<float4>(R, smem, bars, err, [&](const float4 &e) {
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+                step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
+        });
     }
-    if (failed) {
-        if (tid == 0) {
-            atomicOr(err, kErrTimeout);
-            // give copies still in flight a bounded chance to land before exit
-            for (int c = 0; c < st.nchunks && c < 2; ++c)
-                (void)mbar_wait_bounded(&bars[c & 1], 0);
-        }
+    if (!ok)
         return;
-    }
 
     double cp2[S];
 #pragma unroll
@@ -410,7 +475,7 @@ __device__ void body_mixed(const ReqDesc &R, int tile, float4 (*buf)[kChunkSteps
         }
     }
     if (R.project) {
-        double *red = reinterpret_cast<double *>(&buf[0][0]);  // table buffers are free now
+        double *red = reinterpret_cast<double *>(smem);  // the table stages are free now
 #pragma unroll
         for (int s = 0; s < S; ++s)
             red[s * kThreads + tid] = cp2[s];
@@ -427,38 +492,53 @@ __device__ void body_mixed(const ReqDesc &R, int tile, float4 (*buf)[kChunkSteps
 
 struct F64Point {
     double ar, ai, br, bi;
-    double tx, ty;  // dt * p
+    double tx, ty;  // dt * p (times the valley sign)
 };
 
 template <int SCHEME, int DC, int DS>
-__device__ __forceinline__ void step_f64(F64Point &s, double2 a)
+__device__ __forceinline__ void step_f64(F64Point &s, double2 a, double2 d)
 {
     const double Px = s.tx + a.x, Py = s.ty + a.y;  // dt * P (times the valley sign)
-    double c, qr, qi;
+    double c, qr, qi, qz = 0.0;
     if constexpr (SCHEME == 0) {
         const double x = fma(Px, Px, Py * Py);
         c = cos_f64<DC>(x);
         const double sn = sinc_f64<DS>(x);
         qr = sn * Py;
         qi = sn * Px;
-    } else {
+    } else if constexpr (SCHEME == 1) {
         const double xx = Px * Px, xy = Py * Py;
         const double cy = cos_f64<DC>(xy);
         c = cy * cos_f64<DC>(xx);
         qr = Py * sinc_f64<DS>(xy);
         qi = cy * (Px * sinc_f64<DS>(xx));
+    } else {
+        const double nz = fma(Px, d.y, -(Py * d.x));  // see step_coeffs_f32
+        const double x = fma(Px, Px, fma(Py, Py, nz * nz));
+        c = cos_f64<DC>(x);
+        const double sn = sinc_f64<DS>(x);
+        qr = sn * Py;
+        qi = sn * Px;
+        qz = sn * nz;
     }
-    // a' = c a - q b ; b' = conj(q) a + c b, q = qr + i qi
-    const double nar = fma(c, s.ar, fma(-qr, s.br, qi * s.bi));
-    const double nai = fma(c, s.ai, fma(-qr, s.bi, -(qi * s.br)));
-    const double nbr = fma(c, s.br, fma(qr, s.ar, qi * s.ai));
-    const double nbi = fma(c, s.bi, fma(qr, s.ai, -(qi * s.ar)));
+    // a' = (c - i qz) a - q b ; b' = conj(q) a + (c + i qz) b, q = qr + i qi
+    double nar, nai, nbr, nbi;
+    if constexpr (SCHEME == 2) {
+        nar = fma(c, s.ar, fma(qz, s.ai, fma(-qr, s.br, qi * s.bi)));
+        nai = fma(c, s.ai, fma(-qz, s.ar, fma(-qr, s.bi, -(qi * s.br))));
+        nbr = fma(c, s.br, fma(-qz, s.bi, fma(qr, s.ar, qi * s.ai)));
+        nbi = fma(c, s.bi, fma(qz, s.br, fma(qr, s.ai, -(qi * s.ar))));
+    } else {
+        nar = fma(c, s.ar, fma(-qr, s.br, qi * s.bi));
+        nai = fma(c, s.ai, fma(-qr, s.bi, -(qi * s.br)));
+        nbr = fma(c, s.br, fma(qr, s.ar, qi * s.ai));
+        nbi = fma(c, s.bi, fma(qr, s.ai, -(qi * s.ar)));
+    }
     s.ar = nar; s.ai = nai; s.br = nbr; s.bi = nbi;
 }
 
 template <int SCHEME, int DC, int DS>
-__device__ void body_f64(const ReqDesc &R, int tile, double2 (*buf)[kChunkSteps], uint64_t *bars,
-                         int *err)
+__device__ void body_f64(const ReqDesc &R, int tile, unsigned char *smem, uint64_t *bars, int *err)
 {
     constexpr int S = kSpinorsPerThread;
     const int tid = threadIdx.x;
@@ -480,49 +560,34 @@ __device__ void body_f64(const ReqDesc &R, int tile, double2 (*buf)[kChunkSteps]
         pt[s].tx = vs * (R.dt * px);  // valley K- is stepped as K+ on -P
         pt[s].ty = vs * (R.dt * py);
         if (R.fresh || !valid) {
-            initial_spinor(px + R.a_in[0], py + R.a_in[1], vs, pt[s].ar, pt[s].ai, pt[s].br,
-                           pt[s].bi);
+            if (R.init_identity) {
+                pt[s].ar = 1.0; pt[s].ai = 0.0; pt[s].br = 0.0; pt[s].bi = 0.0;
+            } else {
+                initial_spinor(px + R.a_in[0], py + R.a_in[1], vs, pt[s].ar, pt[s].ai, pt[s].br,
+                               pt[s].bi);
+            }
         } else {
             const double2 a = a_plane[idx], b = b_plane[idx];
             pt[s].ar = a.x; pt[s].ai = a.y; pt[s].br = b.x; pt[s].bi = b.y;
         }
     }
 
-    Stager<double2> st{buf, bars, static_cast<const double2 *>(R.table) + R.step_begin,
-                       R.step_end - R.step_begin, 0};
-    st.nchunks = static_cast<int>((st.nsteps + kChunkSteps - 1) / kChunkSteps);
-    if (tid == 0) {
-        if (st.nchunks > 0) st.issue(0);
-        if (st.nchunks > 1) st.issue(1);
-    }
-    bool failed = false;
-    for (int c = 0; c < st.nchunks; ++c) {
-        const bool ok = mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1);
-        if (!__syncthreads_and(ok)) {
-            failed = true;
-            break;
-        }
-        const double2 *tb = buf[c & 1];
-        const int len = st.chunk_len(c);
-#pragma unroll 2
-        for (int j = 0; j < len; ++j) {
-            const double2 a = tb[j];
+    bool ok;
+    if constexpr (SCHEME == 2) {
+        ok = run_steps<F64G2>(R, smem, bars, err, [&](const F64G2 &e) {
 #pragma unroll
             for (int s = 0; s < S; ++s)
-                step_f64<SCHEME, DC, DS>(pt[s], a);
-        }
-        __syncthreads();
-        if (tid == 0 && c + 2 < st.nchunks)
-            st.issue(c + 2);
+                step_f64<SCHEME, DC, DS>(pt[s], e.a, e.d);
+        });
+    } else {
+        ok = run_steps<double2>(R, smem, bars, err, [&](const double2 &e) {
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+                step_f64<SCHEME, DC, DS>(pt[s], e, make_double2(0.0, 0.0));
+        });
     }
-    if (failed) {
-        if (tid == 0) {
-            atomicOr(err, kErrTimeout);
-            for (int c = 0; c < st.nchunks && c < 2; ++c)
-                (void)mbar_wait_bounded(&bars[c & 1], 0);
-        }
+    if (!ok)
         return;
-    }
 
     double cp2[S];
 #pragma unroll
@@ -543,7 +608,7 @@ __device__ void body_f64(const ReqDesc &R, int tile, double2 (*buf)[kChunkSteps]
         }
     }
     if (R.project) {
-        double *red = reinterpret_cast<double *>(&buf[0][0]);
+        double *red = reinterpret_cast<double *>(smem);
 #pragma unroll
         for (int s = 0; s < S; ++s)
             red[s * kThreads + tid] = cp2[s];
@@ -556,24 +621,23 @@ __device__ void body_f64(const ReqDesc &R, int tile, double2 (*buf)[kChunkSteps]
 
 // Block-uniform dispatch on the request's series level (compile-time degrees).
 template <int SCHEME, int L>
-__device__ __forceinline__ void dispatch_mixed(const ReqDesc &R, int tile,
-                                               float4 (*buf)[kChunkSteps], uint64_t *bars,
-                                               int *err)
+__device__ __forceinline__ void dispatch_mixed(const ReqDesc &R, int tile, unsigned char *smem,
+                                               uint64_t *bars, int *err)
 {
     if (R.level == L || L + 1 == kNumLevels)
-        body_mixed<SCHEME, kLevelsF32[L].dc, kLevelsF32[L].ds>(R, tile, buf, bars, err);
+        body_mixed<SCHEME, kLevelsF32[L].dc, kLevelsF32[L].ds>(R, tile, smem, bars, err);
     else if constexpr (L + 1 < kNumLevels)
-        dispatch_mixed<SCHEME, L + 1>(R, tile, buf, bars, err);
+        dispatch_mixed<SCHEME, L + 1>(R, tile, smem, bars, err);
 }
 
 template <int SCHEME, int L>
-__device__ __forceinline__ void dispatch_f64(const ReqDesc &R, int tile,
-                                             double2 (*buf)[kChunkSteps], uint64_t *bars, int *err)
+__device__ __forceinline__ void dispatch_f64(const ReqDesc &R, int tile, unsigned char *smem,
+                                             uint64_t *bars, int *err)
 {
     if (R.level == L || L + 1 == kNumLevels)
-        body_f64<SCHEME, kLevelsF64[L].dc, kLevelsF64[L].ds>(R, tile, buf, bars, err);
+        body_f64<SCHEME, kLevelsF64[L].dc, kLevelsF64[L].ds>(R, tile, smem, bars, err);
     else if constexpr (L + 1 < kNumLevels)
-        dispatch_f64<SCHEME, L + 1>(R, tile, buf, bars, err);
+        dispatch_f64<SCHEME, L + 1>(R, tile, smem, bars, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -583,7 +647,7 @@ __device__ __forceinline__ void dispatch_f64(const ReqDesc &R, int tile,
 __global__ void __launch_bounds__(kThreads, 2)
     evolve_mixed_kernel(const __grid_constant__ EvolveArgs args)
 {
-    __shared__ __align__(128) float4 buf[2][kChunkSteps];
+    __shared__ __align__(128) unsigned char smem[2 * kStageBytes];
     __shared__ __align__(8) uint64_t bars[2];
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
@@ -595,15 +659,17 @@ __global__ void __launch_bounds__(kThreads, 2)
     const ReqDesc &R = args.r[r];
     const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
     if (R.scheme == 0)
-        dispatch_mixed<0, 0>(R, tile, buf, bars, args.err);
+        dispatch_mixed<0, 0>(R, tile, smem, bars, args.err);
+    else if (R.scheme == 1)
+        dispatch_mixed<1, 0>(R, tile, smem, bars, args.err);
     else
-        dispatch_mixed<1, 0>(R, tile, buf, bars, args.err);
+        dispatch_mixed<2, 0>(R, tile, smem, bars, args.err);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
     evolve_f64_kernel(const __grid_constant__ EvolveArgs args)
 {
-    __shared__ __align__(128) double2 buf[2][kChunkSteps];
+    __shared__ __align__(128) unsigned char smem[2 * kStageBytes];
     __shared__ __align__(8) uint64_t bars[2];
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
@@ -615,9 +681,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const ReqDesc &R = args.r[r];
     const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
     if (R.scheme == 0)
-        dispatch_f64<0, 0>(R, tile, buf, bars, args.err);
+        dispatch_f64<0, 0>(R, tile, smem, bars, args.err);
+    else if (R.scheme == 1)
+        dispatch_f64<1, 0>(R, tile, smem, bars, args.err);
     else
-        dispatch_f64<1, 0>(R, tile, buf, bars, args.err);
+        dispatch_f64<2, 0>(R, tile, smem, bars, args.err);
 }
 
 // One CTA per density: fixed-order per-thread sums, then a pairwise tree.
@@ -639,7 +707,70 @@ __global__ void __launch_bounds__(1024) finalize_kernel(const __grid_constant__ 
         *f.out = red[0] * f.scale;
 }
 
+// Time-parallel combination, one thread per momentum: psi <- M_s psi for s =
+// 0 .. S-1 in time order, starting from v(p + A_in), all in FP64.
+template <int PREC>
+__global__ void __launch_bounds__(128) combine_kernel(const __grid_constant__ CombineArgs a)
+{
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= a.n_points)
+        return;
+    const double vs = a.valley > 0 ? 1.0 : -1.0;
+    const double px = grid_node(a.px_min, a.hx, idx % a.nx);
+    const double py = grid_node(a.py_min, a.hy, idx / a.nx);
+    double ar, ai, br, bi;
+    initial_spinor(px + a.a_in[0], py + a.a_in[1], vs, ar, ai, br, bi);
+    const size_t slab = static_cast<size_t>(a.n_points) * 32;
+    for (int s = 0; s < a.n_segments; ++s) {
+        const unsigned char *seg = static_cast<const unsigned char *>(a.segs) + s * slab;
+        double alr, ali, ber, bei;  // (alpha, beta): first column of M_s
+        if constexpr (PREC == 1) {
+            const float4 h = reinterpret_cast<const float4 *>(seg)[idx];
+            const float4 l = reinterpret_cast<const float4 *>(seg)[a.n_points + idx];
+            alr = static_cast<double>(h.x) + l.x;
+            ali = static_cast<double>(h.y) + l.y;
+            ber = static_cast<double>(h.z) + l.z;
+            bei = static_cast<double>(h.w) + l.w;
+        } else {
+            const double2 c0 = reinterpret_cast<const double2 *>(seg)[idx];
+            const double2 c1 = reinterpret_cast<const double2 *>(seg)[a.n_points + idx];
+            alr = c0.x; ali = c0.y; ber = c1.x; bei = c1.y;
+        }
+        // a' = alpha a - conj(beta) b ; b' = beta a + conj(alpha) b
+        const double nar = alr * ar - ali * ai - (ber * br + bei * bi);
+        const double nai = alr * ai + ali * ar - (ber * bi - bei * br);
+        const double nbr = ber * ar - bei * ai + (alr * br + ali * bi);
+        const double nbi = ber * ai + bei * ar + (alr * bi - ali * br);
+        ar = nar; ai = nai; br = nbr; bi = nbi;
+    }
+    if constexpr (PREC == 1) {
+        float4 *hi = static_cast<float4 *>(a.state);
+        float4 *lo = hi + a.n_points;
+        const float h0 = static_cast<float>(ar), h1 = static_cast<float>(ai);
+        const float h2 = static_cast<float>(br), h3 = static_cast<float>(bi);
+        hi[idx] = make_float4(h0, h1, h2, h3);
+        lo[idx] = make_float4(static_cast<float>(ar - h0), static_cast<float>(ai - h1),
+                              static_cast<float>(br - h2), static_cast<float>(bi - h3));
+    } else {
+        double2 *pa = static_cast<double2 *>(a.state);
+        pa[idx] = make_double2(ar, ai);
+        pa[a.n_points + idx] = make_double2(br, bi);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_combine(const CombineArgs &args, int precision, cudaStream_t stream)
+{
+    if (args.n_points <= 0)
+        return cudaSuccess;
+    const int64_t blocks = (args.n_points + 127) / 128;
+    if (precision == 1)
+        combine_kernel<1><<<static_cast<unsigned>(blocks), 128, 0, stream>>>(args);
+    else
+        combine_kernel<0><<<static_cast<unsigned>(blocks), 128, 0, stream>>>(args);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_evolve(const EvolveArgs &args, int precision, cudaStream_t stream)
 {

@@ -101,3 +101,12 @@ def test_paper_pulse_closed_form_matches_oracle_quadrature(lib, orc):
     scale = np.abs(b).max()
     assert scale > 0.1
     assert np.abs(a - b).max() <= 1e-12 * scale and abs(ao[0] - bo[0]) <= 1e-12 * scale
+
+
+def test_gauss_sampler_agrees_with_oracle(lib, orc):
+    for spec in (W.sin2_pulse(1.0, 1.55, 5.0, eps=0.3), W.paper_pulse(phi=0.7),
+                 W.gauss_pulse(2.0, 1.55, 4.0)):
+        a, ai, ao, dt = B.sample_pulse_gauss(spec, 611)
+        b, bi, bo, dtb = orc.pulse_table_gauss(spec, 611)
+        scale = max(1.0, np.abs(b).max())
+        assert dt == dtb and np.abs(a - b).max() <= 1e-12 * scale

@@ -284,15 +284,81 @@ def test_two_colour_4096_full_size_sampled(orc):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
-def test_paper_laser_pulse_map(orc, prec):
-    """Sec. IV pulse (Fig. 1 parameters in eV units): A_in = 0 and A_out != 0, so
-    the projection uses a shifted momentum.  Whole 64x64 map on [-0.5,0.5]^2."""
-    pulse = W.paper_pulse()
+@pytest.mark.parametrize("phi", [0.0, math.pi / 3])
+def test_paper_laser_pulse_map(orc, prec, phi):
+    """Sec. IV pulse (Fig. 1 parameters in eV units).  With phi = 0 the field is
+    odd about T/2, so A_out = 0; phi = pi/3 gives A_out != 0, so the projection
+    uses a shifted momentum.  Whole 64x64 map on [-0.5,0.5]^2."""
+    pulse = W.paper_pulse(phi=phi)
     grid = {"nx": 64, "ny": 64, "px": (-0.5, 0.5), "py": (-0.5, 0.5)}
     steps = 20000
     tab_o = orc.pulse_table(pulse, steps)
-    assert abs(tab_o[2][0]) > 1e-3  # A_out != 0
+    if phi != 0.0:
+        assert abs(tab_o[2][0]) > 1e-3
     ref, nref = run_oracle(orc, grid, tab_o)
     m, n = run_gpu(grid, B.sample_pulse(pulse, steps), prec)
     assert ref.max() > 1e-3
     assert_close(prec, m, n, ref, nref)
+
+
+# ----------------------------------------------------------------------------------------
+# Fourth-order Magnus scheme (two Gauss points per step)
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+@pytest.mark.parametrize("valley", [1, -1])
+def test_magnus4_ragged_against_oracle(orc, prec, valley):
+    grid = {"nx": 67, "ny": 45, "px": (-3.0, 5.0), "py": (-2.5, 3.5)}
+    pulse = W.sin2_pulse(2.0, 1.2, 4.0, eps=0.6)
+    n = 1500
+    a, a_in, a_out, dt = orc.pulse_table_gauss(pulse, n)
+    ref, _, _, nref = orc.solve_grid(67, 45, grid["px"], grid["py"], a, dt, a_in, a_out,
+                                     scheme="magnus4", valley=valley)
+    m, dens = run_gpu(grid, B.sample_pulse_gauss(pulse, n), prec, "magnus4", valley,
+                      pieces=[600, 1, 899])
+    assert_close(prec, m, dens, ref, nref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_magnus4_reaches_midpoint_accuracy_with_fewer_steps(orc, prec):
+    """Against a converged oracle reference, MAGNUS4 with 500 steps is far more
+    accurate than the midpoint scheme with 2000 steps (fourth vs second order)."""
+    cfg = W.config_sin2_64()
+    g = cfg["grid"]
+    a, a_in, a_out, dt = orc.pulse_table_gauss(cfg["pulse"], 16000)
+    ref, _, _, _ = orc.solve_grid(g["nx"], g["ny"], g["px"], g["py"], a, dt, a_in, a_out,
+                                  scheme="magnus4")
+    m4, _ = run_gpu(g, B.sample_pulse_gauss(cfg["pulse"], 500), prec, "magnus4")
+    mid, _ = run_gpu(g, B.sample_pulse(cfg["pulse"], 2000), prec, "exact")
+    err4, err2 = np.abs(m4 - ref).max(), np.abs(mid - ref).max()
+    assert err4 < 0.1 * err2, (err4, err2)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_magnus4_segmented_and_served(orc, prec):
+    grid = {"nx": 48, "ny": 40, "px": (-4.0, 4.0), "py": (-4.0, 4.0)}
+    pulse = W.sin2_pulse(1.5, 1.3, 3.0, eps=0.2)
+    n = 900
+    a, a_in, a_out, dt = orc.pulse_table_gauss(pulse, n)
+    ref, _, _, nref = orc.solve_grid(48, 40, grid["px"], grid["py"], a, dt, a_in, a_out,
+                                     scheme="magnus4")
+    tab = B.sample_pulse_gauss(pulse, n)
+    g = B.Grid(48, 40, grid["px"], grid["py"], prec, "magnus4")
+    g.set_pulse(tab[0], tab[3], tab[1], tab[2])
+    m, dens = g.solve_segmented(0)
+    torch.cuda.synchronize()
+    assert_close(prec, m.double().cpu().numpy(), dens, ref, nref)
+    g.close()
+    m_alone, n_alone = run_gpu(grid, tab, prec, "magnus4")
+    srv = B.server_create(1 << 30, 4, 250)
+    rid = B.server_submit(srv, B.make_request(grid, n, tab[3], tab[1], tab[2], prec, "magnus4",
+                                              keep_map=True), tab[0])
+    for _ in range(100):
+        act, q, f = B.server_step(srv)
+        if act == 0 and q == 0:
+            break
+    out = np.zeros((40, 48), dtype=np.float64 if prec == "fp64" else np.float32)
+    state, dens_s, _ = B.server_query(srv, rid, out)
+    B.server_destroy(srv)
+    assert state == "done" and dens_s == n_alone
+    assert np.array_equal(out.astype(np.float64), m_alone)
