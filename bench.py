@@ -135,8 +135,8 @@ class ClockSampler:
 # SHA-256 of the kernel source the counters were taken on; a different source
 # means the counters are stale and the traffic is reported as null.
 KERNEL_TRAFFIC = {
-    "evolve_mixed_kernel": {"bytes": 90.98e6, "source_sha256": "ada8cc2fdf5c767ae38d81b10519efdcbfc43b213e1e97fee44209421a7661b8",
-                            "profile": "profiles/evolve_kernels_lzs2048_2000steps_full.md"},
+    "evolve_mixed_kernel": {"bytes": 109.78e6, "source_sha256": "61a3a72a01332f57f91f8449f365895a5e8ab606279a9eb481d96c9b738e57e7",
+                            "profile": "profiles/evolve_mixed_lzs2048_1e5_traffic.md"},
 }
 
 
@@ -164,21 +164,24 @@ def load_peaks():
 
 
 # ------------------------------------------------------------------------------------------
-# FP32 lane instructions per spinor-step of the FP32-mixed EXACT step, with series
-# degrees dc (cos) and ds (sin/theta) as the library reports them:
+# FP32 lane instructions of the FP32-mixed EXACT path, with series degrees dc (cos) and
+# ds (sin/theta) as the library reports them.  Per step:
 #   P_h = p_h + A_h, P_l = p_l + A_l, P = P_h + P_l (x and y)   6
 #   theta^2 = fma(Px, Px, Py*Py)                               2
 #   cos(theta) - 1 (Horner, dc - 1 FMA + 1 MUL)                dc
 #   sin(theta)/theta (Horner)                                  ds
 #   q = sinc * (P_y + i P_x)                                   2
-#   (U - I) psi_hi + psi_lo                                    12
+# per PAIR of steps (the two operators multiplied, then one compensated update):
+#   U2 U1 - I: al - 1 (5), Im al (2), Q (6)                    13
+#   (U2 U1 - I) psi_hi + psi_lo                                16
 #   Fast2Sum of the 4 components                               12
+# i.e. 30.5 + dc + ds per spinor-step.
 # FP64 instructions per spinor-step of the FP64 EXACT step:
 #   P (2) + theta^2 (2) + cos (dc) + sinc (ds) + q (2) + U psi (12)
 # ------------------------------------------------------------------------------------------
 
-def ops_mixed(dc, ds):
-    return 34 + dc + ds
+def ops_mixed(dc, ds, paired=True):
+    return (30.5 if paired else 34) + dc + ds
 
 
 def ops_fp64(dc, ds):
@@ -225,7 +228,10 @@ def run_gpu(args):
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def timed_solves(prec, warm, steps, sample_offset):
+    kept = {}  # (precision, sample) -> host |c+|^2 map, for the accuracy check
+    dens_by = {}  # (precision, sample) -> density
+
+    def timed_solves(prec, warm, steps, sample_offset, keep_sample=None):
         h, state, mp = make(prec)
         dens = []
         times = []
@@ -244,12 +250,19 @@ def run_gpu(args):
             B.solve(h, mp.data_ptr(), want_density=False)
             e1.record(stream)
             torch.cuda.synchronize()
+            if s == keep_sample and (prec, s) not in kept:
+                kept[(prec, s)] = mp.double().cpu().numpy()
+            if (prec, s) not in dens_by:
+                dens_by[(prec, s)] = B.reduce_density(h)
             if k >= warm:
                 times.append(e0.elapsed_time(e1) / 1e3)
                 dens.append(B.reduce_density(h))
                 info = B.get_info(h)
-                f = ops_fp64 if prec == "fp64" else ops_mixed
-                ops.append(f(info["cos_degree"], info["sinc_degree"]))
+                if prec == "fp64":
+                    ops.append(ops_fp64(info["cos_degree"], info["sinc_degree"]))
+                else:
+                    ops.append(ops_mixed(info["cos_degree"], info["sinc_degree"],
+                                         bool(info["paired_steps"])))
         B.destroy_grid(h)
         del state, mp
         return times, dens, ops
@@ -257,7 +270,8 @@ def run_gpu(args):
     sampler = ClockSampler(local)
     # ---- FP32-mixed (headline) ----
     sampler.start()
-    t_mixed, d_mixed, o_mixed = timed_solves("fp32_mixed", args.warmup, args.steps, 0)
+    t_mixed, d_mixed, o_mixed = timed_solves("fp32_mixed", args.warmup, args.steps, 0,
+                                             keep_sample=0)
     clocks = sampler.stop()
     tot = sum(t_mixed)
     if world > 1:
@@ -270,9 +284,9 @@ def run_gpu(args):
     # ---- FP64 ----
     fp64 = None
     if not args.no_fp64:
-        # offset so the FP64 leg's timed samples are the FP32-mixed leg's first ones
-        t64, d64, o64 = timed_solves("fp64", args.fp64_warmup, args.fp64_steps,
-                                     (args.warmup - args.fp64_warmup) * world)
+        # sample 0 first (its map is checked against the oracle below)
+        t64, d64, o64 = timed_solves("fp64", args.fp64_warmup, args.fp64_steps, 0,
+                                     keep_sample=0)
         tt = sum(t64)
         if world > 1:
             t = torch.tensor([tt], dtype=torch.float64, device="cuda")
@@ -281,8 +295,9 @@ def run_gpu(args):
         fp64 = {"value": work_per_solve * args.fp64_steps * world / tt, "unit": METRIC,
                 "ms_per_step": 1e3 * tt / args.fp64_steps, "steps": args.fp64_steps,
                 "warmup": args.fp64_warmup}
-        # density of the same samples in both precisions (sample k*world+rank)
-        rels = [abs(a - b) / b for a, b in zip(d_mixed, d64) if b > 0]
+        # density of the same samples in both precisions
+        rels = [abs(dens_by[("fp32_mixed", smp)] - v) / v for (p_, smp), v in dens_by.items()
+                if p_ == "fp64" and ("fp32_mixed", smp) in dens_by and v > 0]
         fp64["density_rel_diff_vs_fp32_mixed"] = max(rels) if rels else None
 
     # ---- end to end through the host-buffer entry point ----
@@ -355,8 +370,10 @@ def run_gpu(args):
 
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None
+    accuracy = None
     if not args.no_cpu_baseline:
-        cpu = cpu_baseline(cfgs[0], args.cpu_seconds, nsteps)
+        cpu, accuracy = cpu_baseline(cfgs[0], args.cpu_seconds, nsteps,
+                                     {p: m for (p, smp), m in kept.items() if smp == 0})
 
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -372,7 +389,7 @@ def run_gpu(args):
         "density_first_step": d_mixed[0] if d_mixed else None,
         "fp64": fp64, "e2e": e2e, "magnus4": magnus, "serving": serving, "small_grid": small,
         "gpu_launches": 2 * args.steps,
-        "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+        "roofline": roof, "cpu_baseline": cpu, "accuracy_vs_oracle": accuracy, "clocks": clocks,
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
     }
     print(json.dumps(line), flush=True)
@@ -508,6 +525,8 @@ def serving_leg(args, solve_rate, stream):
 # ------------------------------------------------------------------------------------------
 
 def oracle_rate(cfg, n_points, nsteps, seed=5):
+    """Times the oracle on n_points seeded points of the grid; returns
+    (spinor-steps/s, seconds, flat indices, |c+|^2 at those points)."""
     from oracle import oracle
     g = cfg["grid"]
     a_mid, a_in, a_out, dt = oracle.pulse_table(cfg["pulse"], nsteps)
@@ -515,20 +534,30 @@ def oracle_rate(cfg, n_points, nsteps, seed=5):
     xs = oracle.grid_nodes(*g["px"], g["nx"])
     ys = oracle.grid_nodes(*g["py"], g["ny"])
     t0 = time.perf_counter()
-    oracle.solve_points(xs[idx % g["nx"]], ys[idx // g["nx"]], a_mid, dt, a_in, a_out)
+    r = oracle.solve_points(xs[idx % g["nx"]], ys[idx // g["nx"]], a_mid, dt, a_in, a_out)
     el = time.perf_counter() - t0
-    return n_points * nsteps / el, el
+    return n_points * nsteps / el, el, idx, r["cplus2"]
 
 
-def cpu_baseline(cfg, seconds, nsteps):
+def cpu_baseline(cfg, seconds, nsteps, gpu_maps=None):
+    """The oracle as it stands on a seeded subset of the grid sized to ~`seconds`;
+    the same points also give the GPU maps' error against the FP64 oracle."""
     from oracle import oracle
     cores = oracle.max_threads()
-    rate, _ = oracle_rate(cfg, 256, nsteps)
+    rate = oracle_rate(cfg, 256, nsteps)[0]
     pts = int(max(256, min(cfg["grid"]["nx"] ** 2, rate * seconds / nsteps)))
-    rate, el = oracle_rate(cfg, pts, nsteps)
-    return {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"{pts} seeded points of the {cfg['grid']['nx']}^2 grid x {nsteps} steps "
-                      f"(sample 0), {el:.1f} s, FP64, OpenMP over points"}
+    rate, el, idx, ref = oracle_rate(cfg, pts, nsteps)
+    sample = (f"{pts} seeded points of the {cfg['grid']['nx']}^2 grid x {nsteps} steps "
+              f"(sample 0), {el:.1f} s, FP64, OpenMP over points")
+    base = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample}
+    acc = None
+    if gpu_maps:
+        acc = {"points": sample, "max_oracle_cplus2": float(ref.max())}
+        for prec, m in gpu_maps.items():
+            got = m.ravel()[idx]
+            acc[prec] = {"max_abs_err_cplus2": float(np.abs(got - ref).max()),
+                         "sampled_density_rel_err": float(abs(got.sum() - ref.sum()) / ref.sum())}
+    return base, acc
 
 
 def run_reference(args):
@@ -541,11 +570,11 @@ def run_reference(args):
     oracle.build()
     cores = oracle.max_threads()
     per_step_s = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    rate, _ = oracle_rate(cfg, 256, nsteps)
+    rate = oracle_rate(cfg, 256, nsteps)[0]
     pts = int(max(64, min(n * n, rate * per_step_s / nsteps)))
     times = []
     for k in range(args.warmup + args.steps):
-        r, el = oracle_rate(cfg, pts, nsteps, seed=100 + k)
+        el = oracle_rate(cfg, pts, nsteps, seed=100 + k)[1]
         if k >= args.warmup:
             times.append(el)
     tot = sum(times)

@@ -59,6 +59,7 @@ struct dsp_grid {
     double quant = 1, inv_quant = 1;
     int32_t level = 0;
     double theta_max = 0.0;
+    bool paired = false;  // FP32_MIXED EXACT with theta_max <= kPairThetaMax
     bool fresh = true;      // state not yet written on the device
     bool projected = false;  // partial sums valid for the current pulse
     dsp_status latched = DSP_OK;
@@ -179,6 +180,7 @@ ReqDesc make_desc(const dsp_grid *g, int64_t begin, int64_t end, bool project, v
     r.fresh = g->fresh ? 1 : 0;
     r.project = project ? 1 : 0;
     r.n_tiles = g->n_tiles;
+    r.paired = g->paired ? 1 : 0;
     return r;
 }
 
@@ -472,6 +474,8 @@ dsp_status prepare_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, doub
     g->inv_quant = 1.0 / quant;
     g->theta_max = tmax;
     g->level = choose_level(g->precision, tmax, n_steps);
+    g->paired = g->precision == DSP_FP32_MIXED && g->scheme == DSP_SCHEME_EXACT &&
+                tmax <= dsp::kPairThetaMax;
     g->fresh = true;
     g->projected = false;
     return DSP_OK;
@@ -846,6 +850,7 @@ dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info)
     info->n_steps = g->n_steps;
     info->cursor = g->cursor;
     info->n_tiles = g->n_tiles;
+    info->paired_steps = g->paired ? 1 : 0;
     info->dt = g->dt;
     info->theta_max = g->theta_max;
     info->quant = g->quant;

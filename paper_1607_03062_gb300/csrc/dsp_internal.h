@@ -59,7 +59,13 @@ struct ReqDesc {
     int32_t init_identity;  // with fresh: start from the column (1, 0) of the identity
                             // (the launch then computes the first column of the
                             // product of its steps' operators)
+    int32_t paired;  // FP32_MIXED EXACT: multiply steps (2j, 2j+1) before one update
+    int32_t pad;
 };
+
+// Step pairs are used when theta_max <= this: the pair's increment (U2 U1 - I) psi
+// stays small next to psi, where the compensated (Fast2Sum) update is exact.
+constexpr double kPairThetaMax = 0.1;
 
 struct EvolveArgs {
     int32_t nreq;

@@ -8,7 +8,8 @@
 //                                theta = dt |P_n|;
 //   Sec. II Eq. (pair_prod_homo) |c+|^2 = |u(p + A_out)^dag psi|^2, summed to n.
 //
-// GB300 design (one CTA = one tile of 1024 momenta; 512 threads x 2 spinors):
+// GB300 design (one CTA = one tile of 1024 momenta; FP32-mixed: 256 threads x 4
+// spinors, FP64: 512 threads x 2 spinors):
 //   * the spinors stay in registers across all steps of a launch: one 16-byte
 //     read and one write per spinor plane per launch;
 //   * A(t) is staged in shared memory in chunks of 1024 steps by 1-D bulk
@@ -20,9 +21,10 @@
 //     the working precision;
 //   * FP32_MIXED: dt*p and dt*A are split into hi + lo with every hi a multiple
 //     of 2^-k, so P_hi = p_hi + A_hi is exact in FP32 and the momentum is known
-//     to ~1e-16 relative; the spinor is stored as hi + lo and each step adds the
-//     increment (U - I) psi with a Fast2Sum, so the FP32 rounding of psi does
-//     not random-walk over 1e5 steps;
+//     to ~1e-16 relative; the spinor is stored as hi + lo and each update adds
+//     the increment (U - I) psi with a Fast2Sum, so the FP32 rounding of psi does
+//     not random-walk over 1e5 steps; the EXACT scheme multiplies two steps into
+//     one SU(2) matrix first, so the compensated update is paid once per pair;
 //   * the projection and the per-tile partial sums of |c+|^2 are fused into the
 //     last launch; partial sums use a fixed pairwise tree, so the density is
 //     bitwise reproducible and independent of the batch a request ran in.
@@ -229,6 +231,24 @@ __device__ __forceinline__ int find_request(const EvolveArgs &a)
 
 constexpr int kStageBytes = 16384;  // per stage; two stages per CTA
 
+// Tuning constants: unroll factor of the step-pair loop, and spinors per thread
+// of the FP32-mixed kernel (a CTA always owns one 1024-point tile).
+#ifndef DSP_PAIR_UNROLL
+#define DSP_PAIR_UNROLL 2
+#endif
+#ifndef DSP_MIXED_SPT
+#define DSP_MIXED_SPT 4
+#endif
+#ifndef DSP_MIXED_MINB
+#define DSP_MIXED_MINB 2
+#endif
+constexpr int kPairUnroll = DSP_PAIR_UNROLL;
+constexpr int kMixedSpt = DSP_MIXED_SPT;
+constexpr int kMixedThreads = kTilePoints / kMixedSpt;
+constexpr int kMixedMinBlocks = DSP_MIXED_MINB;  // resident CTAs per SM the registers allow
+constexpr int kF64Threads = kThreads;
+static_assert(kTilePoints % kMixedSpt == 0, "a CTA owns one whole tile");
+
 // MAGNUS4 table entries: the Gauss-point mean (dt*Abar, valley-signed) and the
 // commutator factor D = -(sqrt(3)/6) dt (A2 - A1) (valley-signed).
 struct MixedG2 {
@@ -297,6 +317,56 @@ __device__ __forceinline__ bool run_steps(const ReqDesc &R, unsigned char *smem,
 #pragma unroll 2
         for (int j = 0; j < len; ++j)
             step(tb[j]);  // shared-memory broadcast
+        __syncthreads();  // everyone is done with stage c & 1
+        if (threadIdx.x == 0 && c + 2 < st.nchunks)
+            st.issue(c + 2);
+    }
+    return true;
+}
+
+// As run_steps, but steps are taken in pairs (2j, 2j + 1) of ABSOLUTE step index
+// (a launch that starts or ends on an odd index takes that one step alone), so
+// any split of a run at even step indices meets the same pairs.  The stages hold
+// whole pairs: staging starts at the even index below step_begin and the stage
+// length is even.
+template <typename E, typename SingleFn, typename PairFn>
+__device__ __forceinline__ bool run_step_pairs(const ReqDesc &R, unsigned char *smem,
+                                               uint64_t *bars, int *err, SingleFn single,
+                                               PairFn pair)
+{
+    const int64_t b_even = R.step_begin & ~static_cast<int64_t>(1);
+    const bool odd_start = (R.step_begin & 1) != 0;
+    Stager<E> st{smem, bars, static_cast<const E *>(R.table) + b_even, R.step_end - b_even, 0};
+    if (R.step_end <= R.step_begin)
+        st.nsteps = 0;
+    static_assert(Stager<E>::kCh % 2 == 0, "stages must hold whole pairs");
+    st.nchunks = static_cast<int>((st.nsteps + Stager<E>::kCh - 1) / Stager<E>::kCh);
+    if (threadIdx.x == 0) {
+        if (st.nchunks > 0) st.issue(0);
+        if (st.nchunks > 1) st.issue(1);
+    }
+    for (int c = 0; c < st.nchunks; ++c) {
+        const bool ok = mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(err, kErrTimeout);
+                for (int k = 0; k < st.nchunks && k < 2; ++k)
+                    (void)mbar_wait_bounded(&bars[k & 1], 0);
+            }
+            return false;
+        }
+        const E *tb = st.stage(c);
+        const int len = st.chunk_len(c);
+        int j = 0;
+        if (c == 0 && odd_start) {  // entry 0 is the even step before step_begin
+            single(tb[1]);
+            j = 2;
+        }
+#pragma unroll kPairUnroll
+        for (; j + 1 < len; j += 2)
+            pair(tb[j], tb[j + 1]);
+        if (j < len)  // odd end (last stage only)
+            single(tb[j]);
         __syncthreads();  // everyone is done with stage c & 1
         if (threadIdx.x == 0 && c + 2 < st.nchunks)
             st.issue(c + 2);
@@ -389,11 +459,38 @@ __device__ __forceinline__ void step_mixed(MixedPoint &p, const float4 &a, float
     apply_f32<SCHEME>(p, cm1, qr, qi, qz);
 }
 
+// Two EXACT steps at once: with U_k = I + [[m_k, -q_k], [conj(q_k), m_k]],
+//   U_2 U_1 - I = [[al - 1, -Q], [conj(Q), conj(al) - 1]],
+//   al - 1 = m1 + m2 + m1 m2 - q2 conj(q1),  Q = q1 + q2 + m2 q1 + m1 q2,
+// applied with one compensated update (the product of two SU(2) steps is SU(2)).
+template <int DC, int DS>
+__device__ __forceinline__ void step_pair_mixed(MixedPoint &p, const float4 &a0, const float4 &a1)
+{
+    float m1, q1r, q1i, m2, q2r, q2i, z;
+    step_coeffs_f32<0, DC, DS>(p.pxh + a0.x, p.pxl + a0.y, p.pyh + a0.z, p.pyl + a0.w,
+                               make_float2(0.0f, 0.0f), m1, q1r, q1i, z);
+    step_coeffs_f32<0, DC, DS>(p.pxh + a1.x, p.pxl + a1.y, p.pyh + a1.z, p.pyl + a1.w,
+                               make_float2(0.0f, 0.0f), m2, q2r, q2i, z);
+    const float alm1 = fmaf(m1, m2, m1 + m2) - fmaf(q2r, q1r, q2i * q1i);
+    const float ali = fmaf(q2r, q1i, -(q2i * q1r));
+    const float Qr = fmaf(m2, q1r, q1r) + fmaf(m1, q2r, q2r);
+    const float Qi = fmaf(m2, q1i, q1i) + fmaf(m1, q2i, q2i);
+    const float dar = fmaf(alm1, p.ar, fmaf(-ali, p.ai, fmaf(-Qr, p.br, fmaf(Qi, p.bi, p.lar))));
+    const float dai = fmaf(alm1, p.ai, fmaf(ali, p.ar, fmaf(-Qr, p.bi, fmaf(-Qi, p.br, p.lai))));
+    const float dbr = fmaf(alm1, p.br, fmaf(ali, p.bi, fmaf(Qr, p.ar, fmaf(Qi, p.ai, p.lbr))));
+    const float dbi = fmaf(alm1, p.bi, fmaf(-ali, p.br, fmaf(Qr, p.ai, fmaf(-Qi, p.ar, p.lbi))));
+    float t;
+    t = p.ar + dar; p.lar = dar - (t - p.ar); p.ar = t;
+    t = p.ai + dai; p.lai = dai - (t - p.ai); p.ai = t;
+    t = p.br + dbr; p.lbr = dbr - (t - p.br); p.br = t;
+    t = p.bi + dbi; p.lbi = dbi - (t - p.bi); p.bi = t;
+}
+
 template <int SCHEME, int DC, int DS>
 __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint64_t *bars,
                            int *err)
 {
-    constexpr int S = kSpinorsPerThread;
+    constexpr int S = kMixedSpt;
     const int tid = threadIdx.x;
     const int64_t base = static_cast<int64_t>(tile) * kTilePoints;
     const double vs = R.valley > 0 ? 1.0 : -1.0;
@@ -403,7 +500,7 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
     MixedPoint pt[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        const int64_t idx = base + s * kThreads + tid;
+        const int64_t idx = base + s * kMixedThreads + tid;
         const bool valid = idx < R.n_points;
         double px = 0.0, py = 0.0;
         if (valid) {
@@ -437,7 +534,28 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
     }
 
     bool ok;
-    if constexpr (SCHEME == 2) {
+    if constexpr (SCHEME == 0) {
+        if (!R.paired) {
+            ok = run_steps<float4>(R, smem, bars, err, [&](const float4 &e) {
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+                    step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
+            });
+        } else {
+        ok = run_step_pairs<float4>(
+            R, smem, bars, err,
+            [&](const float4 &e) {
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+                    step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
+            },
+            [&](const float4 &e0, const float4 &e1) {
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+                    step_pair_mixed<DC, DS>(pt[s], e0, e1);
+            });
+        }
+    } else if constexpr (SCHEME == 2) {
         ok = run_steps<MixedG2>(R, smem, bars, err, [&](const MixedG2 &e) {
 #pragma unroll
             for (int s = 0; s < S; ++s)
@@ -456,7 +574,7 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
     double cp2[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        const int64_t idx = base + s * kThreads + tid;
+        const int64_t idx = base + s * kMixedThreads + tid;
         cp2[s] = 0.0;
         if (idx < R.n_points) {
             hi_plane[idx] = make_float4(pt[s].ar, pt[s].ai, pt[s].br, pt[s].bi);
@@ -478,7 +596,7 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
         double *red = reinterpret_cast<double *>(smem);  // the table stages are free now
 #pragma unroll
         for (int s = 0; s < S; ++s)
-            red[s * kThreads + tid] = cp2[s];
+            red[s * kMixedThreads + tid] = cp2[s];
         __syncthreads();
         const double sum = tile_tree_sum(red);
         if (tid == 0)
@@ -644,7 +762,7 @@ __device__ __forceinline__ void dispatch_f64(const ReqDesc &R, int tile, unsigne
 // Kernels
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kMixedThreads, kMixedMinBlocks)
     evolve_mixed_kernel(const __grid_constant__ EvolveArgs args)
 {
     __shared__ __align__(128) unsigned char smem[2 * kStageBytes];
@@ -777,9 +895,9 @@ cudaError_t launch_evolve(const EvolveArgs &args, int precision, cudaStream_t st
     if (args.nreq <= 0 || args.total_tiles <= 0)
         return cudaSuccess;
     if (precision == 1)
-        evolve_mixed_kernel<<<args.total_tiles, kThreads, 0, stream>>>(args);
+        evolve_mixed_kernel<<<args.total_tiles, kMixedThreads, 0, stream>>>(args);
     else
-        evolve_f64_kernel<<<args.total_tiles, kThreads, 0, stream>>>(args);
+        evolve_f64_kernel<<<args.total_tiles, kF64Threads, 0, stream>>>(args);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,38 @@
+"""The command-line entry point (GPU) and the benchmark's reference arm (CPU)."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_json_line():
+    """bench.py --impl reference times the FP64 oracle on a bounded sample."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0", "--grid", "128", "--time-steps", "200"],
+                         capture_output=True, text=True, timeout=300, check=True)
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["metric"] == "spinor-steps/s" and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+@pytest.mark.gpu
+def test_cli_solve_writes_map_and_density(tmp_path, orc):
+    from paper_1607_03062_gb300 import workloads as W
+    out_npy = tmp_path / "map.npy"
+    res = subprocess.run([sys.executable, "-m", "paper_1607_03062_gb300", "--workload", "sin2_64",
+                          "--precision", "fp64", "--out", str(out_npy)], cwd=ROOT,
+                         capture_output=True, text=True, timeout=300, check=True)
+    line = json.loads(res.stdout.strip().splitlines()[-1])
+    cfg = W.config_sin2_64()
+    g = cfg["grid"]
+    a_mid, a_in, a_out, dt = orc.pulse_table(cfg["pulse"], cfg["steps"])
+    ref, _, _, nref = orc.solve_grid(g["nx"], g["ny"], g["px"], g["py"], a_mid, dt, a_in, a_out)
+    m = np.load(out_npy)
+    assert np.abs(m - ref).max() <= 1e-9
+    assert abs(line["density_eV2"] - nref) <= 1e-10 * nref
