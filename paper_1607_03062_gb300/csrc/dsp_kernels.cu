@@ -242,10 +242,14 @@ constexpr int kStageBytes = 16384;  // per stage; two stages per CTA
 #ifndef DSP_MIXED_MINB
 #define DSP_MIXED_MINB 2
 #endif
+#ifndef DSP_PACKED_PAIRS
+#define DSP_PACKED_PAIRS 1
+#endif
 constexpr int kPairUnroll = DSP_PAIR_UNROLL;
 constexpr int kMixedSpt = DSP_MIXED_SPT;
 constexpr int kMixedThreads = kTilePoints / kMixedSpt;
 constexpr int kMixedMinBlocks = DSP_MIXED_MINB;  // resident CTAs per SM the registers allow
+constexpr bool kPackedPairs = DSP_PACKED_PAIRS != 0;  // FP32x2 form of the paired path
 constexpr int kF64Threads = kThreads;
 static_assert(kTilePoints % kMixedSpt == 0, "a CTA owns one whole tile");
 
@@ -486,6 +490,131 @@ __device__ __forceinline__ void step_pair_mixed(MixedPoint &p, const float4 &a0,
     t = p.bi + dbi; p.lbi = dbi - (t - p.bi); p.bi = t;
 }
 
+// ---------------------------------------------------------------------------
+// Packed FP32x2 form of the paired EXACT path: lane 0 and lane 1 of every
+// float2 belong to two different momenta, and every operation is the scalar
+// path's operation, in the same order, so each lane's result is bitwise the
+// scalar result (the packed instructions round each lane like the scalar ones).
+// One instruction then issues the arithmetic of two spinors.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <int D, int K, int ODD>
+__device__ __forceinline__ float2 horner2(float2 x)
+{
+    constexpr float c = static_cast<float>(((K & 1) ? -1.0 : 1.0) * inv_factorial<2 * K + ODD>());
+    if constexpr (K == D)
+        return bc2(c);
+    else
+        return fma2(horner2<D, K + 1, ODD>(x), x, bc2(c));
+}
+
+struct MixedPack {
+    float2 ar, ai, br, bi, lar, lai, lbr, lbi, pxh, pxl, pyh, pyl;
+};
+
+__device__ __forceinline__ MixedPack pack_points(const MixedPoint &u, const MixedPoint &v)
+{
+    MixedPack p;
+    p.ar = make_float2(u.ar, v.ar); p.ai = make_float2(u.ai, v.ai);
+    p.br = make_float2(u.br, v.br); p.bi = make_float2(u.bi, v.bi);
+    p.lar = make_float2(u.lar, v.lar); p.lai = make_float2(u.lai, v.lai);
+    p.lbr = make_float2(u.lbr, v.lbr); p.lbi = make_float2(u.lbi, v.lbi);
+    p.pxh = make_float2(u.pxh, v.pxh); p.pxl = make_float2(u.pxl, v.pxl);
+    p.pyh = make_float2(u.pyh, v.pyh); p.pyl = make_float2(u.pyl, v.pyl);
+    return p;
+}
+
+__device__ __forceinline__ void unpack_points(const MixedPack &p, MixedPoint &u, MixedPoint &v)
+{
+    u.ar = p.ar.x; v.ar = p.ar.y; u.ai = p.ai.x; v.ai = p.ai.y;
+    u.br = p.br.x; v.br = p.br.y; u.bi = p.bi.x; v.bi = p.bi.y;
+    u.lar = p.lar.x; v.lar = p.lar.y; u.lai = p.lai.x; v.lai = p.lai.y;
+    u.lbr = p.lbr.x; v.lbr = p.lbr.y; u.lbi = p.lbi.x; v.lbi = p.lbi.y;
+}
+
+// step_coeffs_f32<0> on two momenta at once
+template <int DC, int DS>
+__device__ __forceinline__ void coeffs_exact2(const MixedPack &p, const float4 &a, float2 &m,
+                                              float2 &qr, float2 &qi)
+{
+    const float2 Px = add2(add2(p.pxh, bc2(a.x)), add2(p.pxl, bc2(a.y)));
+    const float2 Py = add2(add2(p.pyh, bc2(a.z)), add2(p.pyl, bc2(a.w)));
+    const float2 x = fma2(Px, Px, mul2(Py, Py));
+    m = mul2(horner2<DC, 1, 0>(x), x);
+    const float2 sn = horner2<DS, 0, 1>(x);
+    qr = mul2(sn, Py);
+    qi = mul2(sn, Px);
+}
+
+// Compensated update psi <- psi + d, d = (M - I) psi_hi + psi_lo, for
+// M - I = [[am + i ai, -Q], [conj(Q), am - i ai]] (ai = 0 for one step).
+__device__ __forceinline__ void apply2(MixedPack &p, float2 am, float2 ai, float2 Qr, float2 Qi)
+{
+    const float2 nai = neg2(ai), nQr = neg2(Qr), nQi = neg2(Qi);
+    const float2 dar = fma2(am, p.ar, fma2(nai, p.ai, fma2(nQr, p.br, fma2(Qi, p.bi, p.lar))));
+    const float2 dai = fma2(am, p.ai, fma2(ai, p.ar, fma2(nQr, p.bi, fma2(nQi, p.br, p.lai))));
+    const float2 dbr = fma2(am, p.br, fma2(ai, p.bi, fma2(Qr, p.ar, fma2(Qi, p.ai, p.lbr))));
+    const float2 dbi = fma2(am, p.bi, fma2(nai, p.br, fma2(Qr, p.ai, fma2(nQi, p.ar, p.lbi))));
+    float2 t;
+    t = add2(p.ar, dar); p.lar = sub2(dar, sub2(t, p.ar)); p.ar = t;
+    t = add2(p.ai, dai); p.lai = sub2(dai, sub2(t, p.ai)); p.ai = t;
+    t = add2(p.br, dbr); p.lbr = sub2(dbr, sub2(t, p.br)); p.br = t;
+    t = add2(p.bi, dbi); p.lbi = sub2(dbi, sub2(t, p.bi)); p.bi = t;
+}
+
+// One EXACT step (apply_f32<0> with cm1 = m, q = (qr, qi)).
+template <int DC, int DS>
+__device__ __forceinline__ void step_exact2(MixedPack &p, const float4 &a)
+{
+    float2 m, qr, qi;
+    coeffs_exact2<DC, DS>(p, a, m, qr, qi);
+    const float2 nqr = neg2(qr), nqi = neg2(qi);
+    const float2 dar = fma2(m, p.ar, fma2(nqr, p.br, fma2(qi, p.bi, p.lar)));
+    const float2 dai = fma2(m, p.ai, fma2(nqr, p.bi, fma2(nqi, p.br, p.lai)));
+    const float2 dbr = fma2(m, p.br, fma2(qr, p.ar, fma2(qi, p.ai, p.lbr)));
+    const float2 dbi = fma2(m, p.bi, fma2(qr, p.ai, fma2(nqi, p.ar, p.lbi)));
+    float2 t;
+    t = add2(p.ar, dar); p.lar = sub2(dar, sub2(t, p.ar)); p.ar = t;
+    t = add2(p.ai, dai); p.lai = sub2(dai, sub2(t, p.ai)); p.ai = t;
+    t = add2(p.br, dbr); p.lbr = sub2(dbr, sub2(t, p.br)); p.br = t;
+    t = add2(p.bi, dbi); p.lbi = sub2(dbi, sub2(t, p.bi)); p.bi = t;
+}
+
+// One MAGNUS4 step (step_coeffs_f32<2> + apply_f32<2> on two momenta):
+// U - I = [[m - i qz, -q], [conj(q), m + i qz]].
+template <int DC, int DS>
+__device__ __forceinline__ void step_magnus2(MixedPack &p, const MixedG2 &e)
+{
+    const float2 Px = add2(add2(p.pxh, bc2(e.a.x)), add2(p.pxl, bc2(e.a.y)));
+    const float2 Py = add2(add2(p.pyh, bc2(e.a.z)), add2(p.pyl, bc2(e.a.w)));
+    const float2 nz = fma2(Px, bc2(e.d.y), neg2(mul2(Py, bc2(e.d.x))));
+    const float2 x = fma2(Px, Px, fma2(Py, Py, mul2(nz, nz)));
+    const float2 m = mul2(horner2<DC, 1, 0>(x), x);
+    const float2 sn = horner2<DS, 0, 1>(x);
+    apply2(p, m, neg2(mul2(sn, nz)), mul2(sn, Py), mul2(sn, Px));
+}
+
+// Two EXACT steps multiplied, then one update (step_pair_mixed on two momenta).
+template <int DC, int DS>
+__device__ __forceinline__ void step_pair2(MixedPack &p, const float4 &a0, const float4 &a1)
+{
+    float2 m1, q1r, q1i, m2, q2r, q2i;
+    coeffs_exact2<DC, DS>(p, a0, m1, q1r, q1i);
+    coeffs_exact2<DC, DS>(p, a1, m2, q2r, q2i);
+    const float2 alm1 = sub2(fma2(m1, m2, add2(m1, m2)), fma2(q2r, q1r, mul2(q2i, q1i)));
+    const float2 ali = fma2(q2r, q1i, neg2(mul2(q2i, q1r)));
+    const float2 Qr = add2(fma2(m2, q1r, q1r), fma2(m1, q2r, q2r));
+    const float2 Qi = add2(fma2(m2, q1i, q1i), fma2(m1, q2i, q2i));
+    apply2(p, alm1, ali, Qr, Qi);
+}
+
 template <int SCHEME, int DC, int DS>
 __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint64_t *bars,
                            int *err)
@@ -533,8 +662,42 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
         }
     }
 
+    constexpr bool packed = kPackedPairs && S % 2 == 0;
+    MixedPack pk[packed ? S / 2 : 1];
+    if constexpr (packed) {  // FP32x2: spinors (2k, 2k + 1) share each instruction
+#pragma unroll
+        for (int k = 0; k < S / 2; ++k)
+            pk[k] = pack_points(pt[2 * k], pt[2 * k + 1]);
+    }
     bool ok;
-    if constexpr (SCHEME == 0) {
+    if constexpr (SCHEME == 0 && packed) {
+        if (!R.paired) {
+            ok = run_steps<float4>(R, smem, bars, err, [&](const float4 &e) {
+#pragma unroll
+                for (int k = 0; k < S / 2; ++k)
+                    step_exact2<DC, DS>(pk[k], e);
+            });
+        } else {
+            ok = run_step_pairs<float4>(
+                R, smem, bars, err,
+                [&](const float4 &e) {
+#pragma unroll
+                    for (int k = 0; k < S / 2; ++k)
+                        step_exact2<DC, DS>(pk[k], e);
+                },
+                [&](const float4 &e0, const float4 &e1) {
+#pragma unroll
+                    for (int k = 0; k < S / 2; ++k)
+                        step_pair2<DC, DS>(pk[k], e0, e1);
+                });
+        }
+    } else if constexpr (SCHEME == 2 && packed) {
+        ok = run_steps<MixedG2>(R, smem, bars, err, [&](const MixedG2 &e) {
+#pragma unroll
+            for (int k = 0; k < S / 2; ++k)
+                step_magnus2<DC, DS>(pk[k], e);
+        });
+    } else if constexpr (SCHEME == 0) {
         if (!R.paired) {
             ok = run_steps<float4>(R, smem, bars, err, [&](const float4 &e) {
 #pragma unroll
@@ -542,18 +705,18 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
                     step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
             });
         } else {
-        ok = run_step_pairs<float4>(
-            R, smem, bars, err,
-            [&](const float4 &e) {
+            ok = run_step_pairs<float4>(
+                R, smem, bars, err,
+                [&](const float4 &e) {
 #pragma unroll
-                for (int s = 0; s < S; ++s)
-                    step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
-            },
-            [&](const float4 &e0, const float4 &e1) {
+                    for (int s = 0; s < S; ++s)
+                        step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
+                },
+                [&](const float4 &e0, const float4 &e1) {
 #pragma unroll
-                for (int s = 0; s < S; ++s)
-                    step_pair_mixed<DC, DS>(pt[s], e0, e1);
-            });
+                    for (int s = 0; s < S; ++s)
+                        step_pair_mixed<DC, DS>(pt[s], e0, e1);
+                });
         }
     } else if constexpr (SCHEME == 2) {
         ok = run_steps<MixedG2>(R, smem, bars, err, [&](const MixedG2 &e) {
@@ -567,6 +730,11 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
             for (int s = 0; s < S; ++s)
                 step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
         });
+    }
+    if constexpr (packed && SCHEME != 1) {
+#pragma unroll
+        for (int k = 0; k < S / 2; ++k)
+            unpack_points(pk[k], pt[2 * k], pt[2 * k + 1]);
     }
     if (!ok)
         return;

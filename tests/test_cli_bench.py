@@ -36,3 +36,23 @@ def test_cli_solve_writes_map_and_density(tmp_path, orc):
     m = np.load(out_npy)
     assert np.abs(m - ref).max() <= 1e-9
     assert abs(line["density_eV2"] - nref) <= 1e-10 * nref
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    """Launched like the N > 1 benchmark: rank 0 prints the only JSON line, the
+    other rank exits 0 without work."""
+    import socket
+    sock = socket.socket()
+    sock.bind(("127.0.0.1", 0))
+    port = sock.getsockname()[1]
+    sock.close()
+    out = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                          "--nproc-per-node", "2", "--master-addr", "127.0.0.1",
+                          "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                          "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
+                          "--grid", "64", "--time-steps", "100"],
+                         capture_output=True, text=True, timeout=300, check=True)
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
