@@ -461,9 +461,9 @@ int orc_solve_points(int64_t npts, const double *px, const double *py, int schem
     a.scheme = scheme;
     a.valley = valley;
 #ifdef _OPENMP
-    if (nthreads > 0)
-        omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 16)
+    /* a thread count for this call only (0: all of them) */
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
 #endif
     for (k = 0; k < npts; ++k)
         solve_point(&a, px[k], py[k], cplus2 ? cplus2 + k : NULL, cminus2 ? cminus2 + k : NULL,
