@@ -141,10 +141,13 @@ KERNEL_TRAFFIC = {
 
 
 def kernel_source_sha256():
+    """SHA-256 over the kernel sources (the .cu file and the descriptor header)."""
     import hashlib
-    path = os.path.join(ROOT, "paper_1607_03062_gb300", "csrc", "dsp_kernels.cu")
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    for name in ("dsp_kernels.cu", "dsp_internal.h"):
+        with open(os.path.join(ROOT, "paper_1607_03062_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def kernel_traffic(name):
@@ -524,7 +527,7 @@ def serving_leg(args, solve_rate, stream):
 # CPU oracle (baseline leg and reference arm)
 # ------------------------------------------------------------------------------------------
 
-def oracle_rate(cfg, n_points, nsteps, seed=5):
+def oracle_rate(cfg, n_points, nsteps, seed=5, nthreads=0):
     """Times the oracle on n_points seeded points of the grid; returns
     (spinor-steps/s, seconds, flat indices, |c+|^2 at those points)."""
     from oracle import oracle
@@ -534,7 +537,8 @@ def oracle_rate(cfg, n_points, nsteps, seed=5):
     xs = oracle.grid_nodes(*g["px"], g["nx"])
     ys = oracle.grid_nodes(*g["py"], g["ny"])
     t0 = time.perf_counter()
-    r = oracle.solve_points(xs[idx % g["nx"]], ys[idx // g["nx"]], a_mid, dt, a_in, a_out)
+    r = oracle.solve_points(xs[idx % g["nx"]], ys[idx // g["nx"]], a_mid, dt, a_in, a_out,
+                            nthreads=nthreads)
     el = time.perf_counter() - t0
     return n_points * nsteps / el, el, idx, r["cplus2"]
 
@@ -550,6 +554,9 @@ def cpu_baseline(cfg, seconds, nsteps, gpu_maps=None):
     sample = (f"{pts} seeded points of the {cfg['grid']['nx']}^2 grid x {nsteps} steps "
               f"(sample 0), {el:.1f} s, FP64, OpenMP over points")
     base = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample}
+    one = oracle_rate(cfg, 256, nsteps, seed=9, nthreads=1)
+    base["single_core"] = {"value": one[0], "unit": METRIC, "cores": 1,
+                           "sample": f"256 seeded points x {nsteps} steps, {one[1]:.1f} s"}
     acc = None
     if gpu_maps:
         acc = {"points": sample, "max_oracle_cplus2": float(ref.max())}

@@ -49,6 +49,8 @@ typedef int32_t dsp_status;
 #define DSP_E_STATE (-4)   /* call out of order (no pulse, steps past the end ...) */
 #define DSP_E_CFL (-5)     /* dt * max|p + A| > pi: the step condition of Sec. III */
 #define DSP_E_TIMEOUT (-6) /* a bounded device-side wait gave up (error flag set) */
+#define DSP_E_BOUNDS (-7)  /* an out-of-range device index, found only by a library
+                              built with -DDSP_BOUNDS_CHECK (accesses are skipped) */
 
 /* Arithmetic of the evolution. */
 #define DSP_FP64 0       /* everything in FP64                                      */
@@ -206,6 +208,15 @@ typedef struct {
     int32_t reserved;
 } dsp_grid_info;
 dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info);
+
+/* Test hook for the failure path (not in the paper).  The next launch on this
+ * grid announces its first A(t) chunk to the CTA's mbarrier but never copies
+ * it, so every CTA's bounded wait for it runs out (after about 2 s).  The CTA
+ * then sets the launch's error word and returns: nothing faults, traps or
+ * hangs, and the CUDA context stays usable.  The next synchronising call on
+ * the grid returns DSP_E_TIMEOUT, and the grid stays latched in that state.
+ * Use it on small grids: the waits of successive CTA waves add up. */
+dsp_status dsp_test_withhold_next_copy(dsp_grid *g);
 
 /* Copies the raw spinor state (dsp_state_bytes bytes) to the host, or back
  * from the host, with the step cursor, for checkpoint / resume.  Synchronise. */

@@ -29,7 +29,8 @@ PULSE_KINDS = {"zero": 0, "sin2": 1, "gauss": 2, "two_colour": 3, "const_field":
 REQ_STATES = {0: "queued", 1: "active", 2: "done", 3: "failed", 4: "cancelled"}
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory or over budget", -3: "CUDA error",
           -4: "call out of order", -5: "time step too large (dt*max|p+A| > pi)",
-          -6: "device-side wait timed out"}
+          -6: "device-side wait timed out",
+          -7: "out-of-range index found by a bounds-check build"}
 
 # Every entry point declared in include/dsp.h.
 EXPORTS = (
@@ -39,6 +40,7 @@ EXPORTS = (
     "dsp_sample_pulse", "dsp_server_create", "dsp_server_submit", "dsp_server_step",
     "dsp_server_query", "dsp_server_cancel", "dsp_server_destroy", "dsp_density_noalloc",
     "dsp_get_info", "dsp_solve_segmented", "dsp_sample_pulse_gauss",
+    "dsp_test_withhold_next_copy",
 )
 
 
@@ -75,7 +77,8 @@ class Request(ctypes.Structure):
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libdsp.so, or the variant named by DSP_LIBRARY (e.g. the bounds-check build)."""
+    return os.environ.get("DSP_LIBRARY") or _build.LIB
 
 
 def lib() -> ctypes.CDLL:
@@ -117,6 +120,7 @@ def lib() -> ctypes.CDLL:
                 "dsp_get_info": (i32, [p, ctypes.POINTER(GridInfo)]),
                 "dsp_solve_segmented": (i32, [p, i32, p, pd]),
                 "dsp_sample_pulse_gauss": (i32, [ctypes.POINTER(PulseSpec), i64, p, p, p, pd]),
+                "dsp_test_withhold_next_copy": (i32, [p]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -269,6 +273,12 @@ def density_noalloc(map_ptr: int, precision, nx: int, ny: int, px_range, py_rang
                                      ctypes.c_void_p(int(stream)), ctypes.byref(n)),
            "density_noalloc")
     return n.value
+
+
+def test_withhold_next_copy(h: int):
+    """Failure-path test hook: the next launch's first table chunk is never
+    copied, so its bounded device-side wait runs out (DSP_E_TIMEOUT)."""
+    _check(lib().dsp_test_withhold_next_copy(ctypes.c_void_p(h)), "test_withhold_next_copy")
 
 
 def status_string(code: int) -> str:

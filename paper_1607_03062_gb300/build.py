@@ -32,25 +32,33 @@ def sources() -> list[str]:
     return [os.path.join(CSRC, f) for f in ("dsp_kernels.cu", "dsp_api.cpp", "dsp_noalloc.cu")]
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + [os.path.join(CSRC, "dsp_internal.h"), os.path.join(INCLUDE, "dsp.h"),
                         os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link libdsp.so if any source is newer than it; returns its path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+BOUNDS_LIB = os.path.join(BUILD, "bounds_check", "libdsp.so")
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          bounds_check: bool = False) -> str:
+    """Compile and link libdsp.so if any source is newer than it; returns its path.
+
+    bounds_check=True builds the variant with -DDSP_BOUNDS_CHECK (device index
+    checks that flag DSP_E_BOUNDS instead of accessing) into _build/bounds_check/."""
+    lib = BOUNDS_LIB if bounds_check else LIB
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
     nvcc = _nvcc()
     objs, procs = [], []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, "-c", src, "-o", obj] + COMMON
+        obj = os.path.join(os.path.dirname(lib), os.path.basename(src) + ".o")
+        cmd = [nvcc, "-c", src, "-o", obj] + COMMON + (["-DDSP_BOUNDS_CHECK"] if bounds_check else [])
         if src.endswith(".cu"):
             cmd += ARCH + ["-lineinfo"]
             if ptxas_info:
@@ -68,11 +76,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write("failed: " + " ".join(cmd) + "\n")
     if failed:
         raise RuntimeError("building libdsp.so failed")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     link = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
     subprocess.run(link, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

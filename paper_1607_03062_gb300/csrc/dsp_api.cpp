@@ -7,6 +7,7 @@
 // queues work on the caller's CUDA stream.
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -27,6 +28,14 @@ using dsp::ReqDesc;
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
+
+// Named host-side range for timeline profilers (NVTX; free when none is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 struct DeviceScalars {
     double density;
@@ -60,6 +69,7 @@ struct dsp_grid {
     int32_t level = 0;
     double theta_max = 0.0;
     bool paired = false;  // FP32_MIXED EXACT with theta_max <= kPairThetaMax
+    bool withhold_next = false;  // test hook, see dsp_test_withhold_next_copy
     bool fresh = true;      // state not yet written on the device
     bool projected = false;  // partial sums valid for the current pulse
     dsp_status latched = DSP_OK;
@@ -181,6 +191,8 @@ ReqDesc make_desc(const dsp_grid *g, int64_t begin, int64_t end, bool project, v
     r.project = project ? 1 : 0;
     r.n_tiles = g->n_tiles;
     r.paired = g->paired ? 1 : 0;
+    r.withhold_first_copy = g->withhold_next ? 1 : 0;
+    r.table_steps = g->table_cap;
     return r;
 }
 
@@ -257,6 +269,10 @@ dsp_status read_scalars(dsp_grid *g, double *density)
     if (h.err & dsp::kErrTimeout) {
         g->latched = DSP_E_TIMEOUT;
         return DSP_E_TIMEOUT;
+    }
+    if (h.err & dsp::kErrBounds) {
+        g->latched = DSP_E_BOUNDS;
+        return DSP_E_BOUNDS;
     }
     if (density)
         *density = h.density;
@@ -521,6 +537,7 @@ dsp_status set_pulse_impl(dsp_grid *g, const double *a_mid, int64_t n_steps, dou
 dsp_status run_one(dsp_grid *g, int64_t end, bool project, void *map)
 {
     std::vector<ReqDesc> r(1, make_desc(g, g->cursor, end, project, map));
+    g->withhold_next = false;
     cudaError_t e = launch_requests(r, g->precision, &g->scal->err, g->stream);
     if (e != cudaSuccess)
         return latch_cuda(g, e);
@@ -575,6 +592,7 @@ dsp_status dsp_create_grid(int32_t nx, int32_t ny, double px_min, double px_max,
 dsp_status dsp_set_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, double dt,
                          const double a_in[2], const double a_out[2])
 {
+    Range range_("dsp_set_pulse");
     dsp_status s = check_usable(g);
     if (s != DSP_OK)
         return s;
@@ -583,6 +601,7 @@ dsp_status dsp_set_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, doub
 
 dsp_status dsp_evolve(dsp_grid *g, int64_t steps)
 {
+    Range range_("dsp_evolve");
     dsp_status s = check_usable(g);
     if (s != DSP_OK)
         return s;
@@ -598,6 +617,7 @@ dsp_status dsp_evolve(dsp_grid *g, int64_t steps)
 
 dsp_status dsp_project(dsp_grid *g, void *map_dev)
 {
+    Range range_("dsp_project");
     dsp_status s = check_usable(g);
     if (s != DSP_OK)
         return s;
@@ -610,6 +630,7 @@ dsp_status dsp_project(dsp_grid *g, void *map_dev)
 
 dsp_status dsp_reduce_density(dsp_grid *g, double *n_host)
 {
+    Range range_("dsp_reduce_density");
     dsp_status s = check_usable(g);
     if (s != DSP_OK)
         return s;
@@ -626,6 +647,7 @@ dsp_status dsp_reduce_density(dsp_grid *g, double *n_host)
 
 dsp_status dsp_solve(dsp_grid *g, void *map_dev, double *n_host)
 {
+    Range range_("dsp_solve");
     dsp_status s = check_usable(g);
     if (s != DSP_OK)
         return s;
@@ -651,6 +673,7 @@ dsp_status dsp_solve(dsp_grid *g, void *map_dev, double *n_host)
 
 dsp_status dsp_solve_segmented(dsp_grid *g, int32_t segments, void *map_dev, double *n_host)
 {
+    Range range_("dsp_solve_segmented");
     dsp_status s = check_usable(g);
     if (s != DSP_OK)
         return s;
@@ -781,6 +804,7 @@ dsp_status dsp_solve_host(dsp_grid *g, const double *a_mid, int64_t n_steps, dou
 
 dsp_status dsp_evolve_batch(dsp_grid *const *grids, const int64_t *steps, int32_t count)
 {
+    Range range_("dsp_evolve_batch");
     if (count < 0 || (count > 0 && (!grids || !steps)))
         return DSP_E_INVALID;
     if (count == 0)
@@ -830,6 +854,15 @@ dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps)
         return DSP_E_INVALID;
     *cursor = g->cursor;
     *n_steps = g->n_steps;
+    return DSP_OK;
+}
+
+dsp_status dsp_test_withhold_next_copy(dsp_grid *g)
+{
+    dsp_status s = check_usable(g);
+    if (s != DSP_OK)
+        return s;
+    g->withhold_next = true;
     return DSP_OK;
 }
 
@@ -925,6 +958,7 @@ const char *dsp_status_string(dsp_status s)
     case DSP_E_STATE: return "call out of order";
     case DSP_E_CFL: return "time step too large: dt * max|p + A| > pi";
     case DSP_E_TIMEOUT: return "device-side wait timed out";
+    case DSP_E_BOUNDS: return "out-of-range index found by a bounds-check build";
     default: return "unknown status";
     }
 }
@@ -1349,6 +1383,7 @@ dsp_status dsp_server_submit(dsp_server *s, const dsp_request *req, const double
 dsp_status dsp_server_step(dsp_server *s, int32_t *n_active, int32_t *n_queued,
                            int32_t *n_finished)
 {
+    Range range_("dsp_server_step");
     if (!s)
         return DSP_E_INVALID;
     if (s->latched != DSP_OK)
@@ -1365,20 +1400,23 @@ dsp_status dsp_server_step(dsp_server *s, int32_t *n_active, int32_t *n_queued,
         s->queue.swap(q);
     }
     // 2. admit FIFO while the footprint fits and a slot is free
-    while (!s->queue.empty() && static_cast<int32_t>(s->active.size()) < s->max_active) {
-        ServerReq *r = s->reqs[s->queue.front()].get();
-        if (s->used + footprint_of(r->p) > s->budget)
-            break;
-        s->queue.pop_front();
-        dsp_status st = server_admit(s, r);
-        if (s->latched != DSP_OK)
-            return s->latched;
-        if (st != DSP_OK) {
-            r->state = DSP_REQ_FAILED;
-            std::vector<double>().swap(r->a_mid);
-            continue;
+    {
+        Range admit_range_("server admit");
+        while (!s->queue.empty() && static_cast<int32_t>(s->active.size()) < s->max_active) {
+            ServerReq *r = s->reqs[s->queue.front()].get();
+            if (s->used + footprint_of(r->p) > s->budget)
+                break;
+            s->queue.pop_front();
+            dsp_status st = server_admit(s, r);
+            if (s->latched != DSP_OK)
+                return s->latched;
+            if (st != DSP_OK) {
+                r->state = DSP_REQ_FAILED;
+                std::vector<double>().swap(r->a_mid);
+                continue;
+            }
+            s->active.push_back(r->id);
         }
-        s->active.push_back(r->id);
     }
     // 3. iteration k: one batched launch per precision over the running requests
     bool queued_any = false;
@@ -1438,6 +1476,8 @@ dsp_status dsp_server_step(dsp_server *s, int32_t *n_active, int32_t *n_queued,
             return server_fail(s, DSP_E_CUDA);
         if (*s->err_host & dsp::kErrTimeout)
             return server_fail(s, DSP_E_TIMEOUT);
+        if (*s->err_host & dsp::kErrBounds)
+            return server_fail(s, DSP_E_BOUNDS);
         std::vector<int64_t> keep;
         for (int64_t id : s->active) {
             ServerReq *r = s->reqs[id].get();

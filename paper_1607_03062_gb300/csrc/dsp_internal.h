@@ -14,10 +14,12 @@ constexpr int kTilePoints = 1024;
 // Spinors per thread (independent momenta advanced together for ILP).
 constexpr int kSpinorsPerThread = 2;
 constexpr int kThreads = kTilePoints / kSpinorsPerThread;
-// Requests one evolve launch can carry in its parameter block.
-constexpr int kMaxReqPerLaunch = 48;
+// Requests one evolve launch can carry in its parameter block (96 x 192 bytes:
+// within the 32 KB kernel-parameter limit).
+constexpr int kMaxReqPerLaunch = 96;
 // Device-side error bits (the launch's error word).
 constexpr int kErrTimeout = 1;
+constexpr int kErrBounds = 2;  // only set by builds with -DDSP_BOUNDS_CHECK
 // Bound on one mbarrier wait, in nanoseconds of %globaltimer.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
@@ -60,12 +62,16 @@ struct ReqDesc {
                             // (the launch then computes the first column of the
                             // product of its steps' operators)
     int32_t paired;  // FP32_MIXED EXACT: multiply steps (2j, 2j+1) before one update
-    int32_t pad;
+    int32_t withhold_first_copy;  // test hook: announce chunk 0 but never copy it, so the
+                                  // bounded wait for it runs out (no fault, no hang)
+    int64_t table_steps;          // entries in the table (checked by bounds-check builds)
 };
 
 // Step pairs are used when theta_max <= this: the pair's increment (U2 U1 - I) psi
 // stays small next to psi, where the compensated (Fast2Sum) update is exact.
 constexpr double kPairThetaMax = 0.1;
+
+static_assert(sizeof(ReqDesc) * kMaxReqPerLaunch + 64 < 32764, "kernel parameter limit");
 
 struct EvolveArgs {
     int32_t nreq;

@@ -264,6 +264,41 @@ struct F64G2 {
     double2 d;  // D
 };
 
+// Bounds-check builds (-DDSP_BOUNDS_CHECK) verify, uniformly per CTA, that the
+// table entries a launch stages, [first, step_end), lie inside the table; a bad
+// range sets kErrBounds and the launch does nothing.  Otherwise a no-op.
+__device__ __forceinline__ bool table_range_ok(const ReqDesc &R, int64_t first, int *err)
+{
+#ifdef DSP_BOUNDS_CHECK
+    const bool ok = first >= 0 && R.step_end >= R.step_begin &&
+                    (R.step_end == R.step_begin || R.step_end <= R.table_steps);
+    if (!ok && threadIdx.x == 0)
+        atomicOr(err, kErrBounds);
+    return ok;
+#else
+    (void)R;
+    (void)first;
+    (void)err;
+    return true;
+#endif
+}
+
+// Bounds-check builds verify a CTA's tile index; a bad one sets kErrBounds.
+__device__ __forceinline__ bool tile_ok(const ReqDesc &R, int tile, int *err)
+{
+#ifdef DSP_BOUNDS_CHECK
+    const bool ok = tile >= 0 && tile < R.n_tiles;
+    if (!ok && threadIdx.x == 0)
+        atomicOr(err, kErrBounds);
+    return ok;
+#else
+    (void)R;
+    (void)tile;
+    (void)err;
+    return true;
+#endif
+}
+
 template <typename E>
 struct Stager {
     unsigned char *smem;
@@ -271,6 +306,7 @@ struct Stager {
     const E *table;  // entry step_begin is element 0 of chunk 0
     int64_t nsteps;
     int nchunks;
+    int withhold_first = 0;  // test hook (ReqDesc::withhold_first_copy)
     static constexpr int kCh = kStageBytes / static_cast<int>(sizeof(E));
 
     __device__ __forceinline__ const E *stage(int c) const
@@ -286,8 +322,18 @@ struct Stager {
     {
         const uint32_t bytes = static_cast<uint32_t>(chunk_len(c)) * sizeof(E);
         mbar_arrive_expect_tx(&bars[c & 1], bytes);
+        if (c == 0 && withhold_first)
+            return;  // the phase cannot complete: its waiters time out
         bulk_load(smem + (c & 1) * kStageBytes, table + static_cast<int64_t>(c) * kCh, bytes,
                   &bars[c & 1]);
+    }
+    // After the wait for chunk c timed out (one thread): flags the error and gives
+    // the copy of chunk c + 1, if it was issued, a bounded chance to land first.
+    __device__ __forceinline__ void on_timeout(int c, int *err) const
+    {
+        atomicOr(err, kErrTimeout);
+        if (c + 1 < nchunks)
+            (void)mbar_wait_bounded(&bars[(c + 1) & 1], ((c + 1) >> 1) & 1);
     }
 };
 
@@ -298,8 +344,11 @@ template <typename E, typename StepFn>
 __device__ __forceinline__ bool run_steps(const ReqDesc &R, unsigned char *smem, uint64_t *bars,
                                           int *err, StepFn step)
 {
+    if (!table_range_ok(R, R.step_begin, err))
+        return false;
     Stager<E> st{smem, bars, static_cast<const E *>(R.table) + R.step_begin,
                  R.step_end - R.step_begin, 0};
+    st.withhold_first = R.withhold_first_copy;
     st.nchunks = static_cast<int>((st.nsteps + Stager<E>::kCh - 1) / Stager<E>::kCh);
     if (threadIdx.x == 0) {
         if (st.nchunks > 0) st.issue(0);
@@ -308,12 +357,8 @@ __device__ __forceinline__ bool run_steps(const ReqDesc &R, unsigned char *smem,
     for (int c = 0; c < st.nchunks; ++c) {
         const bool ok = mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1);
         if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) {
-                atomicOr(err, kErrTimeout);
-                // give copies still in flight a bounded chance to land before exit
-                for (int k = 0; k < st.nchunks && k < 2; ++k)
-                    (void)mbar_wait_bounded(&bars[k & 1], 0);
-            }
+            if (threadIdx.x == 0)
+                st.on_timeout(c, err);
             return false;
         }
         const E *tb = st.stage(c);
@@ -340,7 +385,10 @@ __device__ __forceinline__ bool run_step_pairs(const ReqDesc &R, unsigned char *
 {
     const int64_t b_even = R.step_begin & ~static_cast<int64_t>(1);
     const bool odd_start = (R.step_begin & 1) != 0;
+    if (!table_range_ok(R, b_even, err))
+        return false;
     Stager<E> st{smem, bars, static_cast<const E *>(R.table) + b_even, R.step_end - b_even, 0};
+    st.withhold_first = R.withhold_first_copy;
     if (R.step_end <= R.step_begin)
         st.nsteps = 0;
     static_assert(Stager<E>::kCh % 2 == 0, "stages must hold whole pairs");
@@ -352,11 +400,8 @@ __device__ __forceinline__ bool run_step_pairs(const ReqDesc &R, unsigned char *
     for (int c = 0; c < st.nchunks; ++c) {
         const bool ok = mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1);
         if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) {
-                atomicOr(err, kErrTimeout);
-                for (int k = 0; k < st.nchunks && k < 2; ++k)
-                    (void)mbar_wait_bounded(&bars[k & 1], 0);
-            }
+            if (threadIdx.x == 0)
+                st.on_timeout(c, err);
             return false;
         }
         const E *tb = st.stage(c);
@@ -944,6 +989,8 @@ __global__ void __launch_bounds__(kMixedThreads, kMixedMinBlocks)
     const int r = find_request(args);
     const ReqDesc &R = args.r[r];
     const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
+    if (!tile_ok(R, tile, args.err))
+        return;
     if (R.scheme == 0)
         dispatch_mixed<0, 0>(R, tile, smem, bars, args.err);
     else if (R.scheme == 1)
@@ -966,6 +1013,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r = find_request(args);
     const ReqDesc &R = args.r[r];
     const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
+    if (!tile_ok(R, tile, args.err))
+        return;
     if (R.scheme == 0)
         dispatch_f64<0, 0>(R, tile, smem, bars, args.err);
     else if (R.scheme == 1)

@@ -371,3 +371,27 @@ def test_magnus4_segmented_and_served(orc, prec):
     B.server_destroy(srv)
     assert state == "done" and dens_s == n_alone
     assert np.array_equal(out.astype(np.float64), m_alone)
+
+
+def test_device_wait_timeout_is_reported_and_context_survives():
+    """A launch whose first A(t) chunk is never copied: every CTA's bounded
+    mbarrier wait runs out, the kernel flags it and returns; the host reports
+    DSP_E_TIMEOUT and the CUDA context keeps working for a fresh grid."""
+    import time
+    grid = {"nx": 32, "ny": 32, "px": (-2, 2), "py": (-2, 2)}  # one CTA
+    tab = B.sample_pulse(W.sin2_pulse(1.0, 1.55, 2.0), 3000)
+    g = B.Grid(32, 32, grid["px"], grid["py"], "fp32_mixed")
+    g.set_pulse(tab[0], tab[3], tab[1], tab[2])
+    B.test_withhold_next_copy(g.h)
+    t0 = time.perf_counter()
+    with pytest.raises(B.DSPError) as e:
+        g.solve()
+    assert e.value.code == -6
+    assert time.perf_counter() - t0 < 30.0
+    with pytest.raises(B.DSPError) as e:  # the grid stays latched
+        g.evolve(0)
+    assert e.value.code == -6
+    g.close()
+    torch.cuda.synchronize()  # the context is fine
+    m, n = run_gpu(grid, tab, "fp32_mixed")
+    assert np.isfinite(n) and n > 0
