@@ -135,7 +135,7 @@ class ClockSampler:
 # SHA-256 of the kernel source the counters were taken on; a different source
 # means the counters are stale and the traffic is reported as null.
 KERNEL_TRAFFIC = {
-    "evolve_mixed_kernel": {"bytes": 109.78e6, "source_sha256": "61a3a72a01332f57f91f8449f365895a5e8ab606279a9eb481d96c9b738e57e7",
+    "evolve_mixed_kernel": {"bytes": 108.94e6, "source_sha256": "b0f591836df081cf529d5f9436608f742c9b10bc1699d4f31ff37f547d67d23c",
                             "profile": "profiles/evolve_mixed_lzs2048_1e5_traffic.md"},
 }
 
