@@ -360,6 +360,7 @@ def run_gpu(args):
             "traffic": kernel_traffic("evolve_mixed_kernel"), "kernel": "evolve_mixed_kernel",
             "ops_per_spinor_step": o_mixed,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts x max SM clock)"}
+    roof["ceiling_spinor_steps_per_s"] = peak * 1e12 / statistics.mean(o_mixed)
     if clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (SMS * FP32_LANES_PER_SM *
                                                      clocks["sm_mhz"] * 1e6 / 1e12)
@@ -381,7 +382,9 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (compensated hi/lo; FP64 set-up)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "arithmetic": "FP32 spinor stored compensated (hi + lo); momentum p + A as exact FP32 hi/lo "
+                      "pairs; FP64 initial state, projection and density",
         "data": "synthetic (seeded pulses; no dataset)",
         "config": {"workload": f"lzs_scan_{n}x{n}_{nsteps}_steps_fp32_mixed",
                    "grid": [n, n], "p_range_eV": [-10, 10], "time_steps": nsteps,
