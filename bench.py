@@ -174,17 +174,27 @@ def load_peaks():
 #   cos(theta) - 1 (Horner, dc - 1 FMA + 1 MUL)                dc
 #   sin(theta)/theta (Horner)                                  ds
 #   q = sinc * (P_y + i P_x)                                   2
-# per PAIR of steps (the two operators multiplied, then one compensated update):
+# per PAIR of steps (G = 2: the two operators multiplied, then one compensated update):
 #   U2 U1 - I: al - 1 (5), Im al (2), Q (6)                    13
 #   (U2 U1 - I) psi_hi + psi_lo                                16
 #   Fast2Sum of the 4 components                               12
 # i.e. 30.5 + dc + ds per spinor-step.
+# per GROUP of G = 4 or 8 steps (same per-step coefficients, with sin/theta - 1 and
+# q = P + (sinc - 1) P):
+#   alpha = 1 + m1 (1), second step (9), 12 per further step   10 + 12 (G - 2)
+#   Re alpha - 1 rebuilt from unitarity (one Newton step)       8
+#   update and Fast2Sum as above                                28
+# i.e. 22 + dc + ds + 22/G per spinor-step.  Single steps (G = 1): 34 + dc + ds.
 # FP64 instructions per spinor-step of the FP64 EXACT step:
 #   P (2) + theta^2 (2) + cos (dc) + sinc (ds) + q (2) + U psi (12)
 # ------------------------------------------------------------------------------------------
 
-def ops_mixed(dc, ds, paired=True):
-    return (30.5 if paired else 34) + dc + ds
+def ops_mixed(dc, ds, group=2):
+    if group == 1:
+        return 34 + dc + ds
+    if group == 2:
+        return 30.5 + dc + ds
+    return 22 + dc + ds + 22.0 / group
 
 
 def ops_fp64(dc, ds):
@@ -265,7 +275,7 @@ def run_gpu(args):
                     ops.append(ops_fp64(info["cos_degree"], info["sinc_degree"]))
                 else:
                     ops.append(ops_mixed(info["cos_degree"], info["sinc_degree"],
-                                         bool(info["paired_steps"])))
+                                         info["group_steps"]))
         B.destroy_grid(h)
         del state, mp
         return times, dens, ops

@@ -107,11 +107,11 @@ dsp_status dsp_set_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, doub
 /* Advances every point by `steps` time steps (Sec. III, Eq. (ev_op_dt)) from
  * the cursor; steps >= 0 and cursor + steps <= n_steps, else DSP_E_STATE.
  * The spinors stay on the device.  Evolving in pieces gives bitwise the same
- * state as evolving at once when every piece ends on an even step count: with
- * paired steps (dsp_get_info) the steps (2j, 2j + 1) are multiplied into one
- * operator before the compensated update, and a piece boundary at an odd step
- * splits such a pair, which changes rounding only.  Without paired steps any
- * split is bitwise invariant.  Asynchronous. */
+ * state as evolving at once when every piece ends on a multiple of 8 steps:
+ * with grouped steps (group_steps G > 1 in dsp_get_info) the steps
+ * (G j, ..., G j + G - 1) are multiplied into one operator before the
+ * compensated update, and a piece boundary inside such a group changes
+ * rounding only.  With G = 1 any split is bitwise invariant.  Asynchronous. */
 dsp_status dsp_evolve(dsp_grid *g, int64_t steps);
 
 /* Projects psi(t_f) on u(p + A_out) (Sec. II, Eq. (pair_prod_homo)) and writes
@@ -195,16 +195,19 @@ dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps);
  * the cos(theta) and sin(theta)/theta series used per step (picked so their
  * truncation error over all n_steps stays below 2e-8 in FP32_MIXED, 1e-16 in
  * FP64), theta_max = dt * max|p + A_n| over the box, the hi/lo grid 2^k of the
- * FP32_MIXED momentum split, the tile count, and whether steps are taken in
- * pairs (FP32_MIXED EXACT with theta_max <= 0.1: two step operators
- * multiplied, then one compensated update). */
+ * FP32_MIXED momentum split, the tile count, and group_steps G: the number of
+ * step operators multiplied into one before each compensated update
+ * (FP32_MIXED EXACT: the largest of 8, 4, 2 with G * theta_max <= 0.2, else 1;
+ * 1 for the other precisions and schemes).  Not in the paper: with G > 1 the
+ * update is paid once per group, and the group's Re(alpha) - 1 is rebuilt from
+ * unitarity, so the applied operator stays unitary to FP32 rounding. */
 typedef struct {
     int32_t nx, ny, precision, scheme, valley;
     int32_t cos_degree, sinc_degree;
     int32_t n_tiles;
     int64_t n_steps, cursor;
     double dt, theta_max, quant;
-    int32_t paired_steps;
+    int32_t group_steps;
     int32_t reserved;
 } dsp_grid_info;
 dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info);
@@ -292,8 +295,9 @@ typedef struct {
 
 /* hbm_budget_bytes > 0: admission limit on the sum of device footprints
  * (state + table + map + partial sums) of the active requests; max_active
- * >= 1; chunk_steps >= 1: steps per batched launch (keep it even: a request's
- * result is then bitwise the same alone or in any mix, see dsp_evolve).
+ * >= 1; chunk_steps >= 1: steps per batched launch, rounded down to a multiple
+ * of 8 when it is 8 or more (a request's result is then bitwise the same alone
+ * or in any mix, see dsp_evolve).
  * cuda_stream as above. */
 dsp_status dsp_server_create(int64_t hbm_budget_bytes, int32_t max_active, int64_t chunk_steps,
                              void *cuda_stream, dsp_server **out);

@@ -61,7 +61,7 @@ class GridInfo(ctypes.Structure):
                                               "cos_degree", "sinc_degree", "n_tiles")] + [
         ("n_steps", ctypes.c_int64), ("cursor", ctypes.c_int64), ("dt", ctypes.c_double),
         ("theta_max", ctypes.c_double), ("quant", ctypes.c_double),
-        ("paired_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+        ("group_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):

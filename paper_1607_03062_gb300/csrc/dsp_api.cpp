@@ -68,7 +68,7 @@ struct dsp_grid {
     double quant = 1, inv_quant = 1;
     int32_t level = 0;
     double theta_max = 0.0;
-    bool paired = false;  // FP32_MIXED EXACT with theta_max <= kPairThetaMax
+    int32_t group = 1;  // FP32_MIXED EXACT: steps multiplied per update (choose_group)
     bool withhold_next = false;  // test hook, see dsp_test_withhold_next_copy
     bool fresh = true;      // state not yet written on the device
     bool projected = false;  // partial sums valid for the current pulse
@@ -117,6 +117,19 @@ int32_t choose_level(int32_t precision, double theta, int64_t n_steps)
             return i;
     }
     return dsp::kNumLevels - 1;
+}
+
+// Steps multiplied into one operator before each compensated update (FP32_MIXED
+// EXACT only): the largest G in {kGroupMax, 4, 2} whose group rotation G *
+// theta_max stays within kGroupAngleMax, else 1.
+int32_t choose_group(int32_t precision, int32_t scheme, double theta_max)
+{
+    if (precision != DSP_FP32_MIXED || scheme != DSP_SCHEME_EXACT)
+        return 1;
+    for (int32_t G = dsp::kGroupMax; G >= 2; G /= 2)
+        if (G * theta_max <= dsp::kGroupAngleMax)
+            return G;
+    return 1;
 }
 
 double box_abs_max(const dsp_grid *g)
@@ -190,7 +203,7 @@ ReqDesc make_desc(const dsp_grid *g, int64_t begin, int64_t end, bool project, v
     r.fresh = g->fresh ? 1 : 0;
     r.project = project ? 1 : 0;
     r.n_tiles = g->n_tiles;
-    r.paired = g->paired ? 1 : 0;
+    r.group = g->group;
     r.withhold_first_copy = g->withhold_next ? 1 : 0;
     r.table_steps = g->table_cap;
     return r;
@@ -490,8 +503,7 @@ dsp_status prepare_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, doub
     g->inv_quant = 1.0 / quant;
     g->theta_max = tmax;
     g->level = choose_level(g->precision, tmax, n_steps);
-    g->paired = g->precision == DSP_FP32_MIXED && g->scheme == DSP_SCHEME_EXACT &&
-                tmax <= dsp::kPairThetaMax;
+    g->group = choose_group(g->precision, g->scheme, tmax);
     g->fresh = true;
     g->projected = false;
     return DSP_OK;
@@ -883,7 +895,7 @@ dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info)
     info->n_steps = g->n_steps;
     info->cursor = g->cursor;
     info->n_tiles = g->n_tiles;
-    info->paired_steps = g->paired ? 1 : 0;
+    info->group_steps = g->group;
     info->dt = g->dt;
     info->theta_max = g->theta_max;
     info->quant = g->quant;
@@ -1298,7 +1310,9 @@ dsp_status dsp_server_create(int64_t hbm_budget_bytes, int32_t max_active, int64
         return DSP_E_NOMEM;
     s->budget = hbm_budget_bytes;
     s->max_active = max_active;
-    s->chunk = chunk_steps;
+    // whole step groups per launch, so a request meets the same groups alone or in a mix
+    s->chunk = chunk_steps >= dsp::kGroupMax
+                   ? chunk_steps - chunk_steps % dsp::kGroupMax : chunk_steps;
     s->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess)

@@ -61,15 +61,19 @@ struct ReqDesc {
     int32_t init_identity;  // with fresh: start from the column (1, 0) of the identity
                             // (the launch then computes the first column of the
                             // product of its steps' operators)
-    int32_t paired;  // FP32_MIXED EXACT: multiply steps (2j, 2j+1) before one update
+    int32_t group;   // FP32_MIXED EXACT: the steps (G j, ..., G j + G - 1) of absolute index
+                     // are multiplied into one operator before one compensated update;
+                     // G = 1 (every step alone), 2, 4 or kGroupMax
     int32_t withhold_first_copy;  // test hook: announce chunk 0 but never copy it, so the
                                   // bounded wait for it runs out (no fault, no hang)
     int64_t table_steps;          // entries in the table (checked by bounds-check builds)
 };
 
-// Step pairs are used when theta_max <= this: the pair's increment (U2 U1 - I) psi
-// stays small next to psi, where the compensated (Fast2Sum) update is exact.
-constexpr double kPairThetaMax = 0.1;
+// Steps are grouped (G = 8, 4 or 2, the largest allowed) when G * theta_max <=
+// kGroupAngleMax: the group's increment (U_G ... U_1 - I) psi then stays small
+// next to psi, where the compensated (Fast2Sum) update is exact.
+constexpr int kGroupMax = 8;
+constexpr double kGroupAngleMax = 0.2;
 
 static_assert(sizeof(ReqDesc) * kMaxReqPerLaunch + 64 < 32764, "kernel parameter limit");
 

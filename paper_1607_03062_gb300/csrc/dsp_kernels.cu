@@ -23,8 +23,9 @@
 //     of 2^-k, so P_hi = p_hi + A_hi is exact in FP32 and the momentum is known
 //     to ~1e-16 relative; the spinor is stored as hi + lo and each update adds
 //     the increment (U - I) psi with a Fast2Sum, so the FP32 rounding of psi does
-//     not random-walk over 1e5 steps; the EXACT scheme multiplies two steps into
-//     one SU(2) matrix first, so the compensated update is paid once per pair;
+//     not random-walk over 1e5 steps; the EXACT scheme multiplies 2, 4 or 8
+//     steps into one SU(2) matrix first, so the compensated update is paid once
+//     per group;
 //   * the projection and the per-tile partial sums of |c+|^2 are fused into the
 //     last launch; partial sums use a fixed pairwise tree, so the density is
 //     bitwise reproducible and independent of the batch a request ran in.
@@ -231,8 +232,10 @@ __device__ __forceinline__ int find_request(const EvolveArgs &a)
 
 constexpr int kStageBytes = 16384;  // per stage; two stages per CTA
 
-// Tuning constants: unroll factor of the step-pair loop, and spinors per thread
-// of the FP32-mixed kernel (a CTA always owns one 1024-point tile).
+// Tuning constants: unroll factors of the step-pair loop and of the chain inside
+// a step group (measured fastest fully unrolled, although ptxas then keeps a few
+// values in local memory), and spinors per thread of the FP32-mixed kernel (a CTA
+// always owns one 1024-point tile).
 #ifndef DSP_PAIR_UNROLL
 #define DSP_PAIR_UNROLL 2
 #endif
@@ -245,7 +248,11 @@ constexpr int kStageBytes = 16384;  // per stage; two stages per CTA
 #ifndef DSP_PACKED_PAIRS
 #define DSP_PACKED_PAIRS 1
 #endif
+#ifndef DSP_GROUP_UNROLL
+#define DSP_GROUP_UNROLL 8
+#endif
 constexpr int kPairUnroll = DSP_PAIR_UNROLL;
+constexpr int kGroupUnroll = DSP_GROUP_UNROLL;  // chain loop inside one group (>= G - 2: whole)
 constexpr int kMixedSpt = DSP_MIXED_SPT;
 constexpr int kMixedThreads = kTilePoints / kMixedSpt;
 constexpr int kMixedMinBlocks = DSP_MIXED_MINB;  // resident CTAs per SM the registers allow
@@ -373,25 +380,26 @@ __device__ __forceinline__ bool run_steps(const ReqDesc &R, unsigned char *smem,
     return true;
 }
 
-// As run_steps, but steps are taken in pairs (2j, 2j + 1) of ABSOLUTE step index
-// (a launch that starts or ends on an odd index takes that one step alone), so
-// any split of a run at even step indices meets the same pairs.  The stages hold
-// whole pairs: staging starts at the even index below step_begin and the stage
-// length is even.
-template <typename E, typename SingleFn, typename PairFn>
-__device__ __forceinline__ bool run_step_pairs(const ReqDesc &R, unsigned char *smem,
-                                               uint64_t *bars, int *err, SingleFn single,
-                                               PairFn pair)
+// As run_steps, but steps are taken in groups (G j, ..., G j + G - 1) of ABSOLUTE
+// step index (a launch that starts or ends inside a group takes those steps one
+// by one), so any split of a run at multiples of G meets the same groups.  The
+// stages hold whole groups: staging starts at the multiple of G at or below
+// step_begin and the stage length is a multiple of G.  GROUP is called as
+// group(e) with e the group's G consecutive entries in shared memory.
+template <typename E, int G, typename SingleFn, typename GroupFn>
+__device__ __forceinline__ bool run_step_groups(const ReqDesc &R, unsigned char *smem,
+                                                uint64_t *bars, int *err, SingleFn single,
+                                                GroupFn group)
 {
-    const int64_t b_even = R.step_begin & ~static_cast<int64_t>(1);
-    const bool odd_start = (R.step_begin & 1) != 0;
-    if (!table_range_ok(R, b_even, err))
+    static_assert(G >= 2 && (G & (G - 1)) == 0, "group size: a power of two");
+    static_assert(Stager<E>::kCh % G == 0, "stages must hold whole groups");
+    const int64_t b_al = R.step_begin & ~static_cast<int64_t>(G - 1);
+    if (!table_range_ok(R, b_al, err))
         return false;
-    Stager<E> st{smem, bars, static_cast<const E *>(R.table) + b_even, R.step_end - b_even, 0};
+    Stager<E> st{smem, bars, static_cast<const E *>(R.table) + b_al, R.step_end - b_al, 0};
     st.withhold_first = R.withhold_first_copy;
     if (R.step_end <= R.step_begin)
         st.nsteps = 0;
-    static_assert(Stager<E>::kCh % 2 == 0, "stages must hold whole pairs");
     st.nchunks = static_cast<int>((st.nsteps + Stager<E>::kCh - 1) / Stager<E>::kCh);
     if (threadIdx.x == 0) {
         if (st.nchunks > 0) st.issue(0);
@@ -406,15 +414,20 @@ __device__ __forceinline__ bool run_step_pairs(const ReqDesc &R, unsigned char *
         }
         const E *tb = st.stage(c);
         const int len = st.chunk_len(c);
-        int j = 0;
-        if (c == 0 && odd_start) {  // entry 0 is the even step before step_begin
-            single(tb[1]);
-            j = 2;
-        }
+        // entries before step_begin - b_al belong to earlier launches
+        int j = c == 0 ? static_cast<int>(R.step_begin - b_al) : 0;
+        for (; j < len && (j & (G - 1)) != 0; ++j)  // ragged start
+            single(tb[j]);
+        if constexpr (G == 2) {
 #pragma unroll kPairUnroll
-        for (; j + 1 < len; j += 2)
-            pair(tb[j], tb[j + 1]);
-        if (j < len)  // odd end (last stage only)
+            for (; j + G <= len; j += G)
+                group(tb + j);
+        } else {
+#pragma unroll 1
+            for (; j + G <= len; j += G)
+                group(tb + j);
+        }
+        for (; j < len; ++j)  // ragged end (last stage only)
             single(tb[j]);
         __syncthreads();  // everyone is done with stage c & 1
         if (threadIdx.x == 0 && c + 2 < st.nchunks)
@@ -660,6 +673,122 @@ __device__ __forceinline__ void step_pair2(MixedPack &p, const float4 &a0, const
     apply2(p, alm1, ali, Qr, Qi);
 }
 
+// ---------------------------------------------------------------------------
+// Groups of G EXACT steps (G = 4, 8), written once for one momentum (V = float,
+// MixedPoint) and for two (V = float2, MixedPack) with non-contracting
+// intrinsics, so both forms perform the same roundings.
+//
+// The product U_k ... U_1 = [[alpha, -Q], [conj(Q), conj(alpha)]] is carried as
+// (Re alpha, Im alpha, Q).  With U_k = [[1 + m, -q], [conj(q), 1 + m]],
+// m = cos(theta_k) - 1, q = sin(theta_k)/theta_k (dt P_y + i dt P_x):
+//   alpha' = alpha + m alpha - q conj(Q),   Q' = Q + m Q + q conj(alpha).
+// No coefficient of the form 1 + (small) is ever rounded: cos(theta) enters as
+// X + m X and sin(theta)/theta as P + (sinc - 1) P, both accurate to the
+// rounding of the small part.  (Rounding cos(theta) itself to FP32 next to 1
+// errs by up to 3e-8 absolute, the same for every step while theta barely
+// changes, and the step angle then carries a relative bias of that size, which
+// grows along the whole evolution.)  Re alpha is held near 1, where FP32
+// resolves it only to ~6e-8; Re alpha - 1 is rebuilt at the end of the group
+// from the other three entries and unitarity, (1 + am)^2 + ai^2 + |Q|^2 = 1, by
+// one Newton step, so the operator applied is unitary to the rounding of its
+// entries.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return add2(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return mul2(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return fma2(a, b, c); }
+__device__ __forceinline__ float2 vneg(float2 a) { return neg2(a); }
+template <typename V>
+__device__ __forceinline__ V vbc(float v);
+template <>
+__device__ __forceinline__ float vbc<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float2 vbc<float2>(float v) { return bc2(v); }
+
+template <typename V, int D, int K, int ODD>
+__device__ __forceinline__ V vhorner(V x)
+{
+    constexpr float c = static_cast<float>(((K & 1) ? -1.0 : 1.0) * inv_factorial<2 * K + ODD>());
+    if constexpr (K == D)
+        return vbc<V>(c);
+    else
+        return vfma(vhorner<V, D, K + 1, ODD>(x), x, vbc<V>(c));
+}
+
+// m = cos(theta) - 1 and q = (qr, qi) of one EXACT step at dt P = dt p + table
+// entry a, with q = P + (sinc - 1) P.
+template <int DC, int DS, typename Pt, typename V>
+__device__ __forceinline__ void coeffs_group(const Pt &p, const float4 &a, V &m, V &qr, V &qi)
+{
+    const V Px = vadd(vadd(p.pxh, vbc<V>(a.x)), vadd(p.pxl, vbc<V>(a.y)));
+    const V Py = vadd(vadd(p.pyh, vbc<V>(a.z)), vadd(p.pyl, vbc<V>(a.w)));
+    const V x = vfma(Px, Px, vmul(Py, Py));
+    m = vmul(vhorner<V, DC, 1, 0>(x), x);
+    const V s1 = vmul(vhorner<V, DS, 1, 1>(x), x);  // sin(theta)/theta - 1
+    qr = vfma(s1, Py, Py);
+    qi = vfma(s1, Px, Px);
+}
+
+// Compensated update psi <- psi + d, d = (M - I) psi_hi + psi_lo, for
+// M - I = [[am + i ai, -Q], [conj(Q), am - i ai]]: the operations of apply2.
+template <typename Pt, typename V>
+__device__ __forceinline__ void apply_group(Pt &p, V am, V ai, V Qr, V Qi)
+{
+    const V nai = vneg(ai), nQr = vneg(Qr), nQi = vneg(Qi);
+    const V dar = vfma(am, p.ar, vfma(nai, p.ai, vfma(nQr, p.br, vfma(Qi, p.bi, p.lar))));
+    const V dai = vfma(am, p.ai, vfma(ai, p.ar, vfma(nQr, p.bi, vfma(nQi, p.br, p.lai))));
+    const V dbr = vfma(am, p.br, vfma(ai, p.bi, vfma(Qr, p.ar, vfma(Qi, p.ai, p.lbr))));
+    const V dbi = vfma(am, p.bi, vfma(nai, p.br, vfma(Qr, p.ai, vfma(nQi, p.ar, p.lbi))));
+    V t;
+    t = vadd(p.ar, dar); p.lar = vadd(dar, vneg(vadd(t, vneg(p.ar)))); p.ar = t;
+    t = vadd(p.ai, dai); p.lai = vadd(dai, vneg(vadd(t, vneg(p.ai)))); p.ai = t;
+    t = vadd(p.br, dbr); p.lbr = vadd(dbr, vneg(vadd(t, vneg(p.br)))); p.br = t;
+    t = vadd(p.bi, dbi); p.lbi = vadd(dbi, vneg(vadd(t, vneg(p.bi)))); p.bi = t;
+}
+
+// The chain, one step k >= 2 at a time (the second step, with Im alpha still 0,
+// drops its terms):
+//   Re alpha' = Re alpha + m Re alpha - (qr Qr + qi Qi)
+//   Im alpha' = Im alpha + m Im alpha - (qi Qr - qr Qi)
+//   Qr'       = Qr + m Qr + qr Re alpha + qi Im alpha
+//   Qi'       = Qi + m Qi + qi Re alpha - qr Im alpha
+template <int G, int DC, int DS, typename Pt>
+__device__ __forceinline__ void step_group(Pt &p, const float4 *e)
+{
+    using V = decltype(p.ar);
+    V m, qr, qi, Qr, Qi;
+    coeffs_group<DC, DS>(p, e[0], m, Qr, Qi);
+    V Ar = vadd(m, vbc<V>(1.0f));
+    coeffs_group<DC, DS>(p, e[1], m, qr, qi);
+    V ai = vfma(vneg(qi), Qr, vmul(qr, Qi));
+    V nAr = vfma(m, Ar, vfma(vneg(qr), Qr, vfma(vneg(qi), Qi, Ar)));
+    V nQr = vfma(m, Qr, vfma(qr, Ar, Qr));
+    V nQi = vfma(m, Qi, vfma(qi, Ar, Qi));
+    Ar = nAr;
+    Qr = nQr;
+    Qi = nQi;
+#pragma unroll kGroupUnroll
+    for (int k = 2; k < G; ++k) {
+        coeffs_group<DC, DS>(p, e[k], m, qr, qi);
+        nAr = vfma(m, Ar, vfma(vneg(qr), Qr, vfma(vneg(qi), Qi, Ar)));
+        const V nai = vfma(m, ai, vfma(vneg(qi), Qr, vfma(qr, Qi, ai)));
+        nQr = vfma(m, Qr, vfma(qr, Ar, vfma(qi, ai, Qr)));
+        nQi = vfma(m, Qi, vfma(qi, Ar, vfma(vneg(qr), ai, Qi)));
+        Ar = nAr;
+        ai = nai;
+        Qr = nQr;
+        Qi = nQi;
+    }
+    V am = vadd(Ar, vbc<V>(-1.0f));  // exact: Re alpha is within [1/2, 2]
+    const V u = vfma(am, am, vfma(Qi, Qi, vfma(Qr, Qr, vfma(ai, ai, vadd(am, am)))));
+    am = vfma(vneg(u), vfma(vbc<V>(-0.5f), am, vbc<V>(0.5f)), am);  // am -= u / (2 (1 + am))
+    apply_group(p, am, ai, Qr, Qi);
+}
+
 template <int SCHEME, int DC, int DS>
 __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint64_t *bars,
                            int *err)
@@ -716,25 +845,32 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
     }
     bool ok;
     if constexpr (SCHEME == 0 && packed) {
-        if (!R.paired) {
-            ok = run_steps<float4>(R, smem, bars, err, [&](const float4 &e) {
+        const auto single = [&](const float4 &e) {
+#pragma unroll
+            for (int k = 0; k < S / 2; ++k)
+                step_exact2<DC, DS>(pk[k], e);
+        };
+        if (R.group == kGroupMax) {
+            ok = run_step_groups<float4, kGroupMax>(R, smem, bars, err, single,
+                                                    [&](const float4 *e) {
 #pragma unroll
                 for (int k = 0; k < S / 2; ++k)
-                    step_exact2<DC, DS>(pk[k], e);
+                    step_group<kGroupMax, DC, DS>(pk[k], e);
+            });
+        } else if (R.group == 4) {
+            ok = run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
+#pragma unroll
+                for (int k = 0; k < S / 2; ++k)
+                    step_group<4, DC, DS>(pk[k], e);
+            });
+        } else if (R.group == 2) {
+            ok = run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
+#pragma unroll
+                for (int k = 0; k < S / 2; ++k)
+                    step_pair2<DC, DS>(pk[k], e[0], e[1]);
             });
         } else {
-            ok = run_step_pairs<float4>(
-                R, smem, bars, err,
-                [&](const float4 &e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_exact2<DC, DS>(pk[k], e);
-                },
-                [&](const float4 &e0, const float4 &e1) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_pair2<DC, DS>(pk[k], e0, e1);
-                });
+            ok = run_steps<float4>(R, smem, bars, err, single);
         }
     } else if constexpr (SCHEME == 2 && packed) {
         ok = run_steps<MixedG2>(R, smem, bars, err, [&](const MixedG2 &e) {
@@ -743,25 +879,32 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
                 step_magnus2<DC, DS>(pk[k], e);
         });
     } else if constexpr (SCHEME == 0) {
-        if (!R.paired) {
-            ok = run_steps<float4>(R, smem, bars, err, [&](const float4 &e) {
+        const auto single = [&](const float4 &e) {
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+                step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
+        };
+        if (R.group == kGroupMax) {
+            ok = run_step_groups<float4, kGroupMax>(R, smem, bars, err, single,
+                                                    [&](const float4 *e) {
 #pragma unroll
                 for (int s = 0; s < S; ++s)
-                    step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
+                    step_group<kGroupMax, DC, DS>(pt[s], e);
+            });
+        } else if (R.group == 4) {
+            ok = run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+                    step_group<4, DC, DS>(pt[s], e);
+            });
+        } else if (R.group == 2) {
+            ok = run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+                    step_pair_mixed<DC, DS>(pt[s], e[0], e[1]);
             });
         } else {
-            ok = run_step_pairs<float4>(
-                R, smem, bars, err,
-                [&](const float4 &e) {
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
-                },
-                [&](const float4 &e0, const float4 &e1) {
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        step_pair_mixed<DC, DS>(pt[s], e0, e1);
-                });
+            ok = run_steps<float4>(R, smem, bars, err, single);
         }
     } else if constexpr (SCHEME == 2) {
         ok = run_steps<MixedG2>(R, smem, bars, err, [&](const MixedG2 &e) {
