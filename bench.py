@@ -135,7 +135,7 @@ class ClockSampler:
 # SHA-256 of the kernel source the counters were taken on; a different source
 # means the counters are stale and the traffic is reported as null.
 KERNEL_TRAFFIC = {
-    "evolve_mixed_kernel": {"bytes": 108.94e6, "source_sha256": "b0f591836df081cf529d5f9436608f742c9b10bc1699d4f31ff37f547d67d23c",
+    "evolve_mixed_kernel": {"bytes": 109.14e6, "source_sha256": "e7946a5864b2ceeae2d27b738eac51a4f72c082c047d66e89cde73c98c1d09e2",
                             "profile": "profiles/evolve_mixed_lzs2048_1e5_traffic.md"},
 }
 
