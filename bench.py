@@ -169,7 +169,7 @@ def load_peaks():
 # ------------------------------------------------------------------------------------------
 # FP32 lane instructions of the FP32-mixed EXACT path, with series degrees dc (cos) and
 # ds (sin/theta) as the library reports them.  Per step:
-#   P_h = p_h + A_h, P_l = p_l + A_l, P = P_h + P_l (x and y)   6
+#   P = (p_h + A) + p_l (x and y)                               4
 #   theta^2 = fma(Px, Px, Py*Py)                               2
 #   cos(theta) - 1 (Horner, dc - 1 FMA + 1 MUL)                dc
 #   sin(theta)/theta (Horner)                                  ds
@@ -178,23 +178,23 @@ def load_peaks():
 #   U2 U1 - I: al - 1 (5), Im al (2), Q (6)                    13
 #   (U2 U1 - I) psi_hi + psi_lo                                16
 #   Fast2Sum of the 4 components                               12
-# i.e. 30.5 + dc + ds per spinor-step.
+# i.e. 28.5 + dc + ds per spinor-step.
 # per GROUP of G = 4 or 8 steps (same per-step coefficients, with sin/theta - 1 and
 # q = P + (sinc - 1) P):
 #   alpha = 1 + m1 (1), second step (9), 12 per further step   10 + 12 (G - 2)
 #   Re alpha - 1 rebuilt from unitarity (one Newton step)       8
 #   update and Fast2Sum as above                                28
-# i.e. 22 + dc + ds + 22/G per spinor-step.  Single steps (G = 1): 34 + dc + ds.
+# i.e. 20 + dc + ds + 22/G per spinor-step.  Single steps (G = 1): 32 + dc + ds.
 # FP64 instructions per spinor-step of the FP64 EXACT step:
 #   P (2) + theta^2 (2) + cos (dc) + sinc (ds) + q (2) + U psi (12)
 # ------------------------------------------------------------------------------------------
 
 def ops_mixed(dc, ds, group=2):
     if group == 1:
-        return 34 + dc + ds
+        return 32 + dc + ds
     if group == 2:
-        return 30.5 + dc + ds
-    return 22 + dc + ds + 22.0 / group
+        return 28.5 + dc + ds
+    return 20 + dc + ds + 22.0 / group
 
 
 def ops_fp64(dc, ds):
@@ -421,8 +421,8 @@ def run_gpu(args):
 def magnus4_leg(args, cfgs, stream, world, rank, warm=1, reps=2):
     """The same 2048^2 x 1e5-step solves with the fourth-order Magnus step
     (two Gauss-point samples per step), FP32-mixed.  Its instructions per
-    spinor-step: 6 (Pbar) + 2 (n_z) + 3 (|n|^2) + dc + ds + 3 (q, q_z) + 16
-    ((U - I) psi + lo) + 12 (Fast2Sum) = 42 + dc + ds."""
+    spinor-step: 4 (Pbar) + 2 (n_z) + 3 (|n|^2) + dc + ds + 3 (q, q_z) + 16
+    ((U - I) psi + lo) + 12 (Fast2Sum) = 40 + dc + ds."""
     import torch
 
     from paper_1607_03062_gb300 import binding as B
@@ -449,7 +449,7 @@ def magnus4_leg(args, cfgs, stream, world, rank, warm=1, reps=2):
         if k >= warm:
             times.append(e0.elapsed_time(e1) / 1e3)
             info = B.get_info(h)
-            ops.append(42 + info["cos_degree"] + info["sinc_degree"])
+            ops.append(40 + info["cos_degree"] + info["sinc_degree"])
     B.destroy_grid(h)
     work = float(n) * n * args.time_steps
     achieved = statistics.mean(o * work / t for o, t in zip(ops, times)) / 1e12

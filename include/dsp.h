@@ -54,9 +54,10 @@ typedef int32_t dsp_status;
 
 /* Arithmetic of the evolution. */
 #define DSP_FP64 0       /* everything in FP64                                      */
-#define DSP_FP32_MIXED 1 /* spinor in compensated FP32 (hi + lo), momentum P = p + A
-                            as exact FP32 hi/lo pairs, cos/sin of the phase argument
-                            dt|P| in FP32; initial state and projection in FP64     */
+#define DSP_FP32_MIXED 1 /* spinor in compensated FP32 (hi + lo); dt P_n formed as
+                            (dt p_hi + dt A_n) + dt p_lo with dt p an FP32 hi/lo
+                            pair; cos/sin of the phase argument dt|P| in FP32;
+                            initial state and projection in FP64                   */
 
 /* Time-step scheme. */
 #define DSP_SCHEME_EXACT 0     /* the paper's closed-form exponential (Sec. III)    */
@@ -194,8 +195,8 @@ dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps);
 /* What the library chose for the current pulse: the degrees (in theta^2) of
  * the cos(theta) and sin(theta)/theta series used per step (picked so their
  * truncation error over all n_steps stays below 2e-8 in FP32_MIXED, 1e-16 in
- * FP64), theta_max = dt * max|p + A_n| over the box, the hi/lo grid 2^k of the
- * FP32_MIXED momentum split, the tile count, and group_steps G: the number of
+ * FP64), theta_max = dt * max|p + A_n| over the box, the tile count, and
+ * group_steps G: the number of
  * step operators multiplied into one before each compensated update
  * (FP32_MIXED EXACT: the largest of 8, 4, 2 with G * theta_max <= 0.2, else 1;
  * 1 for the other precisions and schemes).  Not in the paper: with G > 1 the
@@ -206,7 +207,7 @@ typedef struct {
     int32_t cos_degree, sinc_degree;
     int32_t n_tiles;
     int64_t n_steps, cursor;
-    double dt, theta_max, quant;
+    double dt, theta_max;
     int32_t group_steps;
     int32_t reserved;
 } dsp_grid_info;

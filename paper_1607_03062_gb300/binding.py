@@ -60,7 +60,7 @@ class GridInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("nx", "ny", "precision", "scheme", "valley",
                                               "cos_degree", "sinc_degree", "n_tiles")] + [
         ("n_steps", ctypes.c_int64), ("cursor", ctypes.c_int64), ("dt", ctypes.c_double),
-        ("theta_max", ctypes.c_double), ("quant", ctypes.c_double),
+        ("theta_max", ctypes.c_double),
         ("group_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 

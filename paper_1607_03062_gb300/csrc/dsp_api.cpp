@@ -65,7 +65,6 @@ struct dsp_grid {
     bool has_pulse = false;
     int64_t n_steps = 0, cursor = 0;
     double dt = 0, a_in[2] = {0, 0}, a_out[2] = {0, 0};
-    double quant = 1, inv_quant = 1;
     int32_t level = 0;
     double theta_max = 0.0;
     int32_t group = 1;  // FP32_MIXED EXACT: steps multiplied per update (choose_group)
@@ -151,21 +150,6 @@ double theta_max(const dsp_grid *g, const double *a_mid, int64_t n, double dt)
     return dt * m;
 }
 
-// 2^k such that hi parts (multiples of 2^-k) of dt*p and dt*A, and their sum,
-// are exact in FP32: |hi| <= B and |sum| < 2B + 2^-k < 2^(24-k).
-double choose_quant(const dsp_grid *g, const double *a_mid, int64_t n, double dt)
-{
-    double b = box_abs_max(g);
-    for (int64_t k = 0; k < 2 * n; ++k)
-        b = std::max(b, std::fabs(a_mid[k]));
-    b *= dt;
-    if (!(b > 0.0))
-        return 1.0;
-    int e = 0;
-    (void)std::frexp(2.0 * b, &e);  // 2b < 2^e
-    return std::ldexp(1.0, 23 - e);
-}
-
 dsp_status check_usable(const dsp_grid *g)
 {
     if (!g)
@@ -190,8 +174,6 @@ ReqDesc make_desc(const dsp_grid *g, int64_t begin, int64_t end, bool project, v
     r.a_in[1] = g->a_in[1];
     r.a_out[0] = g->a_out[0];
     r.a_out[1] = g->a_out[1];
-    r.quant = g->quant;
-    r.inv_quant = g->inv_quant;
     r.n_points = g->n_points;
     r.step_begin = begin;
     r.step_end = end;
@@ -333,14 +315,25 @@ dsp_status validate_pulse_args(const dsp_grid *g, const double *a_mid, int64_t n
 // or two (at the Gauss points) for MAGNUS4.
 int samples_per_step(int32_t scheme) { return scheme == DSP_SCHEME_MAGNUS4 ? 2 : 1; }
 
-// Bytes per step of the device table.
-size_t entry_bytes(int32_t scheme) { return 16 * static_cast<size_t>(samples_per_step(scheme)); }
+// Bytes per step of the device table: per A sample, double2 (FP64) or float2
+// (FP32_MIXED).
+size_t entry_bytes(int32_t precision, int32_t scheme)
+{
+    return (precision == DSP_FP64 ? 16 : 8) * static_cast<size_t>(samples_per_step(scheme));
+}
+
+// Device bytes of a table of n steps: padded to 16 bytes, because the kernels
+// stage it with 1-D bulk copies that start and end on 16-byte boundaries.
+size_t table_bytes(int32_t precision, int32_t scheme, int64_t n)
+{
+    return (entry_bytes(precision, scheme) * static_cast<size_t>(n) + 15) & ~static_cast<size_t>(15);
+}
 
 // Fills the table layout the kernels read (see ReqDesc::table).
-void build_table(const dsp_grid *g, const double *a_mid, int64_t n, double dt, double quant,
-                 double inv_quant, std::vector<unsigned char> &out)
+void build_table(const dsp_grid *g, const double *a_mid, int64_t n, double dt,
+                 std::vector<unsigned char> &out)
 {
-    out.resize(static_cast<size_t>(n) * entry_bytes(g->scheme));
+    out.resize(static_cast<size_t>(n) * entry_bytes(g->precision, g->scheme));
     // valley K- is stepped as K+ on -P, so its table holds -dt*A
     const double vs = g->valley > 0 ? 1.0 : -1.0;
     if (g->scheme == DSP_SCHEME_MAGNUS4) {
@@ -359,17 +352,11 @@ void build_table(const dsp_grid *g, const double *a_mid, int64_t n, double dt, d
                 t[2] = dx;
                 t[3] = dy;
             } else {
-                float *t = reinterpret_cast<float *>(out.data()) + 8 * k;
-                const double hx = std::rint(bx * quant) * inv_quant;
-                const double hy = std::rint(by * quant) * inv_quant;
-                t[0] = static_cast<float>(hx);
-                t[1] = static_cast<float>(bx - hx);
-                t[2] = static_cast<float>(hy);
-                t[3] = static_cast<float>(by - hy);
-                t[4] = static_cast<float>(dx);
-                t[5] = static_cast<float>(dy);
-                t[6] = 0.0f;
-                t[7] = 0.0f;
+                float *t = reinterpret_cast<float *>(out.data()) + 4 * k;
+                t[0] = static_cast<float>(bx);
+                t[1] = static_cast<float>(by);
+                t[2] = static_cast<float>(dx);
+                t[3] = static_cast<float>(dy);
             }
         }
         return;
@@ -382,14 +369,8 @@ void build_table(const dsp_grid *g, const double *a_mid, int64_t n, double dt, d
         }
     } else {
         float *t = reinterpret_cast<float *>(out.data());
-        for (int64_t k = 0; k < n; ++k) {
-            for (int c = 0; c < 2; ++c) {
-                const double v = vs * (dt * a_mid[2 * k + c]);
-                const double hi = std::rint(v * quant) * inv_quant;
-                t[4 * k + 2 * c] = static_cast<float>(hi);
-                t[4 * k + 2 * c + 1] = static_cast<float>(v - hi);
-            }
-        }
+        for (int64_t k = 0; k < 2 * n; ++k)
+            t[k] = static_cast<float>(vs * (dt * a_mid[k]));
     }
 }
 
@@ -489,8 +470,7 @@ dsp_status prepare_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, doub
     if (s != DSP_OK)
         return s;
     const double tmax = n_steps > 0 ? theta_max(g, a_mid, n_samples, dt) : 0.0;
-    const double quant = n_steps > 0 ? choose_quant(g, a_mid, n_samples, dt) : 1.0;
-    build_table(g, a_mid, n_steps, dt, quant, 1.0 / quant, host);
+    build_table(g, a_mid, n_steps, dt, host);
     g->has_pulse = true;
     g->n_steps = n_steps;
     g->cursor = 0;
@@ -499,8 +479,6 @@ dsp_status prepare_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, doub
     g->a_in[1] = a_in[1];
     g->a_out[0] = a_out[0];
     g->a_out[1] = a_out[1];
-    g->quant = quant;
-    g->inv_quant = 1.0 / quant;
     g->theta_max = tmax;
     g->level = choose_level(g->precision, tmax, n_steps);
     g->group = choose_group(g->precision, g->scheme, tmax);
@@ -527,7 +505,7 @@ dsp_status set_pulse_impl(dsp_grid *g, const double *a_mid, int64_t n_steps, dou
             g->table_cap = 0;
         }
         if (e == cudaSuccess)
-            e = cudaMalloc(&g->table, static_cast<size_t>(n_steps) * entry_bytes(g->scheme));
+            e = cudaMalloc(&g->table, table_bytes(g->precision, g->scheme, n_steps));
         if (e != cudaSuccess) {
             cudaGetLastError();
             return e == cudaErrorMemoryAllocation ? DSP_E_NOMEM : latch_cuda(g, e);
@@ -898,7 +876,6 @@ dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info)
     info->group_steps = g->group;
     info->dt = g->dt;
     info->theta_max = g->theta_max;
-    info->quant = g->quant;
     return DSP_OK;
 }
 
@@ -1172,7 +1149,7 @@ int64_t footprint_of(const dsp_request &p)
     const int64_t pts = static_cast<int64_t>(p.nx) * p.ny;
     const int64_t tiles = (pts + dsp::kTilePoints - 1) / dsp::kTilePoints;
     return static_cast<int64_t>(align256(32 * static_cast<size_t>(pts)) +
-                                align256(entry_bytes(p.scheme) * static_cast<size_t>(p.n_steps)) +
+                                align256(table_bytes(p.precision, p.scheme, p.n_steps)) +
                                 align256(8 * static_cast<size_t>(tiles)) +
                                 align256(sizeof(DeviceScalars)) +
                                 align256(map_elem_bytes(p.precision) * static_cast<size_t>(pts)));
@@ -1233,7 +1210,7 @@ dsp_status server_admit(dsp_server *s, ServerReq *r)
         return st;
     const size_t pts = static_cast<size_t>(r->g.n_points);
     const size_t o_table = align256(32 * pts);
-    const size_t o_part = o_table + align256(host.size());
+    const size_t o_part = o_table + align256(table_bytes(p.precision, p.scheme, p.n_steps));
     const size_t o_scal = o_part + align256(8 * static_cast<size_t>(r->g.n_tiles));
     const size_t o_map = o_scal + align256(sizeof(DeviceScalars));
     const size_t total = o_map + align256(map_elem_bytes(p.precision) * pts);

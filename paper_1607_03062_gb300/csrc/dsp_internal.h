@@ -38,10 +38,11 @@ constexpr SeriesLevel kLevelsF64[kNumLevels] = {{3, 3}, {4, 3}, {4, 4}, {5, 5},
 
 struct ReqDesc {
     // Per step, s = valley (valley K- steps as K+ on -P: its operator is K+'s at -P):
-    //   EXACT, STRANG_XY: float4 (FP32_MIXED: s*dt*Ax hi, lo, s*dt*Ay hi, lo) or
-    //     double2 (FP64: s*dt*A), A at the step midpoint;
-    //   MAGNUS4: that for Abar = (A1 + A2)/2, followed by D = -(sqrt(3)/6) s*dt*(A2 - A1)
-    //     as float4 (D_x, D_y, 0, 0) or double2, A1, A2 at the two Gauss points.
+    //   EXACT, STRANG_XY: s*dt*A at the step midpoint, as float2 (FP32_MIXED) or
+    //     double2 (FP64);
+    //   MAGNUS4: s*dt*Abar, Abar = (A1 + A2)/2, and D = -(sqrt(3)/6) s*dt*(A2 - A1),
+    //     A1, A2 at the two Gauss points: float4 (Abar_x, Abar_y, D_x, D_y) or two
+    //     double2.
     const void *table;
     void *state;        // planes: FP32_MIXED float4 hi[n], float4 lo[n]; FP64 double2 a[n], double2 b[n]
     void *map;          // |c+|^2 output (float or double), or nullptr
@@ -49,7 +50,6 @@ struct ReqDesc {
     double px_min, py_min, hx, hy;
     double dt;
     double a_in[2], a_out[2];
-    double quant, inv_quant;  // 2^k and 2^-k: hi parts are multiples of 2^-k (FP32_MIXED)
     int64_t n_points;
     int64_t step_begin, step_end;  // table entries [step_begin, step_end) this launch
     int32_t nx, ny;

@@ -19,9 +19,11 @@
 //     in x = theta^2 = |dt P|^2 (no square root, no sin/cos call): the degree is
 //     chosen per request on the host from theta_max so truncation stays below
 //     the working precision;
-//   * FP32_MIXED: dt*p and dt*A are split into hi + lo with every hi a multiple
-//     of 2^-k, so P_hi = p_hi + A_hi is exact in FP32 and the momentum is known
-//     to ~1e-16 relative; the spinor is stored as hi + lo and each update adds
+//   * FP32_MIXED: dt*p is split into hi + lo (two floats, the momentum of every
+//     point to ~1e-16 relative), dt*A(t_n) is one float per step, and
+//     P_n = (p_hi + A_n) + p_lo: the FP32 roundings of P then change from step
+//     to step with A instead of shifting every step's momentum by the same
+//     amount; the spinor is stored as hi + lo and each update adds
 //     the increment (U - I) psi with a Fast2Sum, so the FP32 rounding of psi does
 //     not random-walk over 1e5 steps; the EXACT scheme multiplies 2, 4 or 8
 //     steps into one SU(2) matrix first, so the compensated update is paid once
@@ -261,19 +263,17 @@ constexpr int kF64Threads = kThreads;
 static_assert(kTilePoints % kMixedSpt == 0, "a CTA owns one whole tile");
 
 // MAGNUS4 table entries: the Gauss-point mean (dt*Abar, valley-signed) and the
-// commutator factor D = -(sqrt(3)/6) dt (A2 - A1) (valley-signed).
-struct MixedG2 {
-    float4 a;  // (Abar_x hi, lo, Abar_y hi, lo)
-    float4 d;  // (D_x, D_y, 0, 0)
-};
+// commutator factor D = -(sqrt(3)/6) dt (A2 - A1) (valley-signed).  FP32_MIXED:
+// one float4 (Abar_x, Abar_y, D_x, D_y).
 struct F64G2 {
     double2 a;  // Abar
     double2 d;  // D
 };
 
 // Bounds-check builds (-DDSP_BOUNDS_CHECK) verify, uniformly per CTA, that the
-// table entries a launch stages, [first, step_end), lie inside the table; a bad
-// range sets kErrBounds and the launch does nothing.  Otherwise a no-op.
+// table entries a launch stages, [first, step_end), lie inside the table (the
+// copy's rounding up to 16 bytes stays in the allocation's padding); a bad range
+// sets kErrBounds and the launch does nothing.  Otherwise a no-op.
 __device__ __forceinline__ bool table_range_ok(const ReqDesc &R, int64_t first, int *err)
 {
 #ifdef DSP_BOUNDS_CHECK
@@ -306,15 +306,23 @@ __device__ __forceinline__ bool tile_ok(const ReqDesc &R, int tile, int *err)
 #endif
 }
 
+// Stages table entries [base, base + nsteps) in chunks of kCh.  A 1-D bulk copy
+// must start and end on 16-byte boundaries: base is a multiple of kAlign entries
+// (16 bytes), every chunk is a multiple of kAlign, and the last copy is rounded
+// up to whole 16 bytes, which stays inside the table's allocation (the library
+// pads it to a multiple of 16 bytes).
 template <typename E>
 struct Stager {
     unsigned char *smem;
     uint64_t *bars;
-    const E *table;  // entry step_begin is element 0 of chunk 0
+    const E *table;  // entry base is element 0 of chunk 0
     int64_t nsteps;
     int nchunks;
     int withhold_first = 0;  // test hook (ReqDesc::withhold_first_copy)
     static constexpr int kCh = kStageBytes / static_cast<int>(sizeof(E));
+    static constexpr int kAlign = sizeof(E) >= 16 ? 1 : static_cast<int>(16 / sizeof(E));
+    static_assert(16 % sizeof(E) == 0 || sizeof(E) % 16 == 0, "entries tile 16 bytes");
+    static_assert(kCh % kAlign == 0, "chunks start on 16-byte boundaries");
 
     __device__ __forceinline__ const E *stage(int c) const
     {
@@ -327,7 +335,7 @@ struct Stager {
     }
     __device__ __forceinline__ void issue(int c) const  // one thread
     {
-        const uint32_t bytes = static_cast<uint32_t>(chunk_len(c)) * sizeof(E);
+        const uint32_t bytes = (static_cast<uint32_t>(chunk_len(c)) * sizeof(E) + 15u) & ~15u;
         mbar_arrive_expect_tx(&bars[c & 1], bytes);
         if (c == 0 && withhold_first)
             return;  // the phase cannot complete: its waiters time out
@@ -351,11 +359,13 @@ template <typename E, typename StepFn>
 __device__ __forceinline__ bool run_steps(const ReqDesc &R, unsigned char *smem, uint64_t *bars,
                                           int *err, StepFn step)
 {
-    if (!table_range_ok(R, R.step_begin, err))
+    const int64_t b_al = R.step_begin & ~static_cast<int64_t>(Stager<E>::kAlign - 1);
+    if (!table_range_ok(R, b_al, err))
         return false;
-    Stager<E> st{smem, bars, static_cast<const E *>(R.table) + R.step_begin,
-                 R.step_end - R.step_begin, 0};
+    Stager<E> st{smem, bars, static_cast<const E *>(R.table) + b_al, R.step_end - b_al, 0};
     st.withhold_first = R.withhold_first_copy;
+    if (R.step_end <= R.step_begin)
+        st.nsteps = 0;
     st.nchunks = static_cast<int>((st.nsteps + Stager<E>::kCh - 1) / Stager<E>::kCh);
     if (threadIdx.x == 0) {
         if (st.nchunks > 0) st.issue(0);
@@ -370,8 +380,9 @@ __device__ __forceinline__ bool run_steps(const ReqDesc &R, unsigned char *smem,
         }
         const E *tb = st.stage(c);
         const int len = st.chunk_len(c);
+        // entries before step_begin - b_al belong to earlier launches
 #pragma unroll 2
-        for (int j = 0; j < len; ++j)
+        for (int j = c == 0 ? static_cast<int>(R.step_begin - b_al) : 0; j < len; ++j)
             step(tb[j]);  // shared-memory broadcast
         __syncthreads();  // everyone is done with stage c & 1
         if (threadIdx.x == 0 && c + 2 < st.nchunks)
@@ -393,6 +404,7 @@ __device__ __forceinline__ bool run_step_groups(const ReqDesc &R, unsigned char 
 {
     static_assert(G >= 2 && (G & (G - 1)) == 0, "group size: a power of two");
     static_assert(Stager<E>::kCh % G == 0, "stages must hold whole groups");
+    static_assert(G % Stager<E>::kAlign == 0, "groups start on 16-byte boundaries");
     const int64_t b_al = R.step_begin & ~static_cast<int64_t>(G - 1);
     if (!table_range_ok(R, b_al, err))
         return false;
@@ -447,16 +459,12 @@ struct MixedPoint {
 };
 
 // Coefficients of U - I = [[cm1 - i qz, -q], [conj(q), cm1 + i qz]], q = qr + i qi,
-// for the step with kinematic momentum dt*P = (Pxh + Pxl, Pyh + Pyl).  P_h = p_h +
-// A_h is exact (common 2^-k grid), so P = fl(P_h + P_l) carries only its own final
-// rounding, which varies from step to step with A: no fixed momentum error.
-// EXACT and STRANG_XY have qz = 0.
+// for the step with kinematic momentum dt*P = (Px, Py).  EXACT and STRANG_XY have
+// qz = 0.
 template <int SCHEME, int DC, int DS>
-__device__ __forceinline__ void step_coeffs_f32(float Pxh, float Pxl, float Pyh, float Pyl,
-                                                float2 d, float &cm1, float &qr, float &qi,
-                                                float &qz)
+__device__ __forceinline__ void step_coeffs_f32(float Px, float Py, float2 d, float &cm1,
+                                                float &qr, float &qi, float &qz)
 {
-    const float Px = Pxh + Pxl, Py = Pyh + Pyl;
     if constexpr (SCHEME == 0) {
         const float x = fmaf(Px, Px, Py * Py);  // theta^2
         cm1 = cosm1_f32<DC>(x);
@@ -512,12 +520,18 @@ __device__ __forceinline__ void apply_f32(MixedPoint &s, float cm1, float qr, fl
     t = s.bi + dbi; s.lbi = dbi - (t - s.bi); s.bi = t;
 }
 
+// dt*P = (dt p_hi + dt A) + dt p_lo, rounded in that order.
+__device__ __forceinline__ float momentum_f32(float ph, float a, float pl)
+{
+    return __fadd_rn(__fadd_rn(ph, a), pl);
+}
+
 template <int SCHEME, int DC, int DS>
-__device__ __forceinline__ void step_mixed(MixedPoint &p, const float4 &a, float2 d)
+__device__ __forceinline__ void step_mixed(MixedPoint &p, const float2 &a, float2 d)
 {
     float cm1, qr, qi, qz;
-    step_coeffs_f32<SCHEME, DC, DS>(p.pxh + a.x, p.pxl + a.y, p.pyh + a.z, p.pyl + a.w, d, cm1,
-                                    qr, qi, qz);
+    step_coeffs_f32<SCHEME, DC, DS>(momentum_f32(p.pxh, a.x, p.pxl),
+                                    momentum_f32(p.pyh, a.y, p.pyl), d, cm1, qr, qi, qz);
     apply_f32<SCHEME>(p, cm1, qr, qi, qz);
 }
 
@@ -526,12 +540,12 @@ __device__ __forceinline__ void step_mixed(MixedPoint &p, const float4 &a, float
 //   al - 1 = m1 + m2 + m1 m2 - q2 conj(q1),  Q = q1 + q2 + m2 q1 + m1 q2,
 // applied with one compensated update (the product of two SU(2) steps is SU(2)).
 template <int DC, int DS>
-__device__ __forceinline__ void step_pair_mixed(MixedPoint &p, const float4 &a0, const float4 &a1)
+__device__ __forceinline__ void step_pair_mixed(MixedPoint &p, const float2 &a0, const float2 &a1)
 {
     float m1, q1r, q1i, m2, q2r, q2i, z;
-    step_coeffs_f32<0, DC, DS>(p.pxh + a0.x, p.pxl + a0.y, p.pyh + a0.z, p.pyl + a0.w,
+    step_coeffs_f32<0, DC, DS>(momentum_f32(p.pxh, a0.x, p.pxl), momentum_f32(p.pyh, a0.y, p.pyl),
                                make_float2(0.0f, 0.0f), m1, q1r, q1i, z);
-    step_coeffs_f32<0, DC, DS>(p.pxh + a1.x, p.pxl + a1.y, p.pyh + a1.z, p.pyl + a1.w,
+    step_coeffs_f32<0, DC, DS>(momentum_f32(p.pxh, a1.x, p.pxl), momentum_f32(p.pyh, a1.y, p.pyl),
                                make_float2(0.0f, 0.0f), m2, q2r, q2i, z);
     const float alm1 = fmaf(m1, m2, m1 + m2) - fmaf(q2r, q1r, q2i * q1i);
     const float ali = fmaf(q2r, q1i, -(q2i * q1r));
@@ -599,11 +613,11 @@ __device__ __forceinline__ void unpack_points(const MixedPack &p, MixedPoint &u,
 
 // step_coeffs_f32<0> on two momenta at once
 template <int DC, int DS>
-__device__ __forceinline__ void coeffs_exact2(const MixedPack &p, const float4 &a, float2 &m,
+__device__ __forceinline__ void coeffs_exact2(const MixedPack &p, const float2 &a, float2 &m,
                                               float2 &qr, float2 &qi)
 {
-    const float2 Px = add2(add2(p.pxh, bc2(a.x)), add2(p.pxl, bc2(a.y)));
-    const float2 Py = add2(add2(p.pyh, bc2(a.z)), add2(p.pyl, bc2(a.w)));
+    const float2 Px = add2(add2(p.pxh, bc2(a.x)), p.pxl);
+    const float2 Py = add2(add2(p.pyh, bc2(a.y)), p.pyl);
     const float2 x = fma2(Px, Px, mul2(Py, Py));
     m = mul2(horner2<DC, 1, 0>(x), x);
     const float2 sn = horner2<DS, 0, 1>(x);
@@ -629,7 +643,7 @@ __device__ __forceinline__ void apply2(MixedPack &p, float2 am, float2 ai, float
 
 // One EXACT step (apply_f32<0> with cm1 = m, q = (qr, qi)).
 template <int DC, int DS>
-__device__ __forceinline__ void step_exact2(MixedPack &p, const float4 &a)
+__device__ __forceinline__ void step_exact2(MixedPack &p, const float2 &a)
 {
     float2 m, qr, qi;
     coeffs_exact2<DC, DS>(p, a, m, qr, qi);
@@ -648,11 +662,11 @@ __device__ __forceinline__ void step_exact2(MixedPack &p, const float4 &a)
 // One MAGNUS4 step (step_coeffs_f32<2> + apply_f32<2> on two momenta):
 // U - I = [[m - i qz, -q], [conj(q), m + i qz]].
 template <int DC, int DS>
-__device__ __forceinline__ void step_magnus2(MixedPack &p, const MixedG2 &e)
+__device__ __forceinline__ void step_magnus2(MixedPack &p, const float4 &e)
 {
-    const float2 Px = add2(add2(p.pxh, bc2(e.a.x)), add2(p.pxl, bc2(e.a.y)));
-    const float2 Py = add2(add2(p.pyh, bc2(e.a.z)), add2(p.pyl, bc2(e.a.w)));
-    const float2 nz = fma2(Px, bc2(e.d.y), neg2(mul2(Py, bc2(e.d.x))));
+    const float2 Px = add2(add2(p.pxh, bc2(e.x)), p.pxl);
+    const float2 Py = add2(add2(p.pyh, bc2(e.y)), p.pyl);
+    const float2 nz = fma2(Px, bc2(e.w), neg2(mul2(Py, bc2(e.z))));
     const float2 x = fma2(Px, Px, fma2(Py, Py, mul2(nz, nz)));
     const float2 m = mul2(horner2<DC, 1, 0>(x), x);
     const float2 sn = horner2<DS, 0, 1>(x);
@@ -661,7 +675,7 @@ __device__ __forceinline__ void step_magnus2(MixedPack &p, const MixedG2 &e)
 
 // Two EXACT steps multiplied, then one update (step_pair_mixed on two momenta).
 template <int DC, int DS>
-__device__ __forceinline__ void step_pair2(MixedPack &p, const float4 &a0, const float4 &a1)
+__device__ __forceinline__ void step_pair2(MixedPack &p, const float2 &a0, const float2 &a1)
 {
     float2 m1, q1r, q1i, m2, q2r, q2i;
     coeffs_exact2<DC, DS>(p, a0, m1, q1r, q1i);
@@ -722,10 +736,10 @@ __device__ __forceinline__ V vhorner(V x)
 // m = cos(theta) - 1 and q = (qr, qi) of one EXACT step at dt P = dt p + table
 // entry a, with q = P + (sinc - 1) P.
 template <int DC, int DS, typename Pt, typename V>
-__device__ __forceinline__ void coeffs_group(const Pt &p, const float4 &a, V &m, V &qr, V &qi)
+__device__ __forceinline__ void coeffs_group(const Pt &p, const float2 &a, V &m, V &qr, V &qi)
 {
-    const V Px = vadd(vadd(p.pxh, vbc<V>(a.x)), vadd(p.pxl, vbc<V>(a.y)));
-    const V Py = vadd(vadd(p.pyh, vbc<V>(a.z)), vadd(p.pyl, vbc<V>(a.w)));
+    const V Px = vadd(vadd(p.pxh, vbc<V>(a.x)), p.pxl);
+    const V Py = vadd(vadd(p.pyh, vbc<V>(a.y)), p.pyl);
     const V x = vfma(Px, Px, vmul(Py, Py));
     m = vmul(vhorner<V, DC, 1, 0>(x), x);
     const V s1 = vmul(vhorner<V, DS, 1, 1>(x), x);  // sin(theta)/theta - 1
@@ -757,7 +771,7 @@ __device__ __forceinline__ void apply_group(Pt &p, V am, V ai, V Qr, V Qi)
 //   Qr'       = Qr + m Qr + qr Re alpha + qi Im alpha
 //   Qi'       = Qi + m Qi + qi Re alpha - qr Im alpha
 template <int G, int DC, int DS, typename Pt>
-__device__ __forceinline__ void step_group(Pt &p, const float4 *e)
+__device__ __forceinline__ void step_group(Pt &p, const float2 *e)
 {
     using V = decltype(p.ar);
     V m, qr, qi, Qr, Qi;
@@ -812,11 +826,10 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
         }
         // valley K- is stepped as K+ on -P: the table holds -dt*A, here -dt*p
         const double tx = vs * (R.dt * px), ty = vs * (R.dt * py);
-        const double hx = rint(tx * R.quant) * R.inv_quant, hy = rint(ty * R.quant) * R.inv_quant;
-        pt[s].pxh = static_cast<float>(hx);
-        pt[s].pxl = static_cast<float>(tx - hx);
-        pt[s].pyh = static_cast<float>(hy);
-        pt[s].pyl = static_cast<float>(ty - hy);
+        pt[s].pxh = static_cast<float>(tx);
+        pt[s].pxl = static_cast<float>(tx - static_cast<double>(pt[s].pxh));
+        pt[s].pyh = static_cast<float>(ty);
+        pt[s].pyl = static_cast<float>(ty - static_cast<double>(pt[s].pyh));
         if (R.fresh || !valid) {
             double ar = 1.0, ai = 0.0, br = 0.0, bi = 0.0;  // identity column
             if (!R.init_identity)
@@ -845,75 +858,75 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
     }
     bool ok;
     if constexpr (SCHEME == 0 && packed) {
-        const auto single = [&](const float4 &e) {
+        const auto single = [&](const float2 &e) {
 #pragma unroll
             for (int k = 0; k < S / 2; ++k)
                 step_exact2<DC, DS>(pk[k], e);
         };
         if (R.group == kGroupMax) {
-            ok = run_step_groups<float4, kGroupMax>(R, smem, bars, err, single,
-                                                    [&](const float4 *e) {
+            ok = run_step_groups<float2, kGroupMax>(R, smem, bars, err, single,
+                                                    [&](const float2 *e) {
 #pragma unroll
                 for (int k = 0; k < S / 2; ++k)
                     step_group<kGroupMax, DC, DS>(pk[k], e);
             });
         } else if (R.group == 4) {
-            ok = run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
+            ok = run_step_groups<float2, 4>(R, smem, bars, err, single, [&](const float2 *e) {
 #pragma unroll
                 for (int k = 0; k < S / 2; ++k)
                     step_group<4, DC, DS>(pk[k], e);
             });
         } else if (R.group == 2) {
-            ok = run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
+            ok = run_step_groups<float2, 2>(R, smem, bars, err, single, [&](const float2 *e) {
 #pragma unroll
                 for (int k = 0; k < S / 2; ++k)
                     step_pair2<DC, DS>(pk[k], e[0], e[1]);
             });
         } else {
-            ok = run_steps<float4>(R, smem, bars, err, single);
+            ok = run_steps<float2>(R, smem, bars, err, single);
         }
     } else if constexpr (SCHEME == 2 && packed) {
-        ok = run_steps<MixedG2>(R, smem, bars, err, [&](const MixedG2 &e) {
+        ok = run_steps<float4>(R, smem, bars, err, [&](const float4 &e) {
 #pragma unroll
             for (int k = 0; k < S / 2; ++k)
                 step_magnus2<DC, DS>(pk[k], e);
         });
     } else if constexpr (SCHEME == 0) {
-        const auto single = [&](const float4 &e) {
+        const auto single = [&](const float2 &e) {
 #pragma unroll
             for (int s = 0; s < S; ++s)
                 step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
         };
         if (R.group == kGroupMax) {
-            ok = run_step_groups<float4, kGroupMax>(R, smem, bars, err, single,
-                                                    [&](const float4 *e) {
+            ok = run_step_groups<float2, kGroupMax>(R, smem, bars, err, single,
+                                                    [&](const float2 *e) {
 #pragma unroll
                 for (int s = 0; s < S; ++s)
                     step_group<kGroupMax, DC, DS>(pt[s], e);
             });
         } else if (R.group == 4) {
-            ok = run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
+            ok = run_step_groups<float2, 4>(R, smem, bars, err, single, [&](const float2 *e) {
 #pragma unroll
                 for (int s = 0; s < S; ++s)
                     step_group<4, DC, DS>(pt[s], e);
             });
         } else if (R.group == 2) {
-            ok = run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
+            ok = run_step_groups<float2, 2>(R, smem, bars, err, single, [&](const float2 *e) {
 #pragma unroll
                 for (int s = 0; s < S; ++s)
                     step_pair_mixed<DC, DS>(pt[s], e[0], e[1]);
             });
         } else {
-            ok = run_steps<float4>(R, smem, bars, err, single);
+            ok = run_steps<float2>(R, smem, bars, err, single);
         }
     } else if constexpr (SCHEME == 2) {
-        ok = run_steps<MixedG2>(R, smem, bars, err, [&](const MixedG2 &e) {
+        ok = run_steps<float4>(R, smem, bars, err, [&](const float4 &e) {
 #pragma unroll
             for (int s = 0; s < S; ++s)
-                step_mixed<SCHEME, DC, DS>(pt[s], e.a, make_float2(e.d.x, e.d.y));
+                step_mixed<SCHEME, DC, DS>(pt[s], make_float2(e.x, e.y), make_float2(e.z, e.w));
         });
     } else {
-        ok = run_steps<float4>(R, smem, bars, err, [&](const float4 &e) {
+        ok = run_steps<float2>(R, smem, bars, err, [&](const float2 &e) {
 #pragma unroll
             for (int s = 0; s < S; ++s)
                 step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
