@@ -135,7 +135,7 @@ class ClockSampler:
 # SHA-256 of the kernel source the counters were taken on; a different source
 # means the counters are stale and the traffic is reported as null.
 KERNEL_TRAFFIC = {
-    "evolve_mixed_kernel": {"bytes": 109.14e6, "source_sha256": "e7946a5864b2ceeae2d27b738eac51a4f72c082c047d66e89cde73c98c1d09e2",
+    "evolve_mixed_kernel": {"bytes": 104.09e6, "source_sha256": "30863d130892e668e9b61f1f1250cb232f8294cd5749d13cc06eaf4e8d73fa82",
                             "profile": "profiles/evolve_mixed_lzs2048_1e5_traffic.md"},
 }
 
