@@ -169,8 +169,9 @@ dsp_status dsp_solve(dsp_grid *g, void *map_dev, double *n_host);
  * (as its first column: every step operator is SU(2), [[a, -conj(b)], [b,
  * conj(a)]], so the column (a, b) determines it), then the segments are
  * multiplied onto v(p + A_in) in time order in FP64.  Same steps, same results
- * as dsp_solve up to rounding (not bitwise).  segments = 0 picks enough to put
- * two CTAs on every SM (at least 16 steps per segment); needs cursor == 0
+ * as dsp_solve up to rounding (not bitwise).  segments = 0 picks enough for one
+ * segment-tile per SM in FP64, one per two SMs in FP32_MIXED (at least 16
+ * steps per segment); needs cursor == 0
  * (DSP_E_STATE otherwise).  Scratch: segments * 32 bytes per point, allocated
  * by the library (at most 16 GB, else DSP_E_INVALID).  map_dev and n_host as
  * in dsp_solve. */

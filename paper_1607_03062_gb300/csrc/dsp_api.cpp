@@ -674,7 +674,11 @@ dsp_status dsp_solve_segmented(dsp_grid *g, int32_t segments, void *map_dev, dou
     if (g->n_steps == 0)
         return dsp_solve(g, map_dev, n_host);
     int64_t S = segments;
-    if (S == 0) {  // enough CTAs for two of them on every SM, >= 16 steps a segment
+    if (S == 0) {
+        // FP64 evolution is bound by the FP64 pipe: one segment-tile per SM.  FP32_MIXED
+        // segments are short and latency bound, and the FP64 combine grows with S: one
+        // segment-tile per two SMs.  At least 16 steps a segment.  (Measured on the 64^2
+        // x 2000-step case, 4 tiles: S = 38 / 19 beat S = 76 by 8% / 40%.)
         static int sms = 0;
         if (sms == 0) {
             int dev = 0;
@@ -684,7 +688,8 @@ dsp_status dsp_solve_segmented(dsp_grid *g, int32_t segments, void *map_dev, dou
                 sms = 152;
             }
         }
-        S = (2 * static_cast<int64_t>(sms) + g->n_tiles - 1) / g->n_tiles;
+        const int64_t ctas = g->precision == DSP_FP64 ? sms : (sms + 1) / 2;
+        S = (ctas + g->n_tiles - 1) / g->n_tiles;
         S = std::min<int64_t>(S, g->n_steps / 16);
     }
     S = std::max<int64_t>(1, std::min<int64_t>(S, g->n_steps));
