@@ -272,20 +272,24 @@ def test_checkpoint_resume_bitwise(prec):
     assert np.array_equal(mp.cpu().numpy().astype(np.float64), m_ref) and n == n_ref
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
-def test_lzs_2048_full_size_sampled(orc, prec):
-    """The 2048x2048, 1e5-step LZS workload (first seeded sample) in the launch
-    configuration the benchmark times; 384 seeded points checked one by one."""
-    cfg = W.config_lzs_2048(0)
+@pytest.mark.parametrize("prec,sample", [("fp64", 0)] + [("fp32_mixed", k) for k in range(8)])
+def test_lzs_2048_full_size_sampled(orc, prec, sample):
+    """The 2048x2048, 1e5-step LZS workload in the launch configuration the
+    benchmark times, every seeded (omega, E0) sample in FP32-mixed (they run at
+    different series degrees and step-group sizes: groups of 4 for the one with
+    theta_max > 0.025) and the first in FP64 (19 s a solve).  384 seeded points, a
+    band around p_y = 0 and the 128 largest |c+|^2 of the map, checked one by one."""
+    cfg = W.config_lzs_2048(sample)
     g = cfg["grid"]
     tab_o = orc.pulse_table(cfg["pulse"], cfg["steps"])
     m, n = run_gpu(g, B.sample_pulse(cfg["pulse"], cfg["steps"]), prec)
-    idx = W.sample_points(g["nx"], g["ny"], 384, seed=11)
-    # points where pairs are likely: around p_y = 0 along the field
+    idx = W.sample_points(g["nx"], g["ny"], 384, seed=11 + sample)
+    # points where pairs are likely: around p_y = 0 along the field, and the map's maxima
     xs = orc.grid_nodes(*g["px"], g["nx"])
     ys = orc.grid_nodes(*g["py"], g["ny"])
     band = np.arange(g["nx"] // 2 - 8, g["nx"] // 2 + 8) * g["nx"] + np.arange(0, g["nx"], 128)[:, None]
-    idx = np.unique(np.concatenate([idx, band.ravel()]))
+    top = np.argsort(m.ravel())[-128:]
+    idx = np.unique(np.concatenate([idx, band.ravel(), top]))
     r = orc.solve_points(xs[idx % g["nx"]], ys[idx // g["nx"]], *tab_o[:1], tab_o[3], tab_o[1],
                          tab_o[2])
     err = np.abs(m.ravel()[idx] - r["cplus2"]).max()
