@@ -197,6 +197,16 @@ def ops_mixed(dc, ds, group=2):
     return 20 + dc + ds + 22.0 / group
 
 
+def ops_magnus4(dc, ds, group=1):
+    """FP32 lane instructions per spinor-step of the MAGNUS4 path.  Per step: 4 (Pbar) +
+    2 (n_z) + 3 (|n|^2) + dc + ds + 3 (q, q_z).  Single steps: + 16 ((U - I) psi + lo)
+    + 12 (Fast2Sum).  Groups of G: + 16 per further step of the chain, 1 to start it,
+    8 (unitarity rebuild) and 28 (update) per group."""
+    if group == 1:
+        return 40 + dc + ds
+    return 28 + dc + ds + 21.0 / group
+
+
 def ops_fp64(dc, ds):
     return 18 + dc + ds
 
@@ -420,9 +430,8 @@ def run_gpu(args):
 
 def magnus4_leg(args, cfgs, stream, world, rank, warm=1, reps=2):
     """The same 2048^2 x 1e5-step solves with the fourth-order Magnus step
-    (two Gauss-point samples per step), FP32-mixed.  Its instructions per
-    spinor-step: 4 (Pbar) + 2 (n_z) + 3 (|n|^2) + dc + ds + 3 (q, q_z) + 16
-    ((U - I) psi + lo) + 12 (Fast2Sum) = 40 + dc + ds."""
+    (two Gauss-point samples per step), FP32-mixed, in step groups like EXACT.
+    Its instructions per spinor-step: ops_magnus4."""
     import torch
 
     from paper_1607_03062_gb300 import binding as B
@@ -449,7 +458,7 @@ def magnus4_leg(args, cfgs, stream, world, rank, warm=1, reps=2):
         if k >= warm:
             times.append(e0.elapsed_time(e1) / 1e3)
             info = B.get_info(h)
-            ops.append(40 + info["cos_degree"] + info["sinc_degree"])
+            ops.append(ops_magnus4(info["cos_degree"], info["sinc_degree"], info["group_steps"]))
     B.destroy_grid(h)
     work = float(n) * n * args.time_steps
     achieved = statistics.mean(o * work / t for o, t in zip(ops, times)) / 1e12

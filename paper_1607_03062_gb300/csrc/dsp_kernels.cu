@@ -255,6 +255,10 @@ constexpr int kStageBytes = 16384;  // per stage; two stages per CTA
 #endif
 constexpr int kPairUnroll = DSP_PAIR_UNROLL;
 constexpr int kGroupUnroll = DSP_GROUP_UNROLL;  // chain loop inside one group (>= G - 2: whole)
+#ifndef DSP_MAGNUS_GROUP_UNROLL
+#define DSP_MAGNUS_GROUP_UNROLL 1
+#endif
+constexpr int kMagnusGroupUnroll = DSP_MAGNUS_GROUP_UNROLL;  // the MAGNUS4 chain's
 constexpr int kMixedSpt = DSP_MIXED_SPT;
 constexpr int kMixedThreads = kTilePoints / kMixedSpt;
 constexpr int kMixedMinBlocks = DSP_MIXED_MINB;  // resident CTAs per SM the registers allow
@@ -803,6 +807,57 @@ __device__ __forceinline__ void step_group(Pt &p, const float2 *e)
     apply_group(p, am, ai, Qr, Qi);
 }
 
+// MAGNUS4 steps in groups (G = 2, 4, 8).  One step is exp(-i n.sigma) with
+// n = (dt Pbar, n_z): U = [[1 + m - i qz, -q], [conj(q), 1 + m + i qz]], m =
+// cos|n| - 1, (q, qz) = sin|n|/|n| (n_y + i n_x, n_z), formed as n + (sinc - 1) n.
+// The chain is the EXACT one with the sigma_z terms added:
+//   Re alpha' = Re alpha + m Re alpha + qz Im alpha - (qr Qr + qi Qi)
+//   Im alpha' = Im alpha + m Im alpha - qz Re alpha - (qi Qr - qr Qi)
+//   Qr'       = Qr + m Qr + qz Qi + qr Re alpha + qi Im alpha
+//   Qi'       = Qi + m Qi - qz Qr + qi Re alpha - qr Im alpha
+// starting from alpha = 1 + m - i qz, Q = q of the group's first step, then the
+// same unitarity rebuild of Re alpha - 1 and compensated update as EXACT groups.
+template <int DC, int DS, typename Pt, typename V>
+__device__ __forceinline__ void coeffs_magnus_group(const Pt &p, const float4 &e, V &m, V &qr,
+                                                    V &qi, V &qz)
+{
+    const V Px = vadd(vadd(p.pxh, vbc<V>(e.x)), p.pxl);
+    const V Py = vadd(vadd(p.pyh, vbc<V>(e.y)), p.pyl);
+    const V nz = vfma(Px, vbc<V>(e.w), vneg(vmul(Py, vbc<V>(e.z))));
+    const V x = vfma(Px, Px, vfma(Py, Py, vmul(nz, nz)));
+    m = vmul(vhorner<V, DC, 1, 0>(x), x);
+    const V s1 = vmul(vhorner<V, DS, 1, 1>(x), x);  // sin|n|/|n| - 1
+    qr = vfma(s1, Py, Py);
+    qi = vfma(s1, Px, Px);
+    qz = vfma(s1, nz, nz);
+}
+
+template <int G, int DC, int DS, typename Pt>
+__device__ __forceinline__ void step_group_magnus(Pt &p, const float4 *e)
+{
+    using V = decltype(p.ar);
+    V m, qr, qi, qz, Qr, Qi;
+    coeffs_magnus_group<DC, DS>(p, e[0], m, Qr, Qi, qz);
+    V Ar = vadd(m, vbc<V>(1.0f));
+    V ai = vneg(qz);
+#pragma unroll kMagnusGroupUnroll
+    for (int k = 1; k < G; ++k) {
+        coeffs_magnus_group<DC, DS>(p, e[k], m, qr, qi, qz);
+        const V nAr = vfma(m, Ar, vfma(qz, ai, vfma(vneg(qr), Qr, vfma(vneg(qi), Qi, Ar))));
+        const V nai = vfma(m, ai, vfma(vneg(qz), Ar, vfma(vneg(qi), Qr, vfma(qr, Qi, ai))));
+        const V nQr = vfma(m, Qr, vfma(qz, Qi, vfma(qr, Ar, vfma(qi, ai, Qr))));
+        const V nQi = vfma(m, Qi, vfma(vneg(qz), Qr, vfma(qi, Ar, vfma(vneg(qr), ai, Qi))));
+        Ar = nAr;
+        ai = nai;
+        Qr = nQr;
+        Qi = nQi;
+    }
+    V am = vadd(Ar, vbc<V>(-1.0f));  // exact: Re alpha is within [1/2, 2]
+    const V u = vfma(am, am, vfma(Qi, Qi, vfma(Qr, Qr, vfma(ai, ai, vadd(am, am)))));
+    am = vfma(vneg(u), vfma(vbc<V>(-0.5f), am, vbc<V>(0.5f)), am);  // am -= u / (2 (1 + am))
+    apply_group(p, am, ai, Qr, Qi);
+}
+
 template <int SCHEME, int DC, int DS>
 __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint64_t *bars,
                            int *err)
@@ -886,11 +941,33 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
             ok = run_steps<float2>(R, smem, bars, err, single);
         }
     } else if constexpr (SCHEME == 2 && packed) {
-        ok = run_steps<float4>(R, smem, bars, err, [&](const float4 &e) {
+        const auto single = [&](const float4 &e) {
 #pragma unroll
             for (int k = 0; k < S / 2; ++k)
                 step_magnus2<DC, DS>(pk[k], e);
-        });
+        };
+        if (R.group == kGroupMax) {
+            ok = run_step_groups<float4, kGroupMax>(R, smem, bars, err, single,
+                                                    [&](const float4 *e) {
+#pragma unroll
+                for (int k = 0; k < S / 2; ++k)
+                    step_group_magnus<kGroupMax, DC, DS>(pk[k], e);
+            });
+        } else if (R.group == 4) {
+            ok = run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
+#pragma unroll
+                for (int k = 0; k < S / 2; ++k)
+                    step_group_magnus<4, DC, DS>(pk[k], e);
+            });
+        } else if (R.group == 2) {
+            ok = run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
+#pragma unroll
+                for (int k = 0; k < S / 2; ++k)
+                    step_group_magnus<2, DC, DS>(pk[k], e);
+            });
+        } else {
+            ok = run_steps<float4>(R, smem, bars, err, single);
+        }
     } else if constexpr (SCHEME == 0) {
         const auto single = [&](const float2 &e) {
 #pragma unroll
@@ -920,11 +997,33 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
             ok = run_steps<float2>(R, smem, bars, err, single);
         }
     } else if constexpr (SCHEME == 2) {
-        ok = run_steps<float4>(R, smem, bars, err, [&](const float4 &e) {
+        const auto single = [&](const float4 &e) {
 #pragma unroll
             for (int s = 0; s < S; ++s)
                 step_mixed<SCHEME, DC, DS>(pt[s], make_float2(e.x, e.y), make_float2(e.z, e.w));
-        });
+        };
+        if (R.group == kGroupMax) {
+            ok = run_step_groups<float4, kGroupMax>(R, smem, bars, err, single,
+                                                    [&](const float4 *e) {
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+                    step_group_magnus<kGroupMax, DC, DS>(pt[s], e);
+            });
+        } else if (R.group == 4) {
+            ok = run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+                    step_group_magnus<4, DC, DS>(pt[s], e);
+            });
+        } else if (R.group == 2) {
+            ok = run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+                    step_group_magnus<2, DC, DS>(pt[s], e);
+            });
+        } else {
+            ok = run_steps<float4>(R, smem, bars, err, single);
+        }
     } else {
         ok = run_steps<float2>(R, smem, bars, err, [&](const float2 &e) {
 #pragma unroll

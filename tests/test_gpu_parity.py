@@ -367,6 +367,36 @@ def test_magnus4_ragged_against_oracle(orc, prec, valley):
     assert_close(prec, m, dens, ref, nref)
 
 
+@pytest.mark.parametrize("G", sorted(GROUP_STEPS))
+def test_magnus4_step_groups_vs_oracle_and_pieces(orc, G):
+    """FP32-mixed MAGNUS4 in each group size (the same step counts pick the same
+    G as for EXACT): the library reports it, the result meets the oracle at the
+    FP32-mixed tolerance, pieces ending on multiples of 8 are bitwise the
+    one-launch result, and boundaries inside groups change rounding only."""
+    grid = {"nx": 48, "ny": 40, "px": (-4, 4), "py": (-4, 4)}
+    pulse = W.sin2_pulse(1.0, 1.55, 5.0, eps=0.4)
+    n = GROUP_STEPS[G]
+    tab = B.sample_pulse_gauss(pulse, n)
+    g = B.Grid(48, 40, grid["px"], grid["py"], "fp32_mixed", "magnus4")
+    g.set_pulse(tab[0], tab[3], tab[1], tab[2])
+    info = B.get_info(g.h)
+    g.close()
+    assert info["group_steps"] == G
+    a, a_in, a_out, dt = orc.pulse_table_gauss(pulse, n)
+    ref, _, _, nref = orc.solve_grid(48, 40, grid["px"], grid["py"], a, dt, a_in, a_out,
+                                     scheme="magnus4")
+    m1, n1 = run_gpu(grid, tab, "fp32_mixed", "magnus4")
+    assert_close("fp32_mixed", m1, n1, ref, nref)
+    m2, n2 = run_gpu(grid, tab, "fp32_mixed", "magnus4", pieces=[8 * 37, 8 * 51, n - 8 * 88])
+    assert np.array_equal(m1, m2) and n1 == n2
+    m3, n3 = run_gpu(grid, tab, "fp32_mixed", "magnus4", pieces=[299, 5, 3, n - 307])
+    assert_close("fp32_mixed", m3, n3, ref, nref)
+    if G == 1:
+        assert np.array_equal(m1, m3) and n1 == n3
+    else:
+        assert np.abs(m1 - m3).max() <= 1e-6
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
 def test_magnus4_reaches_midpoint_accuracy_with_fewer_steps(orc, prec):
     """Against a converged oracle reference, MAGNUS4 with 500 steps is far more
