@@ -135,7 +135,7 @@ class ClockSampler:
 # SHA-256 of the kernel source the counters were taken on; a different source
 # means the counters are stale and the traffic is reported as null.
 KERNEL_TRAFFIC = {
-    "evolve_mixed_kernel": {"bytes": 104.09e6, "source_sha256": "30863d130892e668e9b61f1f1250cb232f8294cd5749d13cc06eaf4e8d73fa82",
+    "evolve_mixed_kernel": {"bytes": 105.90e6, "source_sha256": "c26a5808dc19f6cdb4abbc73ae196bf9a82aa11fb3f9659822994412684f76e2",
                             "profile": "profiles/evolve_mixed_lzs2048_1e5_traffic.md"},
 }
 
