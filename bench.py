@@ -169,7 +169,7 @@ def load_peaks():
 # ------------------------------------------------------------------------------------------
 # FP32 lane instructions of the FP32-mixed EXACT path, with series degrees dc (cos) and
 # ds (sin/theta) as the library reports them.  Per step:
-#   P = (p_h + A) + p_l (x and y)                               4
+#   P = p_h + (A + p_l) (x and y)                               4
 #   theta^2 = fma(Px, Px, Py*Py)                               2
 #   cos(theta) - 1 (Horner, dc - 1 FMA + 1 MUL)                dc
 #   sin(theta)/theta (Horner)                                  ds

@@ -55,7 +55,7 @@ typedef int32_t dsp_status;
 /* Arithmetic of the evolution. */
 #define DSP_FP64 0       /* everything in FP64                                      */
 #define DSP_FP32_MIXED 1 /* spinor in compensated FP32 (hi + lo); dt P_n formed as
-                            (dt p_hi + dt A_n) + dt p_lo with dt p an FP32 hi/lo
+                            dt p_hi + (dt A_n + dt p_lo) with dt p an FP32 hi/lo
                             pair; cos/sin of the phase argument dt|P| in FP32;
                             initial state and projection in FP64                   */
 

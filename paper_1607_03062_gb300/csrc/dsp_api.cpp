@@ -339,6 +339,7 @@ void build_table(const dsp_grid *g, const double *a_mid, int64_t n, double dt,
     if (g->scheme == DSP_SCHEME_MAGNUS4) {
         // (Abar, D): Abar = (A1 + A2)/2, D = -(sqrt(3)/6) (A2 - A1), both times s*dt
         const double kappa = -std::sqrt(3.0) / 6.0;
+        double mresid[2] = {0.0, 0.0};
         for (int64_t k = 0; k < n; ++k) {
             const double *a = a_mid + 4 * k;
             const double bx = vs * (dt * (0.5 * (a[0] + a[2])));
@@ -352,9 +353,13 @@ void build_table(const dsp_grid *g, const double *a_mid, int64_t n, double dt,
                 t[2] = dx;
                 t[3] = dy;
             } else {
+                // Abar rounded with error feedback, as for the midpoint table below
                 float *t = reinterpret_cast<float *>(out.data()) + 4 * k;
-                t[0] = static_cast<float>(bx);
-                t[1] = static_cast<float>(by);
+                const double vx = bx + mresid[0], vy = by + mresid[1];
+                t[0] = static_cast<float>(vx);
+                t[1] = static_cast<float>(vy);
+                mresid[0] = vx - static_cast<double>(t[0]);
+                mresid[1] = vy - static_cast<double>(t[1]);
                 t[2] = static_cast<float>(dx);
                 t[3] = static_cast<float>(dy);
             }
@@ -368,9 +373,19 @@ void build_table(const dsp_grid *g, const double *a_mid, int64_t n, double dt,
             t[2 * k + 1] = vs * (dt * a_mid[2 * k + 1]);
         }
     } else {
+        // Rounded with error feedback: each entry absorbs the previous entries'
+        // rounding residual, so the running sum of the stored dt*A stays within half
+        // a float ulp of the exact running sum.  The phase integrates A over time; the
+        // per-step roundings then cannot random-walk in it, however long the run.
         float *t = reinterpret_cast<float *>(out.data());
-        for (int64_t k = 0; k < 2 * n; ++k)
-            t[k] = static_cast<float>(vs * (dt * a_mid[k]));
+        double resid[2] = {0.0, 0.0};
+        for (int64_t k = 0; k < n; ++k)
+            for (int c = 0; c < 2; ++c) {
+                const double v = vs * (dt * a_mid[2 * k + c]) + resid[c];
+                const float f = static_cast<float>(v);
+                resid[c] = v - static_cast<double>(f);
+                t[2 * k + c] = f;
+            }
     }
 }
 

