@@ -135,7 +135,7 @@ class ClockSampler:
 # SHA-256 of the kernel source the counters were taken on; a different source
 # means the counters are stale and the traffic is reported as null.
 KERNEL_TRAFFIC = {
-    "evolve_mixed_kernel": {"bytes": 105.90e6, "source_sha256": "c26a5808dc19f6cdb4abbc73ae196bf9a82aa11fb3f9659822994412684f76e2",
+    "evolve_mixed_kernel": {"bytes": 101.87e6, "source_sha256": "d2c34b25db4392e908943ff85c2cb4dc679af626b37d882d511287857eb7cf5e",
                             "profile": "profiles/evolve_mixed_lzs2048_1e5_traffic.md"},
 }
 
