@@ -5,7 +5,11 @@
         --scheme magnus4 --out map.npy
 
 ``--spec`` reads a pulse dictionary (see ``workloads.py``: kind, E0, omega, T, ...).
-The |c+|^2 map can be written with ``--out`` (numpy .npy, [ny][nx]).
+The |c+|^2 map can be written with ``--out`` (numpy .npy, [ny][nx]).  ``--sample k``
+picks the k-th seeded (omega, E0) draw of the LZS scan.  ``--vs-fp64`` also solves
+the same grid in FP64 and reports the FP32-mixed map's error over every point:
+
+    python -m paper_1607_03062_gb300 --workload lzs_2048 --sample 6 --vs-fp64
 """
 from __future__ import annotations
 
@@ -20,12 +24,12 @@ from . import binding as B
 from . import workloads as W
 
 WORKLOADS = {
-    "sin2_64": W.config_sin2_64,
-    "gauss_1024": lambda: W.config_gauss_1024(2.0),
-    "lzs_2048": lambda: W.config_lzs_2048(0),
-    "two_colour_4096": W.config_two_colour_4096,
-    "paper": lambda: {"name": "paper_pulse_fig1", "grid": W.grid(256, 0.5),
-                      "pulse": W.paper_pulse(), "steps": 20000},
+    "sin2_64": lambda k: W.config_sin2_64(),
+    "gauss_1024": lambda k: W.config_gauss_1024(2.0),
+    "lzs_2048": lambda k: W.config_lzs_2048(k),
+    "two_colour_4096": lambda k: W.config_two_colour_4096(),
+    "paper": lambda k: {"name": "paper_pulse_fig1", "grid": W.grid(256, 0.5),
+                        "pulse": W.paper_pulse(), "steps": 20000},
 }
 
 
@@ -42,11 +46,15 @@ def main(argv=None):
     ap.add_argument("--segmented", type=int, default=-1,
                     help="time-parallel solve with this many segments (0 = automatic)")
     ap.add_argument("--out", help="write the |c+|^2 map to this .npy file")
+    ap.add_argument("--sample", type=int, default=0,
+                    help="seeded (omega, E0) draw of the LZS scan (lzs_2048 only), 0..7")
+    ap.add_argument("--vs-fp64", action="store_true",
+                    help="also solve in FP64 and report the map's error over every point")
     a = ap.parse_args(argv)
 
     import torch
 
-    cfg = WORKLOADS[a.workload]()
+    cfg = WORKLOADS[a.workload](a.sample)
     if a.spec:
         with open(a.spec) as f:
             cfg["pulse"] = json.load(f)
@@ -70,13 +78,25 @@ def main(argv=None):
     info = B.get_info(grid.h)
     if a.out:
         np.save(a.out, m.cpu().numpy())
-    print(json.dumps({"workload": cfg["name"], "grid": [g["nx"], g["ny"]], "steps": steps,
-                      "precision": a.precision, "scheme": a.scheme, "valley": a.valley,
-                      "density_eV2": n, "max_cplus2": float(m.max().item()), "wall_s": wall,
-                      "spinor_steps_per_s": g["nx"] * g["ny"] * steps / wall,
-                      "series_degrees": [info["cos_degree"], info["sinc_degree"]],
-                      "theta_max": info["theta_max"]}))
+    out = {"workload": cfg["name"], "grid": [g["nx"], g["ny"]], "steps": steps,
+           "precision": a.precision, "scheme": a.scheme, "valley": a.valley,
+           "density_eV2": n, "max_cplus2": float(m.max().item()), "wall_s": wall,
+           "spinor_steps_per_s": g["nx"] * g["ny"] * steps / wall,
+           "series_degrees": [info["cos_degree"], info["sinc_degree"]],
+           "group_steps": info["group_steps"], "theta_max": info["theta_max"]}
     grid.close()
+    if a.vs_fp64 and a.precision != "fp64":
+        ref = B.Grid(g["nx"], g["ny"], g["px"], g["py"], "fp64", a.scheme, a.valley)
+        ref.set_pulse(a_mid, dt, a_in, a_out)
+        m64, n64 = ref.solve()
+        err = (m.double() - m64).abs().flatten().cpu().numpy()
+        k = int(np.argmax(err))
+        out["vs_fp64"] = {"max_abs_err": float(err[k]), "at_ix_iy": [k % g["nx"], k // g["nx"]],
+                          "p99_9": float(np.quantile(err, 0.999)),
+                          "points_above_1e-6": int((err > 1e-6).sum()),
+                          "density_rel_err": abs(n - n64) / n64 if n64 else None}
+        ref.close()
+    print(json.dumps(out))
     return 0
 
 

@@ -38,6 +38,22 @@ def test_cli_solve_writes_map_and_density(tmp_path, orc):
     assert abs(line["density_eV2"] - nref) <= 1e-10 * nref
 
 
+@pytest.mark.gpu
+def test_cli_fp32_mixed_against_fp64_map():
+    """--vs-fp64 solves the same grid in both precisions and reports the
+    FP32-mixed map's error over every point; on the 64^2 case it must sit within
+    the FP32-mixed tolerance and agree with a direct comparison of the two maps."""
+    res = subprocess.run([sys.executable, "-m", "paper_1607_03062_gb300", "--workload", "sin2_64",
+                          "--vs-fp64"], cwd=ROOT, capture_output=True, text=True, timeout=300,
+                         check=True)
+    line = json.loads(res.stdout.strip().splitlines()[-1])
+    v = line["vs_fp64"]
+    assert line["precision"] == "fp32_mixed" and line["group_steps"] >= 1
+    assert 0.0 < v["max_abs_err"] <= 1e-5 and v["p99_9"] <= v["max_abs_err"]
+    assert abs(v["density_rel_err"]) <= 1e-4
+    assert 0 <= v["at_ix_iy"][0] < 64 and 0 <= v["at_ix_iy"][1] < 64
+
+
 def test_reference_arm_under_torchrun_two_ranks():
     """Launched like the N > 1 benchmark: rank 0 prints the only JSON line, the
     other rank exits 0 without work."""
