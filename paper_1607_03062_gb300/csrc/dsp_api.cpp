@@ -131,12 +131,6 @@ int32_t choose_group(int32_t precision, int32_t scheme, double theta_max)
     return 1;
 }
 
-double box_abs_max(const dsp_grid *g)
-{
-    return std::max(std::max(std::fabs(g->px_min), std::fabs(g->px_max)),
-                    std::max(std::fabs(g->py_min), std::fabs(g->py_max)));
-}
-
 // dt * max over steps and box corners of |p + A_n| (|P| is convex in p, so the
 // maximum over the box is at a corner).
 double theta_max(const dsp_grid *g, const double *a_mid, int64_t n, double dt)

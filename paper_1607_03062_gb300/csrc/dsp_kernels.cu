@@ -713,20 +713,28 @@ __device__ __forceinline__ void step_pair2(MixedPack &p, const float2 &a0, const
 // entries.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ float vneg(float a) { return -a; }
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return add2(a, b); }
-__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return mul2(a, b); }
-__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return fma2(a, b, c); }
-__device__ __forceinline__ float2 vneg(float2 a) { return neg2(a); }
+// Either set of forms can go unused, depending on the build (the float forms serve
+// builds without the packed path: DSP_PACKED_PAIRS=0 or an odd DSP_MIXED_SPT).
+[[maybe_unused]] __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+[[maybe_unused]] __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+[[maybe_unused]] __device__ __forceinline__ float vfma(float a, float b, float c)
+{
+    return __fmaf_rn(a, b, c);
+}
+[[maybe_unused]] __device__ __forceinline__ float vneg(float a) { return -a; }
+[[maybe_unused]] __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return add2(a, b); }
+[[maybe_unused]] __device__ __forceinline__ float2 vmul(float2 a, float2 b) { return mul2(a, b); }
+[[maybe_unused]] __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c)
+{
+    return fma2(a, b, c);
+}
+[[maybe_unused]] __device__ __forceinline__ float2 vneg(float2 a) { return neg2(a); }
 template <typename V>
 __device__ __forceinline__ V vbc(float v);
 template <>
-__device__ __forceinline__ float vbc<float>(float v) { return v; }
+[[maybe_unused]] __device__ __forceinline__ float vbc<float>(float v) { return v; }
 template <>
-__device__ __forceinline__ float2 vbc<float2>(float v) { return bc2(v); }
+[[maybe_unused]] __device__ __forceinline__ float2 vbc<float2>(float v) { return bc2(v); }
 
 template <typename V, int D, int K, int ODD>
 __device__ __forceinline__ V vhorner(V x)
