@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--serving-chunk", type=int, default=2000)
     ap.add_argument("--no-small-grid", action="store_true", help="skip the 64x64 latency leg")
     ap.add_argument("--no-magnus4", action="store_true", help="skip the fourth-order leg")
+    ap.add_argument("--no-strang", action="store_true", help="skip the STRANG_XY leg")
     return ap.parse_args()
 
 
@@ -207,6 +208,16 @@ def ops_magnus4(dc, ds, group=1):
     return 28 + dc + ds + 21.0 / group
 
 
+def ops_strang(dc, ds, group=1):
+    """FP32 lane instructions per spinor-step of the STRANG_XY path.  Per step: 4 (P) +
+    2 (P_x^2, P_y^2) + 2 dc + 2 ds (cos - 1 and sin/theta - 1 of both) + 5 (sin 2a, sin b,
+    cos b sin 2a, m).  Single steps: + 28 (update, Fast2Sum).  Groups of G: the EXACT
+    chain, + 12 per further step, 10 to start it, 8 + 28 per group."""
+    if group == 1:
+        return 39 + 2 * (dc + ds)
+    return 23 + 2 * (dc + ds) + 22.0 / group
+
+
 def ops_fp64(dc, ds):
     return 18 + dc + ds
 
@@ -345,14 +356,17 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_tot = float(t.item())
     e2e = {"value": work_per_solve * args.steps * world / e2e_tot, "unit": METRIC,
-           "h2d_bytes_per_step": 16 * nsteps + 2 * 16,
+           "h2d_bytes_per_step": 8 * nsteps,  # the FP32 pulse table the host builds
            "d2h_bytes_per_step": 4 * n * n + 16,
            "note": "dsp_solve_host: host midpoint table in, host |c+|^2 map and density out"}
 
-    # ---- fourth-order Magnus scheme on the same workload ----
+    # ---- the other step schemes on the same workload ----
     magnus = None
     if not args.no_magnus4:
-        magnus = magnus4_leg(args, cfgs, st_ptr, world, rank)
+        magnus = scheme_leg(args, cfgs, st_ptr, world, rank, "magnus4")
+    strang = None
+    if not args.no_strang:
+        strang = scheme_leg(args, cfgs, st_ptr, world, rank, "strang_xy")
 
     # ---- small grid: sequential vs time-parallel solve latency ----
     small = None
@@ -413,7 +427,7 @@ def run_gpu(args):
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world} (independent samples per rank)"},
         "density_first_step": d_mixed[0] if d_mixed else None,
-        "fp64": fp64, "e2e": e2e, "magnus4": magnus, "serving": serving, "small_grid": small,
+        "fp64": fp64, "e2e": e2e, "magnus4": magnus, "strang_xy": strang, "serving": serving, "small_grid": small,
         "gpu_launches": 2 * args.steps,
         "roofline": roof, "cpu_baseline": cpu, "accuracy_vs_oracle": accuracy, "clocks": clocks,
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
@@ -428,10 +442,17 @@ def run_gpu(args):
 # Fourth-order Magnus leg
 # ------------------------------------------------------------------------------------------
 
-def magnus4_leg(args, cfgs, stream, world, rank, warm=1, reps=2):
-    """The same 2048^2 x 1e5-step solves with the fourth-order Magnus step
-    (two Gauss-point samples per step), FP32-mixed, in step groups like EXACT.
-    Its instructions per spinor-step: ops_magnus4."""
+SCHEME_LEGS = {
+    "magnus4": ("magnus4 (fourth order, 2 Gauss points/step)", ops_magnus4),
+    "strang_xy": ("strang_xy (sigma_x / sigma_y split of each step)", ops_strang),
+}
+
+
+def scheme_leg(args, cfgs, stream, world, rank, scheme, warm=1, reps=2):
+    """The same 2048^2 x 1e5-step solves with another step scheme, FP32-mixed, in
+    step groups like EXACT: the fourth-order Magnus step (two Gauss-point samples
+    per step) or the sigma_x / sigma_y split.  Instructions per spinor-step from
+    ops_magnus4 / ops_strang."""
     import torch
 
     from paper_1607_03062_gb300 import binding as B
@@ -441,12 +462,14 @@ def magnus4_leg(args, cfgs, stream, world, rank, warm=1, reps=2):
     nbytes = B.state_bytes(n, n, "fp32_mixed")
     state = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
     mp = torch.empty((n, n), dtype=torch.float32, device="cuda")
-    h = B.create_grid(n, n, g0["px"], g0["py"], "fp32_mixed", "magnus4", 1, stream,
+    label, ops_fn = SCHEME_LEGS[scheme]
+    sample = B.sample_pulse_gauss if scheme == "magnus4" else B.sample_pulse
+    h = B.create_grid(n, n, g0["px"], g0["py"], "fp32_mixed", scheme, 1, stream,
                       state.data_ptr(), nbytes)
     times, ops = [], []
     for k in range(warm + reps):
         c = cfgs[(k * world + rank) % len(cfgs)]
-        a, a_in, a_out, dt = B.sample_pulse_gauss(c["pulse"], args.time_steps)
+        a, a_in, a_out, dt = sample(c["pulse"], args.time_steps)
         B.set_pulse(h, a, dt, a_in, a_out)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -458,13 +481,13 @@ def magnus4_leg(args, cfgs, stream, world, rank, warm=1, reps=2):
         if k >= warm:
             times.append(e0.elapsed_time(e1) / 1e3)
             info = B.get_info(h)
-            ops.append(ops_magnus4(info["cos_degree"], info["sinc_degree"], info["group_steps"]))
+            ops.append(ops_fn(info["cos_degree"], info["sinc_degree"], info["group_steps"]))
     B.destroy_grid(h)
     work = float(n) * n * args.time_steps
     achieved = statistics.mean(o * work / t for o, t in zip(ops, times)) / 1e12
     peak = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     return {"value": work * reps / sum(times), "unit": METRIC, "ms_per_step": 1e3 * statistics.mean(times),
-            "steps": reps, "warmup": warm, "scheme": "magnus4 (fourth order, 2 Gauss points/step)",
+            "steps": reps, "warmup": warm, "scheme": label,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "frac": achieved / peak,
                          "unit": "Tinst/s (FP32 lane instructions)", "ops_per_spinor_step": ops}}
 

@@ -198,8 +198,8 @@ dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps);
  * truncation error over all n_steps stays below 2e-8 in FP32_MIXED, 1e-16 in
  * FP64), theta_max = dt * max|p + A_n| over the box, the tile count, and
  * group_steps G: the number of step operators multiplied into one before each
- * compensated update (FP32_MIXED EXACT and MAGNUS4: the largest of 8, 4, 2 with
- * G * theta_max <= 0.2, else 1; 1 in FP64 and for STRANG_XY).  Not in the paper: with G > 1 the
+ * compensated update (FP32_MIXED, every scheme: the largest of 8, 4, 2 with
+ * G * theta_max <= 0.2, else 1; 1 in FP64).  Not in the paper: with G > 1 the
  * update is paid once per group, and the group's Re(alpha) - 1 is rebuilt from
  * unitarity, so the applied operator stays unitary to FP32 rounding. */
 typedef struct {

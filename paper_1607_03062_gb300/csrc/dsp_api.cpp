@@ -118,12 +118,13 @@ int32_t choose_level(int32_t precision, double theta, int64_t n_steps)
     return dsp::kNumLevels - 1;
 }
 
-// Steps multiplied into one operator before each compensated update (FP32_MIXED
-// EXACT and MAGNUS4): the largest G in {kGroupMax, 4, 2} whose group rotation
+// Steps multiplied into one operator before each compensated update (FP32_MIXED,
+// every scheme): the largest G in {kGroupMax, 4, 2} whose group rotation
 // G * theta_max stays within kGroupAngleMax, else 1.
 int32_t choose_group(int32_t precision, int32_t scheme, double theta_max)
 {
-    if (precision != DSP_FP32_MIXED || scheme == DSP_SCHEME_STRANG_XY)
+    (void)scheme;
+    if (precision != DSP_FP32_MIXED)
         return 1;
     for (int32_t G = dsp::kGroupMax; G >= 2; G /= 2)
         if (G * theta_max <= dsp::kGroupAngleMax)

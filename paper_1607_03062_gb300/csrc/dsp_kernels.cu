@@ -777,20 +777,59 @@ __device__ __forceinline__ void apply_group(Pt &p, V am, V ai, V Qr, V Qi)
     t = vadd(p.bi, dbi); p.lbi = vadd(dbi, vneg(vadd(t, vneg(p.bi)))); p.bi = t;
 }
 
+// STRANG_XY's merged step X(a) Y(b) X(a), 2a = dt Px, b = dt Py, as m = cos b
+// cos 2a - 1 and q = sin b + i cos b sin 2a, from small parts only:
+// m = cx + cy + cx cy (cx = cos 2a - 1, cy = cos b - 1), sin 2a = Px + (sinc - 1) Px,
+// sin b likewise, cos b sin 2a = sin 2a + cy sin 2a.
+template <int DC, int DS, typename Pt, typename V>
+__device__ __forceinline__ void coeffs_strang_group(const Pt &p, const float2 &a, V &m, V &qr,
+                                                    V &qi)
+{
+    const V Px = vadd(p.pxh, vadd(vbc<V>(a.x), p.pxl));
+    const V Py = vadd(p.pyh, vadd(vbc<V>(a.y), p.pyl));
+    const V xx = vmul(Px, Px), xy = vmul(Py, Py);
+    const V cx = vmul(vhorner<V, DC, 1, 0>(xx), xx), cy = vmul(vhorner<V, DC, 1, 0>(xy), xy);
+    const V sx = vfma(vmul(vhorner<V, DS, 1, 1>(xx), xx), Px, Px);
+    qr = vfma(vmul(vhorner<V, DS, 1, 1>(xy), xy), Py, Py);
+    qi = vfma(cy, sx, sx);
+    m = vfma(cx, cy, vadd(cx, cy));
+}
+
+// (m, q) of one step of an EXACT-structured scheme: 0 = EXACT, 1 = STRANG_XY.
+template <int SCHEME, int DC, int DS, typename Pt, typename V>
+__device__ __forceinline__ void coeffs_scheme(const Pt &p, const float2 &a, V &m, V &qr, V &qi)
+{
+    if constexpr (SCHEME == 1)
+        coeffs_strang_group<DC, DS>(p, a, m, qr, qi);
+    else
+        coeffs_group<DC, DS>(p, a, m, qr, qi);
+}
+
+// One step alone through the group update (ragged ends of a grouped STRANG_XY
+// run, or all of an ungrouped one): U - I = [[m, -q], [conj(q), m]].
+template <int SCHEME, int DC, int DS, typename Pt>
+__device__ __forceinline__ void step_single_scheme(Pt &p, const float2 &a)
+{
+    using V = decltype(p.ar);
+    V m, qr, qi;
+    coeffs_scheme<SCHEME, DC, DS>(p, a, m, qr, qi);
+    apply_group(p, m, vbc<V>(0.0f), qr, qi);
+}
+
 // The chain, one step k >= 2 at a time (the second step, with Im alpha still 0,
 // drops its terms):
 //   Re alpha' = Re alpha + m Re alpha - (qr Qr + qi Qi)
 //   Im alpha' = Im alpha + m Im alpha - (qi Qr - qr Qi)
 //   Qr'       = Qr + m Qr + qr Re alpha + qi Im alpha
 //   Qi'       = Qi + m Qi + qi Re alpha - qr Im alpha
-template <int G, int DC, int DS, typename Pt>
+template <int G, int DC, int DS, int SCHEME = 0, typename Pt>
 __device__ __forceinline__ void step_group(Pt &p, const float2 *e)
 {
     using V = decltype(p.ar);
     V m, qr, qi, Qr, Qi;
-    coeffs_group<DC, DS>(p, e[0], m, Qr, Qi);
+    coeffs_scheme<SCHEME, DC, DS>(p, e[0], m, Qr, Qi);
     V Ar = vadd(m, vbc<V>(1.0f));
-    coeffs_group<DC, DS>(p, e[1], m, qr, qi);
+    coeffs_scheme<SCHEME, DC, DS>(p, e[1], m, qr, qi);
     V ai = vfma(vneg(qi), Qr, vmul(qr, Qi));
     V nAr = vfma(m, Ar, vfma(vneg(qr), Qr, vfma(vneg(qi), Qi, Ar)));
     V nQr = vfma(m, Qr, vfma(qr, Ar, Qr));
@@ -800,7 +839,7 @@ __device__ __forceinline__ void step_group(Pt &p, const float2 *e)
     Qi = nQi;
 #pragma unroll kGroupUnroll
     for (int k = 2; k < G; ++k) {
-        coeffs_group<DC, DS>(p, e[k], m, qr, qi);
+        coeffs_scheme<SCHEME, DC, DS>(p, e[k], m, qr, qi);
         nAr = vfma(m, Ar, vfma(vneg(qr), Qr, vfma(vneg(qi), Qi, Ar)));
         const V nai = vfma(m, ai, vfma(vneg(qi), Qr, vfma(qr, Qi, ai)));
         nQr = vfma(m, Qr, vfma(qr, Ar, vfma(qi, ai, Qr)));
@@ -949,6 +988,34 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
         } else {
             ok = run_steps<float2>(R, smem, bars, err, single);
         }
+    } else if constexpr (SCHEME == 1 && packed) {
+        const auto single = [&](const float2 &e) {
+#pragma unroll
+            for (int k = 0; k < S / 2; ++k)
+                step_single_scheme<1, DC, DS>(pk[k], e);
+        };
+        if (R.group == kGroupMax) {
+            ok = run_step_groups<float2, kGroupMax>(R, smem, bars, err, single,
+                                                    [&](const float2 *e) {
+#pragma unroll
+                for (int k = 0; k < S / 2; ++k)
+                    step_group<kGroupMax, DC, DS, 1>(pk[k], e);
+            });
+        } else if (R.group == 4) {
+            ok = run_step_groups<float2, 4>(R, smem, bars, err, single, [&](const float2 *e) {
+#pragma unroll
+                for (int k = 0; k < S / 2; ++k)
+                    step_group<4, DC, DS, 1>(pk[k], e);
+            });
+        } else if (R.group == 2) {
+            ok = run_step_groups<float2, 2>(R, smem, bars, err, single, [&](const float2 *e) {
+#pragma unroll
+                for (int k = 0; k < S / 2; ++k)
+                    step_group<2, DC, DS, 1>(pk[k], e);
+            });
+        } else {
+            ok = run_steps<float2>(R, smem, bars, err, single);
+        }
     } else if constexpr (SCHEME == 2 && packed) {
         const auto single = [&](const float4 &e) {
 #pragma unroll
@@ -1040,7 +1107,7 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
                 step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
         });
     }
-    if constexpr (packed && SCHEME != 1) {
+    if constexpr (packed) {
 #pragma unroll
         for (int k = 0; k < S / 2; ++k)
             unpack_points(pk[k], pt[2 * k], pt[2 * k + 1]);

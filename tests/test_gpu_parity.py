@@ -92,15 +92,19 @@ def test_ragged_tiles_and_chunks(orc, prec, scheme, valley):
 @pytest.mark.parametrize("scheme", ["exact", "strang_xy"])
 def test_pieces_equal_one_launch_bitwise(prec, scheme):
     """Pieces that end on multiples of 8 steps give bitwise the one-launch result;
-    a boundary inside a step group changes rounding only (bitwise for the
-    ungrouped paths: FP64, STRANG_XY, and this pulse's theta_max > 0.1)."""
+    a boundary inside a step group changes rounding only (bitwise where the
+    library takes every step alone: FP64, or group_steps == 1)."""
     grid = {"nx": 100, "ny": 37, "px": (-4, 4), "py": (-4, 4)}
     tab = B.sample_pulse(W.gauss_pulse(2.0, 1.55, 1.0), 3100)
+    g = B.Grid(100, 37, grid["px"], grid["py"], prec, scheme)
+    g.set_pulse(tab[0], tab[3], tab[1], tab[2])
+    group = B.get_info(g.h)["group_steps"]
+    g.close()
     m1, n1 = run_gpu(grid, tab, prec, scheme)
     m2, n2 = run_gpu(grid, tab, prec, scheme, pieces=[1024, 1000, 8, 1068])
     assert np.array_equal(m1, m2) and n1 == n2
     m3, n3 = run_gpu(grid, tab, prec, scheme, pieces=[1023, 1, 1, 2075])
-    if prec == "fp64" or scheme != "exact":
+    if group == 1:
         assert np.array_equal(m1, m3) and n1 == n3
     else:
         assert np.abs(m1 - m3).max() <= 1e-6 and abs(n1 - n3) <= 1e-6 * n1
@@ -111,29 +115,31 @@ def test_pieces_equal_one_launch_bitwise(prec, scheme):
 GROUP_STEPS = {1: 1000, 2: 1600, 4: 3000, 8: 6000}
 
 
+@pytest.mark.parametrize("scheme", ["exact", "strang_xy"])
 @pytest.mark.parametrize("G", sorted(GROUP_STEPS))
-def test_step_groups_vs_oracle_and_pieces(orc, G):
-    """Each FP32-mixed EXACT group size: the library reports it, the result meets
-    the oracle at the FP32-mixed tolerance, pieces ending on multiples of 8 are
-    bitwise the one-launch result, and boundaries inside groups (the ragged
-    single steps at both ends of a launch) change rounding only."""
+def test_step_groups_vs_oracle_and_pieces(orc, G, scheme):
+    """Each FP32-mixed group size, EXACT and STRANG_XY: the library reports it,
+    the result meets the oracle at the FP32-mixed tolerance, pieces ending on
+    multiples of 8 are bitwise the one-launch result, and boundaries inside
+    groups (the ragged single steps at both ends of a launch) change rounding
+    only."""
     grid = {"nx": 48, "ny": 40, "px": (-4, 4), "py": (-4, 4)}
     pulse = W.sin2_pulse(1.0, 1.55, 5.0, eps=0.4)
     n = GROUP_STEPS[G]
     tab = B.sample_pulse(pulse, n)
-    g = B.Grid(48, 40, grid["px"], grid["py"], "fp32_mixed")
+    g = B.Grid(48, 40, grid["px"], grid["py"], "fp32_mixed", scheme)
     g.set_pulse(tab[0], tab[3], tab[1], tab[2])
     info = B.get_info(g.h)
     g.close()
     assert info["group_steps"] == G
     assert G * info["theta_max"] <= 0.2 and (G == 8 or 2 * G * info["theta_max"] > 0.2)
-    ref, nref = run_oracle(orc, grid, orc.pulse_table(pulse, n))
-    m1, n1 = run_gpu(grid, tab)
+    ref, nref = run_oracle(orc, grid, orc.pulse_table(pulse, n), scheme)
+    m1, n1 = run_gpu(grid, tab, "fp32_mixed", scheme)
     assert_close("fp32_mixed", m1, n1, ref, nref)
     cut = [8 * 37, 8 * 51, n - 8 * 88]
-    m2, n2 = run_gpu(grid, tab, pieces=cut)
+    m2, n2 = run_gpu(grid, tab, "fp32_mixed", scheme, pieces=cut)
     assert np.array_equal(m1, m2) and n1 == n2
-    m3, n3 = run_gpu(grid, tab, pieces=[299, 5, 3, n - 307])
+    m3, n3 = run_gpu(grid, tab, "fp32_mixed", scheme, pieces=[299, 5, 3, n - 307])
     assert_close("fp32_mixed", m3, n3, ref, nref)
     if G == 1:
         assert np.array_equal(m1, m3) and n1 == n3
