@@ -136,7 +136,7 @@ class ClockSampler:
 # SHA-256 of the kernel source the counters were taken on; a different source
 # means the counters are stale and the traffic is reported as null.
 KERNEL_TRAFFIC = {
-    "evolve_mixed_kernel": {"bytes": 101.87e6, "source_sha256": "d2c34b25db4392e908943ff85c2cb4dc679af626b37d882d511287857eb7cf5e",
+    "evolve_mixed_kernel": {"bytes": 104.87e6, "source_sha256": "bd23e194c75878e6a77f9a2ebcf07f43beca24e9c1bc91deb472677456419df9",
                             "profile": "profiles/evolve_mixed_lzs2048_1e5_traffic.md"},
 }
 
