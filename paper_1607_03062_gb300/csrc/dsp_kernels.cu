@@ -12,9 +12,10 @@
 // spinors, FP64: 512 threads x 2 spinors):
 //   * the spinors stay in registers across all steps of a launch: one 16-byte
 //     read and one write per spinor plane per launch;
-//   * A(t) is staged in shared memory in chunks of 1024 steps by 1-D bulk
-//     copies (cp.async.bulk) completing on an mbarrier, double buffered, so the
-//     step loop reads it with one broadcast LDS.128 per step;
+//   * A(t) is staged in shared memory in 16 KB chunks (2048 FP32_MIXED steps,
+//     1024 FP64 ones) by 1-D bulk copies (cp.async.bulk) completing on an
+//     mbarrier, double buffered, so the step loop reads each entry with one
+//     broadcast shared-memory load;
 //   * cos(theta) - 1 and sin(theta)/theta are evaluated as their Taylor series
 //     in x = theta^2 = |dt P|^2 (no square root, no sin/cos call): the degree is
 //     chosen per request on the host from theta_max so truncation stays below
@@ -23,12 +24,12 @@
 //     point to ~1e-16 relative), dt*A(t_n) is one float per step, and
 //     P_n = p_hi + (A_n + p_lo): the FP32 roundings of P then change from step
 //     to step with A instead of shifting every step's momentum by the same
-//     amount, and the first one is at A's scale, not P's; the spinor is stored
-//     as hi + lo and each update adds
-//     the increment (U - I) psi with a Fast2Sum, so the FP32 rounding of psi does
-//     not random-walk over 1e5 steps; the EXACT scheme multiplies 2, 4 or 8
-//     steps into one SU(2) matrix first, so the compensated update is paid once
-//     per group;
+//     amount, and the first one is at A's scale, not P's;
+//   * FP32_MIXED: the spinor is stored as hi + lo and each update adds the
+//     increment (U - I) psi with a Fast2Sum, so the FP32 rounding of psi does not
+//     random-walk over 1e5 steps; every scheme multiplies 2, 4 or 8 steps into one
+//     SU(2) matrix first, so the compensated update is paid once per group, and
+//     two momenta share each packed FP32x2 instruction;
 //   * the projection and the per-tile partial sums of |c+|^2 are fused into the
 //     last launch; partial sums use a fixed pairwise tree, so the density is
 //     bitwise reproducible and independent of the batch a request ran in.
