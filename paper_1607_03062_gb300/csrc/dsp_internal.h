@@ -61,9 +61,9 @@ struct ReqDesc {
     int32_t init_identity;  // with fresh: start from the column (1, 0) of the identity
                             // (the launch then computes the first column of the
                             // product of its steps' operators)
-    int32_t group;   // FP32_MIXED (every scheme): the steps (G j, ..., G j + G - 1) of absolute index
-                     // are multiplied into one operator before one compensated update;
-                     // G = 1 (every step alone), 2, 4 or kGroupMax
+    int32_t group;   // FP32_MIXED (every scheme): the steps (G j, ..., G j + G - 1) of
+                     // absolute index are multiplied into one operator before one
+                     // compensated update; G = 1 (every step alone), 2, 4 or kGroupMax
     int32_t withhold_first_copy;  // test hook: announce chunk 0 but never copy it, so the
                                   // bounded wait for it runs out (no fault, no hang)
     int64_t table_steps;          // entries in the table (checked by bounds-check builds)
