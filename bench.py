@@ -136,7 +136,7 @@ class ClockSampler:
 # SHA-256 of the kernel source the counters were taken on; a different source
 # means the counters are stale and the traffic is reported as null.
 KERNEL_TRAFFIC = {
-    "evolve_mixed_kernel": {"bytes": 104.87e6, "source_sha256": "bd23e194c75878e6a77f9a2ebcf07f43beca24e9c1bc91deb472677456419df9",
+    "evolve_mixed_kernel": {"bytes": 105.94e6, "source_sha256": "d4cad9445359aed6ac5218e5cf58be4f50217d99314e33baf465edf77acc126f",
                             "profile": "profiles/evolve_mixed_lzs2048_1e5_traffic.md"},
 }
 
