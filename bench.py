@@ -609,6 +609,13 @@ def cpu_baseline(cfg, seconds, nsteps, gpu_maps=None):
             got = m.ravel()[idx]
             acc[prec] = {"max_abs_err_cplus2": float(np.abs(got - ref).max()),
                          "sampled_density_rel_err": float(abs(got.sum() - ref.sum()) / ref.sum())}
+        if "fp32_mixed" in gpu_maps and "fp64" in gpu_maps:
+            # every point of the grid: FP32-mixed against the FP64 kernel's map (which
+            # meets the oracle to ~1e-13 on the points above)
+            err = np.abs(gpu_maps["fp32_mixed"] - gpu_maps["fp64"]).ravel()
+            acc["fp32_mixed_vs_fp64_every_point"] = {
+                "points": int(err.size), "max_abs_err_cplus2": float(err.max()),
+                "p99_9_abs_err_cplus2": float(np.quantile(err, 0.999))}
     return base, acc
 
 
