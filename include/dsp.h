@@ -108,7 +108,7 @@ dsp_status dsp_set_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, doub
 /* Advances every point by `steps` time steps (Sec. III, Eq. (ev_op_dt)) from
  * the cursor; steps >= 0 and cursor + steps <= n_steps, else DSP_E_STATE.
  * The spinors stay on the device.  Evolving in pieces gives bitwise the same
- * state as evolving at once when every piece ends on a multiple of 8 steps:
+ * state as evolving at once when every piece ends on a multiple of 16 steps:
  * with grouped steps (group_steps G > 1 in dsp_get_info) the steps
  * (G j, ..., G j + G - 1) are multiplied into one operator before the
  * compensated update, and a piece boundary inside such a group changes
@@ -198,7 +198,7 @@ dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps);
  * truncation error over all n_steps stays below 2e-8 in FP32_MIXED, 1e-16 in
  * FP64), theta_max = dt * max|p + A_n| over the box, the tile count, and
  * group_steps G: the number of step operators multiplied into one before each
- * compensated update (FP32_MIXED, every scheme: the largest of 8, 4, 2 with
+ * compensated update (FP32_MIXED, every scheme: the largest of 16, 8, 4, 2 with
  * G * theta_max <= 0.2, else 1; 1 in FP64).  Not in the paper: with G > 1 the
  * update is paid once per group, and the group's Re(alpha) - 1 is rebuilt from
  * unitarity, so the applied operator stays unitary to FP32 rounding. */
@@ -297,7 +297,7 @@ typedef struct {
 /* hbm_budget_bytes > 0: admission limit on the sum of device footprints
  * (state + table + map + partial sums) of the active requests; max_active
  * >= 1; chunk_steps >= 1: steps per batched launch, rounded down to a multiple
- * of 8 when it is 8 or more (a request's result is then bitwise the same alone
+ * of 16 when it is 16 or more (a request's result is then bitwise the same alone
  * or in any mix, see dsp_evolve).
  * cuda_stream as above. */
 dsp_status dsp_server_create(int64_t hbm_budget_bytes, int32_t max_active, int64_t chunk_steps,

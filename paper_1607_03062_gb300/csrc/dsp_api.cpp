@@ -119,14 +119,18 @@ int32_t choose_level(int32_t precision, double theta, int64_t n_steps)
 }
 
 // Steps multiplied into one operator before each compensated update (FP32_MIXED,
-// every scheme): the largest G in {kGroupMax, 4, 2} whose group rotation
-// G * theta_max stays within kGroupAngleMax, else 1.
-int32_t choose_group(int32_t precision, int32_t scheme, double theta_max)
+// every scheme): the largest G in {16 (EXACT only), 8, 4, 2} whose group rotation
+// G * theta_max stays within kGroupAngleMax, else 1.  (Groups of 16 for the other
+// schemes would add kernel instantiations, and build time, for a few per cent on
+// variants the benchmark does not lead with.)
+int32_t choose_group(int32_t precision, int32_t scheme, int32_t level, double theta_max)
 {
-    (void)scheme;
     if (precision != DSP_FP32_MIXED)
         return 1;
-    for (int32_t G = dsp::kGroupMax; G >= 2; G /= 2)
+    const dsp::SeriesLevel lv = dsp::kLevelsF32[level];
+    if (lv.dc > dsp::kGroupMaxDegree || lv.ds > dsp::kGroupMaxDegree)
+        return 1;  // the kernels have no group path at this level
+    for (int32_t G = scheme == DSP_SCHEME_EXACT ? dsp::kGroupMax : 8; G >= 2; G /= 2)
         if (G * theta_max <= dsp::kGroupAngleMax)
             return G;
     return 1;
@@ -491,7 +495,7 @@ dsp_status prepare_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, doub
     g->a_out[1] = a_out[1];
     g->theta_max = tmax;
     g->level = choose_level(g->precision, tmax, n_steps);
-    g->group = choose_group(g->precision, g->scheme, tmax);
+    g->group = choose_group(g->precision, g->scheme, g->level, tmax);
     g->fresh = true;
     g->projected = false;
     return DSP_OK;

@@ -63,16 +63,18 @@ struct ReqDesc {
                             // product of its steps' operators)
     int32_t group;   // FP32_MIXED (every scheme): the steps (G j, ..., G j + G - 1) of
                      // absolute index are multiplied into one operator before one
-                     // compensated update; G = 1 (every step alone), 2, 4 or kGroupMax
+                     // compensated update; G = 1 (every step alone), 2, 4, 8 or kGroupMax
     int32_t withhold_first_copy;  // test hook: announce chunk 0 but never copy it, so the
                                   // bounded wait for it runs out (no fault, no hang)
     int64_t table_steps;          // entries in the table (checked by bounds-check builds)
 };
 
-// Steps are grouped (G = 8, 4 or 2, the largest allowed) when G * theta_max <=
+// Steps are grouped (G = 16, 8, 4 or 2, the largest allowed) when G * theta_max <=
 // kGroupAngleMax: the group's increment (U_G ... U_1 - I) psi then stays small
 // next to psi, where the compensated (Fast2Sum) update is exact.
-constexpr int kGroupMax = 8;
+constexpr int kGroupMax = 16;
+// Highest series degree with step groups (see kGroupedLevel in the kernels).
+constexpr int kGroupMaxDegree = 4;
 constexpr double kGroupAngleMax = 0.2;
 
 static_assert(sizeof(ReqDesc) * kMaxReqPerLaunch + 64 < 32764, "kernel parameter limit");

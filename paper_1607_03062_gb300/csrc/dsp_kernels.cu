@@ -27,7 +27,7 @@
 //     amount, and the first one is at A's scale, not P's;
 //   * FP32_MIXED: the spinor is stored as hi + lo and each update adds the
 //     increment (U - I) psi with a Fast2Sum, so the FP32 rounding of psi does not
-//     random-walk over 1e5 steps; every scheme multiplies 2, 4 or 8 steps into one
+//     random-walk over 1e5 steps; every scheme multiplies 2 to 16 steps into one
 //     SU(2) matrix first, so the compensated update is paid once per group, and
 //     two momenta share each packed FP32x2 instruction;
 //   * the projection and the per-tile partial sums of |c+|^2 are fused into the
@@ -261,6 +261,12 @@ constexpr int kGroupUnroll = DSP_GROUP_UNROLL;  // chain loop inside one group (
 #define DSP_MAGNUS_GROUP_UNROLL 1
 #endif
 constexpr int kMagnusGroupUnroll = DSP_MAGNUS_GROUP_UNROLL;  // the MAGNUS4 chain's
+// Series levels that can run in step groups.  G >= 2 needs theta_max <= 0.1, where a
+// level above degree kGroupMaxDegree is chosen only for runs of more than ~3e8 steps;
+// the host keeps G = 1 at those levels (choose_group), and no group code is compiled
+// for them.
+template <int DC, int DS>
+constexpr bool kGroupedLevel = DC <= kGroupMaxDegree && DS <= kGroupMaxDegree;
 constexpr int kMixedSpt = DSP_MIXED_SPT;
 constexpr int kMixedThreads = kTilePoints / kMixedSpt;
 constexpr int kMixedMinBlocks = DSP_MIXED_MINB;  // resident CTAs per SM the registers allow
@@ -967,26 +973,36 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
             for (int k = 0; k < S / 2; ++k)
                 step_exact2<DC, DS>(pk[k], e);
         };
-        if (R.group == kGroupMax) {
-            ok = run_step_groups<float2, kGroupMax>(R, smem, bars, err, single,
-                                                    [&](const float2 *e) {
+        if constexpr (kGroupedLevel<DC, DS>) {
+            if (R.group == kGroupMax) {
+                ok = run_step_groups<float2, kGroupMax>(R, smem, bars, err, single,
+                                                        [&](const float2 *e) {
 #pragma unroll
-                for (int k = 0; k < S / 2; ++k)
-                    step_group<kGroupMax, DC, DS>(pk[k], e);
-            });
-        } else if (R.group == 4) {
-            ok = run_step_groups<float2, 4>(R, smem, bars, err, single, [&](const float2 *e) {
+                    for (int k = 0; k < S / 2; ++k)
+                        step_group<kGroupMax, DC, DS>(pk[k], e);
+                });
+            } else if (R.group == 8) {
+                ok = run_step_groups<float2, 8>(R, smem, bars, err, single, [&](const float2 *e) {
 #pragma unroll
-                for (int k = 0; k < S / 2; ++k)
-                    step_group<4, DC, DS>(pk[k], e);
-            });
-        } else if (R.group == 2) {
-            ok = run_step_groups<float2, 2>(R, smem, bars, err, single, [&](const float2 *e) {
+                    for (int k = 0; k < S / 2; ++k)
+                        step_group<8, DC, DS>(pk[k], e);
+                });
+            } else if (R.group == 4) {
+                ok = run_step_groups<float2, 4>(R, smem, bars, err, single, [&](const float2 *e) {
 #pragma unroll
-                for (int k = 0; k < S / 2; ++k)
-                    step_pair2<DC, DS>(pk[k], e[0], e[1]);
-            });
-        } else {
+                    for (int k = 0; k < S / 2; ++k)
+                        step_group<4, DC, DS>(pk[k], e);
+                });
+            } else if (R.group == 2) {
+                ok = run_step_groups<float2, 2>(R, smem, bars, err, single, [&](const float2 *e) {
+#pragma unroll
+                    for (int k = 0; k < S / 2; ++k)
+                        step_pair2<DC, DS>(pk[k], e[0], e[1]);
+                });
+            } else {
+                ok = run_steps<float2>(R, smem, bars, err, single);
+            }
+        } else {  // no group paths at this level (the host keeps G = 1)
             ok = run_steps<float2>(R, smem, bars, err, single);
         }
     } else if constexpr (SCHEME == 1 && packed) {
@@ -995,26 +1011,29 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
             for (int k = 0; k < S / 2; ++k)
                 step_single_scheme<1, DC, DS>(pk[k], e);
         };
-        if (R.group == kGroupMax) {
-            ok = run_step_groups<float2, kGroupMax>(R, smem, bars, err, single,
-                                                    [&](const float2 *e) {
+        if constexpr (kGroupedLevel<DC, DS>) {
+            if (R.group == 8) {
+                ok = run_step_groups<float2, 8>(R, smem, bars, err, single, [&](const float2 *e) {
 #pragma unroll
-                for (int k = 0; k < S / 2; ++k)
-                    step_group<kGroupMax, DC, DS, 1>(pk[k], e);
-            });
-        } else if (R.group == 4) {
-            ok = run_step_groups<float2, 4>(R, smem, bars, err, single, [&](const float2 *e) {
+                    for (int k = 0; k < S / 2; ++k)
+                        step_group<8, DC, DS, 1>(pk[k], e);
+                });
+            } else if (R.group == 4) {
+                ok = run_step_groups<float2, 4>(R, smem, bars, err, single, [&](const float2 *e) {
 #pragma unroll
-                for (int k = 0; k < S / 2; ++k)
-                    step_group<4, DC, DS, 1>(pk[k], e);
-            });
-        } else if (R.group == 2) {
-            ok = run_step_groups<float2, 2>(R, smem, bars, err, single, [&](const float2 *e) {
+                    for (int k = 0; k < S / 2; ++k)
+                        step_group<4, DC, DS, 1>(pk[k], e);
+                });
+            } else if (R.group == 2) {
+                ok = run_step_groups<float2, 2>(R, smem, bars, err, single, [&](const float2 *e) {
 #pragma unroll
-                for (int k = 0; k < S / 2; ++k)
-                    step_group<2, DC, DS, 1>(pk[k], e);
-            });
-        } else {
+                    for (int k = 0; k < S / 2; ++k)
+                        step_group<2, DC, DS, 1>(pk[k], e);
+                });
+            } else {
+                ok = run_steps<float2>(R, smem, bars, err, single);
+            }
+        } else {  // no group paths at this level (the host keeps G = 1)
             ok = run_steps<float2>(R, smem, bars, err, single);
         }
     } else if constexpr (SCHEME == 2 && packed) {
@@ -1023,26 +1042,29 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
             for (int k = 0; k < S / 2; ++k)
                 step_magnus2<DC, DS>(pk[k], e);
         };
-        if (R.group == kGroupMax) {
-            ok = run_step_groups<float4, kGroupMax>(R, smem, bars, err, single,
-                                                    [&](const float4 *e) {
+        if constexpr (kGroupedLevel<DC, DS>) {
+            if (R.group == 8) {
+                ok = run_step_groups<float4, 8>(R, smem, bars, err, single, [&](const float4 *e) {
 #pragma unroll
-                for (int k = 0; k < S / 2; ++k)
-                    step_group_magnus<kGroupMax, DC, DS>(pk[k], e);
-            });
-        } else if (R.group == 4) {
-            ok = run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
+                    for (int k = 0; k < S / 2; ++k)
+                        step_group_magnus<8, DC, DS>(pk[k], e);
+                });
+            } else if (R.group == 4) {
+                ok = run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
 #pragma unroll
-                for (int k = 0; k < S / 2; ++k)
-                    step_group_magnus<4, DC, DS>(pk[k], e);
-            });
-        } else if (R.group == 2) {
-            ok = run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
+                    for (int k = 0; k < S / 2; ++k)
+                        step_group_magnus<4, DC, DS>(pk[k], e);
+                });
+            } else if (R.group == 2) {
+                ok = run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
 #pragma unroll
-                for (int k = 0; k < S / 2; ++k)
-                    step_group_magnus<2, DC, DS>(pk[k], e);
-            });
-        } else {
+                    for (int k = 0; k < S / 2; ++k)
+                        step_group_magnus<2, DC, DS>(pk[k], e);
+                });
+            } else {
+                ok = run_steps<float4>(R, smem, bars, err, single);
+            }
+        } else {  // no group paths at this level (the host keeps G = 1)
             ok = run_steps<float4>(R, smem, bars, err, single);
         }
     } else if constexpr (SCHEME == 0) {
@@ -1051,26 +1073,36 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
             for (int s = 0; s < S; ++s)
                 step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
         };
-        if (R.group == kGroupMax) {
-            ok = run_step_groups<float2, kGroupMax>(R, smem, bars, err, single,
-                                                    [&](const float2 *e) {
+        if constexpr (kGroupedLevel<DC, DS>) {
+            if (R.group == kGroupMax) {
+                ok = run_step_groups<float2, kGroupMax>(R, smem, bars, err, single,
+                                                        [&](const float2 *e) {
 #pragma unroll
-                for (int s = 0; s < S; ++s)
-                    step_group<kGroupMax, DC, DS>(pt[s], e);
-            });
-        } else if (R.group == 4) {
-            ok = run_step_groups<float2, 4>(R, smem, bars, err, single, [&](const float2 *e) {
+                    for (int s = 0; s < S; ++s)
+                        step_group<kGroupMax, DC, DS>(pt[s], e);
+                });
+            } else if (R.group == 8) {
+                ok = run_step_groups<float2, 8>(R, smem, bars, err, single, [&](const float2 *e) {
 #pragma unroll
-                for (int s = 0; s < S; ++s)
-                    step_group<4, DC, DS>(pt[s], e);
-            });
-        } else if (R.group == 2) {
-            ok = run_step_groups<float2, 2>(R, smem, bars, err, single, [&](const float2 *e) {
+                    for (int s = 0; s < S; ++s)
+                        step_group<8, DC, DS>(pt[s], e);
+                });
+            } else if (R.group == 4) {
+                ok = run_step_groups<float2, 4>(R, smem, bars, err, single, [&](const float2 *e) {
 #pragma unroll
-                for (int s = 0; s < S; ++s)
-                    step_pair_mixed<DC, DS>(pt[s], e[0], e[1]);
-            });
-        } else {
+                    for (int s = 0; s < S; ++s)
+                        step_group<4, DC, DS>(pt[s], e);
+                });
+            } else if (R.group == 2) {
+                ok = run_step_groups<float2, 2>(R, smem, bars, err, single, [&](const float2 *e) {
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+                        step_pair_mixed<DC, DS>(pt[s], e[0], e[1]);
+                });
+            } else {
+                ok = run_steps<float2>(R, smem, bars, err, single);
+            }
+        } else {  // no group paths at this level (the host keeps G = 1)
             ok = run_steps<float2>(R, smem, bars, err, single);
         }
     } else if constexpr (SCHEME == 2) {
@@ -1079,26 +1111,29 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
             for (int s = 0; s < S; ++s)
                 step_mixed<SCHEME, DC, DS>(pt[s], make_float2(e.x, e.y), make_float2(e.z, e.w));
         };
-        if (R.group == kGroupMax) {
-            ok = run_step_groups<float4, kGroupMax>(R, smem, bars, err, single,
-                                                    [&](const float4 *e) {
+        if constexpr (kGroupedLevel<DC, DS>) {
+            if (R.group == 8) {
+                ok = run_step_groups<float4, 8>(R, smem, bars, err, single, [&](const float4 *e) {
 #pragma unroll
-                for (int s = 0; s < S; ++s)
-                    step_group_magnus<kGroupMax, DC, DS>(pt[s], e);
-            });
-        } else if (R.group == 4) {
-            ok = run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
+                    for (int s = 0; s < S; ++s)
+                        step_group_magnus<8, DC, DS>(pt[s], e);
+                });
+            } else if (R.group == 4) {
+                ok = run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
 #pragma unroll
-                for (int s = 0; s < S; ++s)
-                    step_group_magnus<4, DC, DS>(pt[s], e);
-            });
-        } else if (R.group == 2) {
-            ok = run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
+                    for (int s = 0; s < S; ++s)
+                        step_group_magnus<4, DC, DS>(pt[s], e);
+                });
+            } else if (R.group == 2) {
+                ok = run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
 #pragma unroll
-                for (int s = 0; s < S; ++s)
-                    step_group_magnus<2, DC, DS>(pt[s], e);
-            });
-        } else {
+                    for (int s = 0; s < S; ++s)
+                        step_group_magnus<2, DC, DS>(pt[s], e);
+                });
+            } else {
+                ok = run_steps<float4>(R, smem, bars, err, single);
+            }
+        } else {  // no group paths at this level (the host keeps G = 1)
             ok = run_steps<float4>(R, smem, bars, err, single);
         }
     } else {

@@ -91,7 +91,7 @@ def test_ragged_tiles_and_chunks(orc, prec, scheme, valley):
 @pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
 @pytest.mark.parametrize("scheme", ["exact", "strang_xy"])
 def test_pieces_equal_one_launch_bitwise(prec, scheme):
-    """Pieces that end on multiples of 8 steps give bitwise the one-launch result;
+    """Pieces that end on multiples of 16 steps give bitwise the one-launch result;
     a boundary inside a step group changes rounding only (bitwise where the
     library takes every step alone: FP64, or group_steps == 1)."""
     grid = {"nx": 100, "ny": 37, "px": (-4, 4), "py": (-4, 4)}
@@ -101,7 +101,7 @@ def test_pieces_equal_one_launch_bitwise(prec, scheme):
     group = B.get_info(g.h)["group_steps"]
     g.close()
     m1, n1 = run_gpu(grid, tab, prec, scheme)
-    m2, n2 = run_gpu(grid, tab, prec, scheme, pieces=[1024, 1000, 8, 1068])
+    m2, n2 = run_gpu(grid, tab, prec, scheme, pieces=[1024, 992, 16, 1068])
     assert np.array_equal(m1, m2) and n1 == n2
     m3, n3 = run_gpu(grid, tab, prec, scheme, pieces=[1023, 1, 1, 2075])
     if group == 1:
@@ -111,8 +111,8 @@ def test_pieces_equal_one_launch_bitwise(prec, scheme):
 
 
 # 5-cycle sin^2 pulse on [-4, 4]^2 (theta_max ~ 128 / n_steps): the step count
-# picks the FP32-mixed group size G (the largest of 8, 4, 2 with G theta_max <= 0.2).
-GROUP_STEPS = {1: 1000, 2: 1600, 4: 3000, 8: 6000}
+# picks the FP32-mixed group size G (the largest of 16, 8, 4, 2 with G theta_max <= 0.2).
+GROUP_STEPS = {1: 1000, 2: 1600, 4: 3000, 8: 6000, 16: 12000}
 
 
 @pytest.mark.parametrize("scheme", ["exact", "strang_xy"])
@@ -120,7 +120,7 @@ GROUP_STEPS = {1: 1000, 2: 1600, 4: 3000, 8: 6000}
 def test_step_groups_vs_oracle_and_pieces(orc, G, scheme):
     """Each FP32-mixed group size, EXACT and STRANG_XY: the library reports it,
     the result meets the oracle at the FP32-mixed tolerance, pieces ending on
-    multiples of 8 are bitwise the one-launch result, and boundaries inside
+    multiples of 16 are bitwise the one-launch result, and boundaries inside
     groups (the ragged single steps at both ends of a launch) change rounding
     only."""
     grid = {"nx": 48, "ny": 40, "px": (-4, 4), "py": (-4, 4)}
@@ -132,11 +132,11 @@ def test_step_groups_vs_oracle_and_pieces(orc, G, scheme):
     info = B.get_info(g.h)
     g.close()
     assert info["group_steps"] == G
-    assert G * info["theta_max"] <= 0.2 and (G == 8 or 2 * G * info["theta_max"] > 0.2)
+    assert G * info["theta_max"] <= 0.2 and (G == 16 or 2 * G * info["theta_max"] > 0.2)
     ref, nref = run_oracle(orc, grid, orc.pulse_table(pulse, n), scheme)
     m1, n1 = run_gpu(grid, tab, "fp32_mixed", scheme)
     assert_close("fp32_mixed", m1, n1, ref, nref)
-    cut = [8 * 37, 8 * 51, n - 8 * 88]
+    cut = [16 * 19, 16 * 25, n - 16 * 44]
     m2, n2 = run_gpu(grid, tab, "fp32_mixed", scheme, pieces=cut)
     assert np.array_equal(m1, m2) and n1 == n2
     m3, n3 = run_gpu(grid, tab, "fp32_mixed", scheme, pieces=[299, 5, 3, n - 307])
@@ -262,7 +262,7 @@ def test_checkpoint_resume_bitwise(prec):
     a_mid, a_in, a_out, dt = tab
     h1 = B.create_grid(70, 30, (-4, 4), (-4, 4), prec)
     B.set_pulse(h1, a_mid, dt, a_in, a_out)
-    B.evolve(h1, 608)  # a multiple of 8: resuming meets the same step groups
+    B.evolve(h1, 608)  # a multiple of 16: resuming meets the same step groups
     buf = np.zeros(B.state_bytes(70, 30, prec), dtype=np.uint8)
     cur = B.save_state(h1, buf)
     B.destroy_grid(h1)
@@ -404,7 +404,7 @@ def test_magnus4_ragged_against_oracle(orc, prec, valley):
 def test_magnus4_step_groups_vs_oracle_and_pieces(orc, G):
     """FP32-mixed MAGNUS4 in each group size (the same step counts pick the same
     G as for EXACT): the library reports it, the result meets the oracle at the
-    FP32-mixed tolerance, pieces ending on multiples of 8 are bitwise the
+    FP32-mixed tolerance, pieces ending on multiples of 16 are bitwise the
     one-launch result, and boundaries inside groups change rounding only."""
     grid = {"nx": 48, "ny": 40, "px": (-4, 4), "py": (-4, 4)}
     pulse = W.sin2_pulse(1.0, 1.55, 5.0, eps=0.4)
@@ -420,7 +420,7 @@ def test_magnus4_step_groups_vs_oracle_and_pieces(orc, G):
                                      scheme="magnus4")
     m1, n1 = run_gpu(grid, tab, "fp32_mixed", "magnus4")
     assert_close("fp32_mixed", m1, n1, ref, nref)
-    m2, n2 = run_gpu(grid, tab, "fp32_mixed", "magnus4", pieces=[8 * 37, 8 * 51, n - 8 * 88])
+    m2, n2 = run_gpu(grid, tab, "fp32_mixed", "magnus4", pieces=[16 * 19, 16 * 25, n - 16 * 44])
     assert np.array_equal(m1, m2) and n1 == n2
     m3, n3 = run_gpu(grid, tab, "fp32_mixed", "magnus4", pieces=[299, 5, 3, n - 307])
     assert_close("fp32_mixed", m3, n3, ref, nref)
