@@ -131,8 +131,9 @@ def test_step_groups_vs_oracle_and_pieces(orc, G, scheme):
     g.set_pulse(tab[0], tab[3], tab[1], tab[2])
     info = B.get_info(g.h)
     g.close()
+    G = min(G, 16 if scheme == "exact" else 8)  # groups of 16 for EXACT only
     assert info["group_steps"] == G
-    assert G * info["theta_max"] <= 0.2 and (G == 16 or 2 * G * info["theta_max"] > 0.2)
+    assert G * info["theta_max"] <= 0.2 and (G >= 8 or 2 * G * info["theta_max"] > 0.2)
     ref, nref = run_oracle(orc, grid, orc.pulse_table(pulse, n), scheme)
     m1, n1 = run_gpu(grid, tab, "fp32_mixed", scheme)
     assert_close("fp32_mixed", m1, n1, ref, nref)
@@ -414,6 +415,7 @@ def test_magnus4_step_groups_vs_oracle_and_pieces(orc, G):
     g.set_pulse(tab[0], tab[3], tab[1], tab[2])
     info = B.get_info(g.h)
     g.close()
+    G = min(G, 8)  # MAGNUS4 groups stop at 8
     assert info["group_steps"] == G
     a, a_in, a_out, dt = orc.pulse_table_gauss(pulse, n)
     ref, _, _, nref = orc.solve_grid(48, 40, grid["px"], grid["py"], a, dt, a_in, a_out,
