@@ -136,7 +136,7 @@ class ClockSampler:
 # SHA-256 of the kernel source the counters were taken on; a different source
 # means the counters are stale and the traffic is reported as null.
 KERNEL_TRAFFIC = {
-    "evolve_mixed_kernel": {"bytes": 105.94e6, "source_sha256": "d4cad9445359aed6ac5218e5cf58be4f50217d99314e33baf465edf77acc126f",
+    "evolve_mixed_kernel": {"bytes": 103.58e6, "source_sha256": "49af387877960baa9b3d1202a97696e556fd6116cf6921efd3f793d3c8d428a5",
                             "profile": "profiles/evolve_mixed_lzs2048_1e5_traffic.md"},
 }
 
