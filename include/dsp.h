@@ -56,8 +56,9 @@ typedef int32_t dsp_status;
 #define DSP_FP64 0       /* everything in FP64                                      */
 #define DSP_FP32_MIXED 1 /* spinor in compensated FP32 (hi + lo); dt P_n formed as
                             dt p_hi + (dt A_n + dt p_lo) with dt p an FP32 hi/lo
-                            pair; cos/sin of the phase argument dt|P| in FP32;
-                            initial state and projection in FP64                   */
+                            pair and dt A_n one FP32 per step, rounded on the host
+                            with error feedback; cos/sin of the phase argument
+                            dt|P| in FP32; initial state in FP64               */
 
 /* Time-step scheme. */
 #define DSP_SCHEME_EXACT 0     /* the paper's closed-form exponential (Sec. III)    */
@@ -90,6 +91,35 @@ dsp_status dsp_create_grid(int32_t nx, int32_t ny, double px_min, double px_max,
                            void *cuda_stream, void *state_dev, int64_t state_dev_bytes,
                            dsp_grid **out);
 
+/* Creates a grid that holds the rows [row_begin, row_end) of the nx by ny grid
+ * on the box (0 <= row_begin < row_end <= ny): a band for sharding one grid's
+ * momenta across devices (they are independent, Sec. III).  Its nodes are the
+ * full grid's, p_y(j) = py_min + (j + 1/2)(py_max - py_min)/ny for the global
+ * row j, and every choice that depends on the grid (the step condition, the
+ * series degrees, the step-group size: all taken over the full box) is the full
+ * grid's, so each point of the band evolves and projects bitwise as in the
+ * full grid.  Arrays (state, map) hold the band's rows only,
+ * [row_end - row_begin][nx]; dsp_state_bytes(nx, row_end - row_begin, ...)
+ * sizes the state.  dsp_reduce_density returns the band's share of the full
+ * grid's density (the same 4/(2 pi)^2 hx hy factor, summed over the band's
+ * points): the shares of all bands add up to the full density up to rounding
+ * (their partial sums are grouped differently).  Other arguments and errors as
+ * in dsp_create_grid; nx * (row_end - row_begin) <= 2^31 - 1. */
+dsp_status dsp_create_band(int32_t nx, int32_t ny, int32_t row_begin, int32_t row_end,
+                           double px_min, double px_max, double py_min, double py_max,
+                           int32_t precision, int32_t scheme, int32_t valley, void *cuda_stream,
+                           void *state_dev, int64_t state_dev_bytes, dsp_grid **out);
+
+/* keep = 1 (the default): every launch leaves the spinor state in device
+ * memory.  keep = 0: the launch that takes the last step and projects in the
+ * same kernel (dsp_solve, dsp_solve_host) does not write the final state back,
+ * saving 32 bytes of HBM writes per point when only the map and the density
+ * are wanted.  The final state is then gone: dsp_project, dsp_solve and
+ * dsp_save_state return DSP_E_STATE until the next dsp_set_pulse or
+ * dsp_load_state.  The map and the density are bitwise the same either way.
+ * Not in the paper (a memory-traffic option). */
+dsp_status dsp_set_keep_final_state(dsp_grid *g, int32_t keep);
+
 /* Sets the pulse: a_mid is a host array [n_steps][2] of (A_x, A_y) sampled at
  * the step midpoints t_i + (n + 1/2) dt (Sec. III, Eq. (approx_time)) -- for
  * DSP_SCHEME_MAGNUS4 it is [n_steps][2][2], (A_x, A_y) at t_i + (n + 1/2 -
@@ -120,7 +150,11 @@ dsp_status dsp_evolve(dsp_grid *g, int64_t steps);
  * double for DSP_FP64, float for DSP_FP32_MIXED.  Needs cursor == n_steps
  * (DSP_E_STATE otherwise).  Also leaves per-tile FP64 partial sums for
  * dsp_reduce_density.  Points with |p + A_out| == 0 get |c+|^2 = 0.
- * Asynchronous. */
+ * In both precisions |c+|^2 is evaluated in double-float arithmetic (pairs of
+ * FP32, about 48 bits, ~1e-14 absolute), the same code as the projection fused
+ * into the last evolve launch, so the two give the same bits.  A projection of
+ * a state already on the device reads it (32 bytes per point) without writing
+ * it back and writes the map (4 or 8 bytes per point).  Asynchronous. */
 dsp_status dsp_project(dsp_grid *g, void *map_dev);
 
 /* Reduces the last projection to the pair density n (eV^2) with a fixed-order
@@ -138,19 +172,23 @@ dsp_status dsp_reduce_density(dsp_grid *g, double *n_host);
  *   map_dev: the caller's device map, nx*ny values row-major [ny][nx], double
  *     for DSP_FP64 or float for DSP_FP32_MIXED (as written by dsp_project);
  *   the box and nx, ny give hx = (px_max - px_min)/nx, hy likewise, and
- *   *n_host receives 4/(2 pi)^2 * hx * hy * sum |c+|^2 (Sec. II, Eq.
- *   (pair_prod_homo)), summed in the same fixed order as dsp_reduce_density
- *   (bitwise equal to it for an FP64 map).
+ *   *n_host receives 4/(2 pi)^2 * hx * hy * sum |c+|^2, the quantity
+ *   dsp_reduce_density returns, summed in the same fixed order (bitwise equal
+ *   to it for an FP64 map).
  * Scratch: a static device array inside the library sized for at most
  * DSP_NOALLOC_MAX_POINTS points (about 512 KB, held on every GPU that loads
  * the library until the process exits); larger maps are refused with
  * DSP_E_INVALID before anything is queued.  The first call made with a given
- * device current looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call overwrites the
- * whole scratch it reads, so no state leaks between calls, but all calls
+ * device current looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it for the rest of the process; make that first call before any
+ * stream capture.  A cudaDeviceReset of that device after the first call is
+ * not supported (the cached address would be stale).  Every call overwrites
+ * the whole scratch it reads, so no state leaks between calls, but all calls
  * share the one array: calls that overlap on the GPU (other streams, other
  * host threads) race and must be serialised by the caller.  Work is queued on
- * cuda_stream (NULL: legacy stream), which the call synchronises. */
+ * cuda_stream (NULL: legacy stream), which the call synchronises.  Errors left
+ * by earlier launches of the caller's are cleared first, so DSP_E_CUDA
+ * reports this call's own. */
 #define DSP_NOALLOC_MAX_POINTS 67108864
 dsp_status dsp_density_noalloc(const void *map_dev, int32_t precision, int32_t nx, int32_t ny,
                                double px_min, double px_max, double py_min, double py_max,
@@ -185,9 +223,15 @@ dsp_status dsp_solve_host(dsp_grid *g, const double *a_mid, int64_t n_steps, dou
                           const double a_in[2], const double a_out[2], void *map_host,
                           double *n_host);
 
-/* One launch that advances several grids (each by steps[i], same rules as
- * dsp_evolve).  All grids must share one CUDA stream; work goes on that
- * stream.  Results are bitwise identical to advancing each grid alone. */
+/* Advances several grids, each by steps[i] (same rules as dsp_evolve), in one
+ * batched launch per precision present (a launch carries at most 96 grids;
+ * more are split over further launches).  The momenta of all the grids are
+ * independent (Sec. III: every p carries its own spinor), so the batch only
+ * shares launches.  All grids must share one CUDA stream; work goes on that
+ * stream.  Results are bitwise identical to advancing each grid alone.  Each
+ * grid keeps its own device error word: a bounded wait that runs out (or a
+ * bounds-check hit) in one grid's tiles is reported, and latched, by that
+ * grid's next synchronising call, not by the others'. */
 dsp_status dsp_evolve_batch(dsp_grid *const *grids, const int64_t *steps, int32_t count);
 
 /* Cursor and pulse length of a grid. */
@@ -209,6 +253,8 @@ typedef struct {
     int64_t n_steps, cursor;
     double dt, theta_max;
     int32_t group_steps;
+    int32_t row_begin; /* first global row (0 unless the grid is a band)      */
+    int32_t ny_total;  /* rows of the full grid (ny unless the grid is a band) */
     int32_t reserved;
 } dsp_grid_info;
 dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info);
@@ -227,7 +273,8 @@ dsp_status dsp_test_withhold_next_copy(dsp_grid *g);
 dsp_status dsp_save_state(dsp_grid *g, void *host_buf, int64_t bytes, int64_t *cursor);
 dsp_status dsp_load_state(dsp_grid *g, const void *host_buf, int64_t bytes, int64_t cursor);
 
-/* Frees the grid (and the state if the library allocated it).  NULL is OK. */
+/* Frees the grid (and the state if the library allocated it).  NULL is OK.
+ * Resource management only: the paper has no counterpart. */
 dsp_status dsp_destroy_grid(dsp_grid *g);
 
 /* Static string for a status code. */

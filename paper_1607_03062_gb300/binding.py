@@ -40,7 +40,7 @@ EXPORTS = (
     "dsp_sample_pulse", "dsp_server_create", "dsp_server_submit", "dsp_server_step",
     "dsp_server_query", "dsp_server_cancel", "dsp_server_destroy", "dsp_density_noalloc",
     "dsp_get_info", "dsp_solve_segmented", "dsp_sample_pulse_gauss",
-    "dsp_test_withhold_next_copy",
+    "dsp_test_withhold_next_copy", "dsp_create_band", "dsp_set_keep_final_state",
 )
 
 
@@ -61,7 +61,8 @@ class GridInfo(ctypes.Structure):
                                               "cos_degree", "sinc_degree", "n_tiles")] + [
         ("n_steps", ctypes.c_int64), ("cursor", ctypes.c_int64), ("dt", ctypes.c_double),
         ("theta_max", ctypes.c_double),
-        ("group_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+        ("group_steps", ctypes.c_int32), ("row_begin", ctypes.c_int32),
+        ("ny_total", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -97,6 +98,9 @@ def lib() -> ctypes.CDLL:
                 "dsp_state_bytes": (i64, [i32, i32, i32]),
                 "dsp_create_grid": (i32, [i32, i32, d, d, d, d, i32, i32, i32, p, p, i64,
                                           ctypes.POINTER(p)]),
+                "dsp_create_band": (i32, [i32, i32, i32, i32, d, d, d, d, i32, i32, i32, p, p,
+                                          i64, ctypes.POINTER(p)]),
+                "dsp_set_keep_final_state": (i32, [p, i32]),
                 "dsp_set_pulse": (i32, [p, p, i64, d, p, p]),
                 "dsp_evolve": (i32, [p, i64]),
                 "dsp_project": (i32, [p, p]),
@@ -165,6 +169,26 @@ def create_grid(nx, ny, px_range, py_range, precision="fp32_mixed", scheme="exac
                                int(state_bytes_), ctypes.byref(h))
     _check(rc, "create_grid")
     return h.value
+
+
+def create_band(nx, ny, rows, px_range, py_range, precision="fp32_mixed", scheme="exact",
+                valley=1, stream=0, state_ptr=0, state_bytes_=0) -> int:
+    """A grid holding the rows [rows[0], rows[1]) of the nx by ny grid on the box:
+    the full grid's nodes and step choices (see include/dsp.h)."""
+    h = ctypes.c_void_p()
+    rc = lib().dsp_create_band(int(nx), int(ny), int(rows[0]), int(rows[1]),
+                               float(px_range[0]), float(px_range[1]),
+                               float(py_range[0]), float(py_range[1]),
+                               _enum(precision, PRECISIONS), _enum(scheme, SCHEMES), int(valley),
+                               ctypes.c_void_p(int(stream)), ctypes.c_void_p(int(state_ptr)),
+                               int(state_bytes_), ctypes.byref(h))
+    _check(rc, "create_band")
+    return h.value
+
+
+def set_keep_final_state(h: int, keep: bool):
+    _check(lib().dsp_set_keep_final_state(ctypes.c_void_p(h), 1 if keep else 0),
+           "set_keep_final_state")
 
 
 def _steps(a_mid):
@@ -385,22 +409,30 @@ def server_destroy(s: int):
 
 class Grid:
     """One momentum grid; the spinor state and the |c+|^2 map are torch tensors on
-    the current CUDA device, work goes on torch's current stream."""
+    the current CUDA device, work goes on torch's current stream.  With
+    ``rows=(r0, r1)`` the grid is the band of rows [r0, r1) of the nx by ny grid
+    (``dsp_create_band``); its map then holds those rows only."""
 
     def __init__(self, nx, ny, px_range, py_range, precision="fp32_mixed", scheme="exact",
-                 valley=1, device=None):
+                 valley=1, device=None, rows=None):
         import torch
         self.torch = torch
-        self.nx, self.ny = int(nx), int(ny)
+        self.nx = int(nx)
+        self.rows = (0, int(ny)) if rows is None else (int(rows[0]), int(rows[1]))
+        self.ny = self.rows[1] - self.rows[0]
         self.precision = _enum(precision, PRECISIONS)
         dev = torch.device("cuda" if device is None else device)
-        nbytes = state_bytes(nx, ny, self.precision)
+        nbytes = state_bytes(nx, self.ny, self.precision)
         self.state = torch.empty(nbytes // 4, dtype=torch.float32, device=dev)
         mdt = torch.float64 if self.precision == FP64 else torch.float32
         self.map = torch.empty((self.ny, self.nx), dtype=mdt, device=dev)
         self.stream = torch.cuda.current_stream(dev).cuda_stream
-        self.h = create_grid(nx, ny, px_range, py_range, self.precision, scheme, valley,
-                             self.stream, self.state.data_ptr(), nbytes)
+        if rows is None:
+            self.h = create_grid(nx, ny, px_range, py_range, self.precision, scheme, valley,
+                                 self.stream, self.state.data_ptr(), nbytes)
+        else:
+            self.h = create_band(nx, ny, self.rows, px_range, py_range, self.precision, scheme,
+                                 valley, self.stream, self.state.data_ptr(), nbytes)
 
     def set_pulse(self, a_mid, dt, a_in, a_out):
         set_pulse(self.h, a_mid, dt, a_in, a_out)

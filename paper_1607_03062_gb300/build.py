@@ -1,7 +1,10 @@
 """Builds the in-tree CUDA library ``_build/libdsp.so`` for sm_103a.
 
-Two translation units (kernels, host API) are compiled in parallel with nvcc,
-then linked into one shared library with the CUDA runtime linked statically.
+Three translation units (kernels, host API, the allocation-free density) are
+compiled in parallel with nvcc, then linked into one shared library with the
+CUDA runtime linked statically.  Host code is compiled without floating-point
+contraction, so the host-side arithmetic (pulse tables, projection nodes) rounds
+the same way on every host architecture.
 """
 from __future__ import annotations
 
@@ -59,6 +62,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
     for src in sources():
         obj = os.path.join(os.path.dirname(lib), os.path.basename(src) + ".o")
         cmd = [nvcc, "-c", src, "-o", obj] + COMMON + (["-DDSP_BOUNDS_CHECK"] if bounds_check else [])
+        cmd += ["-Xcompiler", "-ffp-contract=off"]
         if src.endswith(".cu"):
             cmd += ARCH + ["-lineinfo"]
             if ptxas_info:

@@ -47,6 +47,7 @@ struct DeviceScalars {
 
 struct dsp_grid {
     int32_t nx = 0, ny = 0, precision = 0, scheme = 0, valley = 1;
+    int32_t row0 = 0, ny_total = 0;  // rows [row0, row0 + ny) of an ny_total-row grid
     double px_min = 0, px_max = 0, py_min = 0, py_max = 0, hx = 0, hy = 0;
     int64_t n_points = 0;
     int32_t n_tiles = 0;
@@ -58,6 +59,7 @@ struct dsp_grid {
     int64_t table_cap = 0;  // entries
     double *partials = nullptr;
     DeviceScalars *scal = nullptr;
+    float2 *nodes = nullptr;  // projection nodes s (p + A_out), FP32 hi/lo: nx columns, ny rows
     void *own_map = nullptr;  // used by dsp_solve when the caller passes no map
     void *seg_buf = nullptr;  // time-segment columns for dsp_solve_segmented
     size_t seg_cap = 0;
@@ -71,6 +73,8 @@ struct dsp_grid {
     bool withhold_next = false;  // test hook, see dsp_test_withhold_next_copy
     bool fresh = true;      // state not yet written on the device
     bool projected = false;  // partial sums valid for the current pulse
+    bool keep_final_state = true;  // dsp_set_keep_final_state
+    bool state_stale = false;  // the last launch did not write the final state back
     dsp_status latched = DSP_OK;
 };
 
@@ -164,6 +168,8 @@ ReqDesc make_desc(const dsp_grid *g, int64_t begin, int64_t end, bool project, v
     r.state = g->state;
     r.map = map;
     r.partials = g->partials;
+    r.err = g->scal ? &g->scal->err : nullptr;
+    r.nodes_out = g->nodes;
     r.px_min = g->px_min;
     r.py_min = g->py_min;
     r.hx = g->hx;
@@ -178,6 +184,13 @@ ReqDesc make_desc(const dsp_grid *g, int64_t begin, int64_t end, bool project, v
     r.step_end = end;
     r.nx = g->nx;
     r.ny = g->ny;
+    r.row0 = g->row0;
+    // A state that is only read (a projection of the state on the device) is not
+    // written back; with keep_final_state off, neither is the state after the
+    // last step when it is projected in the same launch.
+    const bool read_only = begin == end && !g->fresh;
+    const bool final_dropped = project && end == g->n_steps && !g->keep_final_state;
+    r.store_state = (read_only || final_dropped) ? 0 : 1;
     r.scheme = g->scheme;
     r.valley = g->valley;
     r.level = g->level;
@@ -195,16 +208,25 @@ double density_scale(const dsp_grid *g)
     return 4.0 / ((2.0 * kPi) * (2.0 * kPi)) * g->hx * g->hy;
 }
 
-// Queues launches advancing several requests of one precision; requests are
-// split into launches of at most kMaxReqPerLaunch.
-cudaError_t launch_requests(const std::vector<ReqDesc> &reqs, int precision, int *err,
-                            cudaStream_t stream)
+// A launch that only projects a state already on the device.
+bool project_only(const ReqDesc &r)
 {
+    return r.step_begin == r.step_end && r.project && !r.fresh && r.nodes_out;
+}
+
+// Queues launches advancing several requests of one precision; requests are
+// split into launches of at most kMaxReqPerLaunch.  Each request reports device
+// errors in its own error word (ReqDesc::err).  A batch in which every request
+// only projects goes to the projection kernel.
+cudaError_t launch_requests(const std::vector<ReqDesc> &reqs, int precision, cudaStream_t stream)
+{
+    bool proj = !reqs.empty();
+    for (const ReqDesc &r : reqs)
+        proj = proj && project_only(r);
     size_t i = 0;
     while (i < reqs.size()) {
         std::unique_ptr<EvolveArgs> a(new EvolveArgs());
         std::memset(a.get(), 0, sizeof(EvolveArgs));
-        a->err = err;
         int tiles = 0;
         int n = 0;
         while (i < reqs.size() && n < dsp::kMaxReqPerLaunch) {
@@ -216,7 +238,8 @@ cudaError_t launch_requests(const std::vector<ReqDesc> &reqs, int precision, int
         }
         a->nreq = n;
         a->total_tiles = tiles;
-        cudaError_t e = dsp::launch_evolve(*a, precision, stream);
+        cudaError_t e = proj ? dsp::launch_project(*a, precision, stream)
+                             : dsp::launch_evolve(*a, precision, stream);
         if (e != cudaSuccess)
             return e;
     }
@@ -388,6 +411,33 @@ void build_table(const dsp_grid *g, const double *a_mid, int64_t n, double dt,
     }
 }
 
+// Projection nodes of the grid's columns and rows, s (p + A_out) with s the
+// valley, formed in FP64 as the kernels form the grid nodes (p = lo + (i + 1/2) h),
+// each split into an FP32 hi + lo pair for the double-float projection: nx
+// columns, then the grid's ny rows (global rows row0 ...).
+void build_nodes(const dsp_grid *g, std::vector<float2> &out)
+{
+    out.resize(static_cast<size_t>(g->nx) + static_cast<size_t>(g->ny));
+    const double vs = g->valley > 0 ? 1.0 : -1.0;
+    const auto put = [&](size_t k, double v) {
+        const float h = static_cast<float>(v);
+        out[k] = make_float2(h, static_cast<float>(v - static_cast<double>(h)));
+    };
+    for (int32_t i = 0; i < g->nx; ++i) {
+        const double p = g->px_min + (static_cast<double>(i) + 0.5) * g->hx;
+        put(static_cast<size_t>(i), vs * (p + g->a_out[0]));
+    }
+    for (int32_t j = 0; j < g->ny; ++j) {
+        const double p = g->py_min + (static_cast<double>(g->row0 + j) + 0.5) * g->hy;
+        put(static_cast<size_t>(g->nx) + static_cast<size_t>(j), vs * (p + g->a_out[1]));
+    }
+}
+
+size_t node_bytes(const dsp_grid *g)
+{
+    return sizeof(float2) * (static_cast<size_t>(g->nx) + static_cast<size_t>(g->ny));
+}
+
 void free_grid_memory(dsp_grid *g)
 {
     if (g->owns_state && g->state)
@@ -400,6 +450,8 @@ void free_grid_memory(dsp_grid *g)
         cudaFree(g->scal);
     if (g->own_map)
         cudaFree(g->own_map);
+    if (g->nodes)
+        cudaFree(g->nodes);
     if (g->seg_buf)
         cudaFree(g->seg_buf);
     g->seg_buf = nullptr;
@@ -407,15 +459,21 @@ void free_grid_memory(dsp_grid *g)
     g->state = g->table = g->own_map = nullptr;
     g->partials = nullptr;
     g->scal = nullptr;
+    g->nodes = nullptr;
 }
 
-// Geometry and arithmetic fields of a grid (no allocation).
+// Geometry and arithmetic fields of a grid (no allocation): rows [row0, row0 +
+// rows) of the nx by ny grid on the box.
 void fill_grid(dsp_grid *g, int32_t nx, int32_t ny, double px_min, double px_max, double py_min,
                double py_max, int32_t precision, int32_t scheme, int32_t valley,
-               cudaStream_t stream)
+               cudaStream_t stream, int32_t row0 = 0, int32_t rows = -1)
 {
+    if (rows < 0)
+        rows = ny;
     g->nx = nx;
-    g->ny = ny;
+    g->ny = rows;
+    g->row0 = row0;
+    g->ny_total = ny;
     g->precision = precision;
     g->scheme = scheme;
     g->valley = valley;
@@ -425,7 +483,7 @@ void fill_grid(dsp_grid *g, int32_t nx, int32_t ny, double px_min, double px_max
     g->py_max = py_max;
     g->hx = (px_max - px_min) / nx;
     g->hy = (py_max - py_min) / ny;
-    g->n_points = static_cast<int64_t>(nx) * ny;
+    g->n_points = static_cast<int64_t>(nx) * rows;
     g->n_tiles = static_cast<int32_t>((g->n_points + dsp::kTilePoints - 1) / dsp::kTilePoints);
     g->stream = stream;
 }
@@ -433,22 +491,28 @@ void fill_grid(dsp_grid *g, int32_t nx, int32_t ny, double px_min, double px_max
 dsp_status create_grid_impl(int32_t nx, int32_t ny, double px_min, double px_max, double py_min,
                             double py_max, int32_t precision, int32_t scheme, int32_t valley,
                             cudaStream_t stream, void *state_dev, int64_t state_bytes,
-                            dsp_grid **out)
+                            dsp_grid **out, int32_t row_begin = 0, int32_t row_end = -1)
 {
     if (!out)
         return DSP_E_INVALID;
     *out = nullptr;
-    dsp_status s =
-        validate_grid_args(nx, ny, px_min, px_max, py_min, py_max, precision, scheme, valley);
+    if (row_end < 0)
+        row_end = ny;
+    if (ny < 1 || row_begin < 0 || row_begin >= row_end || row_end > ny)
+        return DSP_E_INVALID;
+    // the grid holds nx x (row_end - row_begin) points; ny only sets the spacing
+    dsp_status s = validate_grid_args(nx, row_end - row_begin, px_min, px_max, py_min, py_max,
+                                      precision, scheme, valley);
     if (s != DSP_OK)
         return s;
-    const int64_t need = dsp_state_bytes(nx, ny, precision);
+    const int64_t need = dsp_state_bytes(nx, row_end - row_begin, precision);
     if (state_dev && (state_bytes < need || (reinterpret_cast<uintptr_t>(state_dev) & 15u)))
         return DSP_E_INVALID;
     dsp_grid *g = new (std::nothrow) dsp_grid();
     if (!g)
         return DSP_E_NOMEM;
-    fill_grid(g, nx, ny, px_min, px_max, py_min, py_max, precision, scheme, valley, stream);
+    fill_grid(g, nx, ny, px_min, px_max, py_min, py_max, precision, scheme, valley, stream,
+              row_begin, row_end - row_begin);
     cudaError_t e = cudaSuccess;
     if (state_dev) {
         g->state = state_dev;
@@ -461,6 +525,8 @@ dsp_status create_grid_impl(int32_t nx, int32_t ny, double px_min, double px_max
     if (e == cudaSuccess)
         e = cudaMalloc(reinterpret_cast<void **>(&g->scal), sizeof(DeviceScalars));
     if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void **>(&g->nodes), node_bytes(g));
+    if (e == cudaSuccess)
         e = cudaMemsetAsync(g->scal, 0, sizeof(DeviceScalars), stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -472,11 +538,12 @@ dsp_status create_grid_impl(int32_t nx, int32_t ny, double px_min, double px_max
     return DSP_OK;
 }
 
-// Host part of setting a pulse: validates, fills the grid's pulse fields and
-// lays out the device table in `host` (n_steps * 16 bytes).  Nothing is queued.
+// Host part of setting a pulse: validates, fills the grid's pulse fields, lays
+// out the device table in `host` and the projection nodes in `nodes`.  Nothing
+// is queued.
 dsp_status prepare_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, double dt,
                          const double a_in[2], const double a_out[2],
-                         std::vector<unsigned char> &host)
+                         std::vector<unsigned char> &host, std::vector<float2> &nodes)
 {
     // every (A_x, A_y) sample of the table, whatever the samples per step
     const int64_t n_samples = n_steps * samples_per_step(g->scheme);
@@ -498,6 +565,8 @@ dsp_status prepare_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, doub
     g->group = choose_group(g->precision, g->scheme, g->level, tmax);
     g->fresh = true;
     g->projected = false;
+    g->state_stale = false;
+    build_nodes(g, nodes);
     return DSP_OK;
 }
 
@@ -506,7 +575,8 @@ dsp_status set_pulse_impl(dsp_grid *g, const double *a_mid, int64_t n_steps, dou
 {
     dsp_grid staged = *g;
     std::vector<unsigned char> host;
-    dsp_status s = prepare_pulse(&staged, a_mid, n_steps, dt, a_in, a_out, host);
+    std::vector<float2> nodes;
+    dsp_status s = prepare_pulse(&staged, a_mid, n_steps, dt, a_in, a_out, host, nodes);
     if (s != DSP_OK)
         return s;
     cudaError_t e = cudaSuccess;
@@ -531,6 +601,9 @@ dsp_status set_pulse_impl(dsp_grid *g, const double *a_mid, int64_t n_steps, dou
         if (e != cudaSuccess)
             return latch_cuda(g, e);
     }
+    e = cudaMemcpyAsync(g->nodes, nodes.data(), node_bytes(g), cudaMemcpyHostToDevice, g->stream);
+    if (e != cudaSuccess)
+        return latch_cuda(g, e);
     staged.table = g->table;
     staged.table_cap = g->table_cap;
     *g = staged;
@@ -540,11 +613,15 @@ dsp_status set_pulse_impl(dsp_grid *g, const double *a_mid, int64_t n_steps, dou
 // Advances one grid to `end`, optionally projecting into `map` at the end.
 dsp_status run_one(dsp_grid *g, int64_t end, bool project, void *map)
 {
+    if (g->state_stale && !g->fresh)
+        return DSP_E_STATE;  // the final state was not kept (dsp_set_keep_final_state)
     std::vector<ReqDesc> r(1, make_desc(g, g->cursor, end, project, map));
     g->withhold_next = false;
-    cudaError_t e = launch_requests(r, g->precision, &g->scal->err, g->stream);
+    cudaError_t e = launch_requests(r, g->precision, g->stream);
     if (e != cudaSuccess)
         return latch_cuda(g, e);
+    if (!r[0].store_state && !(r[0].step_begin == r[0].step_end && !r[0].fresh))
+        g->state_stale = true;
     g->cursor = end;
     g->fresh = false;
     if (project)
@@ -591,6 +668,31 @@ dsp_status dsp_create_grid(int32_t nx, int32_t ny, double px_min, double px_max,
     return create_grid_impl(nx, ny, px_min, px_max, py_min, py_max, precision, scheme, valley,
                             static_cast<cudaStream_t>(cuda_stream), state_dev, state_dev_bytes,
                             out);
+}
+
+dsp_status dsp_create_band(int32_t nx, int32_t ny, int32_t row_begin, int32_t row_end,
+                           double px_min, double px_max, double py_min, double py_max,
+                           int32_t precision, int32_t scheme, int32_t valley, void *cuda_stream,
+                           void *state_dev, int64_t state_dev_bytes, dsp_grid **out)
+{
+    if (out)
+        *out = nullptr;
+    if (row_end < 0)
+        return DSP_E_INVALID;
+    return create_grid_impl(nx, ny, px_min, px_max, py_min, py_max, precision, scheme, valley,
+                            static_cast<cudaStream_t>(cuda_stream), state_dev, state_dev_bytes,
+                            out, row_begin, row_end);
+}
+
+dsp_status dsp_set_keep_final_state(dsp_grid *g, int32_t keep)
+{
+    dsp_status s = check_usable(g);
+    if (s != DSP_OK)
+        return s;
+    if (keep != 0 && keep != 1)
+        return DSP_E_INVALID;
+    g->keep_final_state = keep != 0;
+    return DSP_OK;
 }
 
 dsp_status dsp_set_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, double dt,
@@ -746,7 +848,7 @@ dsp_status dsp_solve_segmented(dsp_grid *g, int32_t segments, void *map_dev, dou
         d.init_identity = 1;
         descs.push_back(d);
     }
-    e = launch_requests(descs, g->precision, &g->scal->err, g->stream);
+    e = launch_requests(descs, g->precision, g->stream);
     // 2. psi = M_{S-1} ... M_0 v(p + A_in)
     if (e == cudaSuccess) {
         dsp::CombineArgs c;
@@ -763,6 +865,7 @@ dsp_status dsp_solve_segmented(dsp_grid *g, int32_t segments, void *map_dev, dou
         c.a_in[0] = g->a_in[0];
         c.a_in[1] = g->a_in[1];
         c.valley = g->valley;
+        c.row0 = g->row0;
         e = dsp::launch_combine(c, g->precision, g->stream);
     }
     if (e != cudaSuccess)
@@ -840,7 +943,9 @@ dsp_status dsp_evolve_batch(dsp_grid *const *grids, const int64_t *steps, int32_
         }
         if (reqs.empty())
             continue;
-        cudaError_t e = launch_requests(reqs, prec, &grids[0]->scal->err, grids[0]->stream);
+        // every descriptor carries its own grid's error word: a timeout or a bounds
+        // hit in one grid's tiles is latched on that grid
+        cudaError_t e = launch_requests(reqs, prec, grids[0]->stream);
         if (e != cudaSuccess) {
             for (int32_t i = 0; i < count; ++i)
                 latch_cuda(grids[i], e);
@@ -850,6 +955,7 @@ dsp_status dsp_evolve_batch(dsp_grid *const *grids, const int64_t *steps, int32_
     for (int32_t i = 0; i < count; ++i) {
         if (steps[i] == 0)
             continue;
+        grids[i]->withhold_next = false;
         grids[i]->cursor += steps[i];
         grids[i]->fresh = false;
         grids[i]->projected = false;
@@ -895,6 +1001,8 @@ dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info)
     info->group_steps = g->group;
     info->dt = g->dt;
     info->theta_max = g->theta_max;
+    info->row_begin = g->row0;
+    info->ny_total = g->ny_total;
     return DSP_OK;
 }
 
@@ -906,7 +1014,7 @@ dsp_status dsp_save_state(dsp_grid *g, void *host_buf, int64_t bytes, int64_t *c
     const int64_t need = dsp_state_bytes(g->nx, g->ny, g->precision);
     if (!host_buf || !cursor || bytes < need)
         return DSP_E_INVALID;
-    if (!g->has_pulse)
+    if (!g->has_pulse || (g->state_stale && !g->fresh))
         return DSP_E_STATE;
     if (g->fresh) {  // materialise v(p + A_in) on the device first
         s = run_one(g, g->cursor, false, nullptr);
@@ -942,6 +1050,7 @@ dsp_status dsp_load_state(dsp_grid *g, const void *host_buf, int64_t bytes, int6
     g->cursor = cursor;
     g->fresh = false;
     g->projected = false;
+    g->state_stale = false;
     return DSP_OK;
 }
 
@@ -1167,8 +1276,9 @@ int64_t footprint_of(const dsp_request &p)
 {
     const int64_t pts = static_cast<int64_t>(p.nx) * p.ny;
     const int64_t tiles = (pts + dsp::kTilePoints - 1) / dsp::kTilePoints;
+    const size_t nodes = sizeof(float2) * (static_cast<size_t>(p.nx) + static_cast<size_t>(p.ny));
     return static_cast<int64_t>(align256(32 * static_cast<size_t>(pts)) +
-                                align256(table_bytes(p.precision, p.scheme, p.n_steps)) +
+                                align256(table_bytes(p.precision, p.scheme, p.n_steps) + nodes) +
                                 align256(8 * static_cast<size_t>(tiles)) +
                                 align256(sizeof(DeviceScalars)) +
                                 align256(map_elem_bytes(p.precision) * static_cast<size_t>(pts)));
@@ -1224,12 +1334,19 @@ dsp_status server_admit(dsp_server *s, ServerReq *r)
     fill_grid(&r->g, p.nx, p.ny, p.px_min, p.px_max, p.py_min, p.py_max, p.precision, p.scheme,
               p.valley, s->stream);
     std::vector<unsigned char> host;
-    dsp_status st = prepare_pulse(&r->g, r->a_mid.data(), p.n_steps, p.dt, p.a_in, p.a_out, host);
+    std::vector<float2> nodes;
+    dsp_status st =
+        prepare_pulse(&r->g, r->a_mid.data(), p.n_steps, p.dt, p.a_in, p.a_out, host, nodes);
     if (st != DSP_OK)
         return st;
+    r->g.keep_final_state = false;  // a finished request's state is never read again
+    // table (padded to 16 bytes) and projection nodes, uploaded in one copy
+    const size_t tb = table_bytes(p.precision, p.scheme, p.n_steps);
+    host.resize(tb + node_bytes(&r->g), 0);
+    std::memcpy(host.data() + tb, nodes.data(), node_bytes(&r->g));
     const size_t pts = static_cast<size_t>(r->g.n_points);
     const size_t o_table = align256(32 * pts);
-    const size_t o_part = o_table + align256(table_bytes(p.precision, p.scheme, p.n_steps));
+    const size_t o_part = o_table + align256(host.size());
     const size_t o_scal = o_part + align256(8 * static_cast<size_t>(r->g.n_tiles));
     const size_t o_map = o_scal + align256(sizeof(DeviceScalars));
     const size_t total = o_map + align256(map_elem_bytes(p.precision) * pts);
@@ -1246,6 +1363,7 @@ dsp_status server_admit(dsp_server *s, ServerReq *r)
     r->g.state = b;
     r->g.table = b + o_table;
     r->g.table_cap = p.n_steps;
+    r->g.nodes = reinterpret_cast<float2 *>(b + o_table + tb);
     r->g.partials = reinterpret_cast<double *>(b + o_part);
     r->g.scal = reinterpret_cast<DeviceScalars *>(b + o_scal);
     r->map_dev = b + o_map;
@@ -1442,6 +1560,7 @@ dsp_status dsp_server_step(dsp_server *s, int32_t *n_active, int32_t *n_queued,
             const int64_t end = std::min(g.n_steps, g.cursor + s->chunk);
             const bool fin = (end == g.n_steps);
             descs.push_back(make_desc(&g, g.cursor, end, fin, r->map_dev));
+            descs.back().err = s->err;  // one error word for the server's launches
             g.cursor = end;
             g.fresh = false;
             if (fin) {
@@ -1453,7 +1572,7 @@ dsp_status dsp_server_step(dsp_server *s, int32_t *n_active, int32_t *n_queued,
         if (descs.empty())
             continue;
         queued_any = true;
-        if (launch_requests(descs, prec, s->err, s->stream) != cudaSuccess)
+        if (launch_requests(descs, prec, s->stream) != cudaSuccess)
             return server_fail(s, DSP_E_CUDA);
     }
     if (launch_finalizes(fins, s->stream) != cudaSuccess)

@@ -14,7 +14,7 @@ constexpr int kTilePoints = 1024;
 // Spinors per thread (independent momenta advanced together for ILP).
 constexpr int kSpinorsPerThread = 2;
 constexpr int kThreads = kTilePoints / kSpinorsPerThread;
-// Requests one evolve launch can carry in its parameter block (96 x 192 bytes:
+// Requests one evolve launch can carry in its parameter block (96 x 208 bytes:
 // within the 32 KB kernel-parameter limit).
 constexpr int kMaxReqPerLaunch = 96;
 // Device-side error bits (the launch's error word).
@@ -47,12 +47,17 @@ struct ReqDesc {
     void *state;        // planes: FP32_MIXED float4 hi[n], float4 lo[n]; FP64 double2 a[n], double2 b[n]
     void *map;          // |c+|^2 output (float or double), or nullptr
     double *partials;   // one double per tile (written when projecting)
+    int *err;           // the request's device error word (bits kErr*)
+    const float2 *nodes_out;  // projection nodes p + A_out as FP32 hi/lo pairs: nx
+                              // columns, then the grid's ny rows (see node_tables)
     double px_min, py_min, hx, hy;
     double dt;
     double a_in[2], a_out[2];
     int64_t n_points;
     int64_t step_begin, step_end;  // table entries [step_begin, step_end) this launch
     int32_t nx, ny;
+    int32_t row0;     // global row index of the grid's first row (row bands; 0 otherwise)
+    int32_t store_state;  // 1: write the spinor state back at the end of the launch
     int32_t scheme, valley, level;
     int32_t fresh;    // 1: start from v(p + A_in) instead of reading the state
     int32_t project;  // 1: project at the end (map + partials)
@@ -82,7 +87,6 @@ static_assert(sizeof(ReqDesc) * kMaxReqPerLaunch + 64 < 32764, "kernel parameter
 struct EvolveArgs {
     int32_t nreq;
     int32_t total_tiles;
-    int *err;  // device error word (bits kErr*)
     ReqDesc r[kMaxReqPerLaunch];
 };
 
@@ -114,11 +118,14 @@ struct CombineArgs {
     double px_min, py_min, hx, hy;
     double a_in[2];
     int32_t valley;
-    int32_t pad;
+    int32_t row0;  // global row index of the grid's first row
 };
 
 // precision: 0 = FP64, 1 = FP32_MIXED.  Every request in args must have that precision.
 cudaError_t launch_evolve(const EvolveArgs &args, int precision, cudaStream_t stream);
+// Projection only, of states already on the device: every request in args has
+// step_begin == step_end, project == 1, fresh == 0 and a node table.
+cudaError_t launch_project(const EvolveArgs &args, int precision, cudaStream_t stream);
 cudaError_t launch_finalize(const FinalizeArgs &args, cudaStream_t stream);
 cudaError_t launch_combine(const CombineArgs &args, int precision, cudaStream_t stream);
 

@@ -38,6 +38,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "dsp_internal.h"
 
 namespace dsp {
@@ -192,6 +194,8 @@ __device__ __forceinline__ void initial_spinor(double Px, double Py, double sgn,
 }
 
 // |u(P_out)^dag psi|^2 with u = [1, valley (Px + i Py)/E]/sqrt(2); 0 at P_out = 0.
+// FP64; used only for the rare points whose |P_out| is too small for the
+// double-float form below.
 __device__ __forceinline__ double project_point(double Px, double Py, double sgn, double ar,
                                                 double ai, double br, double bi)
 {
@@ -202,6 +206,146 @@ __device__ __forceinline__ double project_point(double Px, double Py, double sgn
     const double cr = ar + (wr * br - wi * bi);
     const double ci = ai + (wr * bi + wi * br);
     return 0.5 * (cr * cr + ci * ci);
+}
+
+// ---------------------------------------------------------------------------
+// The projection |c+|^2 = |u(P_out)^dag psi|^2 in double-float FP32 arithmetic.
+//
+// GB300 issues FP64 at about 1/64 of its FP32 rate, and an FP64 projection (a
+// square root and two divisions per point) would make a projection-only launch
+// FP64-bound at a small fraction of HBM speed.  Here every quantity is an
+// unevaluated pair hi + lo of floats (about 48 significant bits): products are
+// split exactly with FMA, the large terms of c+ are summed with TwoSum, so
+// |c+|^2 comes out to ~1e-14 absolute; only its conversion to double and the
+// tile tree use FP64.  The node P_out = p + A_out (valley-signed) comes from a
+// per-grid table of hi/lo pairs built on the host in FP64.  Written from the
+// definitions (TwoSum, the FMA product split, one Newton step for 1/sqrt);
+// all operations are non-contracting intrinsics, so every kernel that calls it
+// gets the same bits.
+// ---------------------------------------------------------------------------
+
+// s + e = a + b exactly (TwoSum, no condition on the magnitudes).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fadd_rn(s, -a);
+    e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+}
+
+// The double x as hi + lo floats: hi = x rounded toward zero (same exponent as
+// x), lo = the 29 fraction bits hi drops, rounded to a float (x - hi - lo is
+// below 2^-48 |x|).  Integer operations only, no FP64 arithmetic.  Values
+// below 2^-74 in magnitude keep lo = 0 (their lo is below 2^-97).
+__device__ __forceinline__ void split_f64(double x, float &hi, float &lo)
+{
+    hi = __double2float_rz(x);
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned int e = static_cast<unsigned int>(bits >> 52) & 0x7FFu;
+    const unsigned int m = static_cast<unsigned int>(bits) & 0x1FFFFFFFu;
+    lo = 0.0f;
+    if (e >= 949u && e <= 1202u) {  // 2^(e - 1075) is a normal float
+        lo = __fmul_rn(__uint2float_rn(m), __int_as_float(static_cast<int>((e - 948u) << 23)));
+        if (bits >> 63)
+            lo = -lo;
+    }
+}
+
+// Points with E^2 = |P_out|^2 below this (|P_out| < 2^-45 eV) take the FP64
+// form: their squares would lose bits near the bottom of the float range.
+constexpr float kProjTinyE2 = 0x1p-90f;
+
+// |c+|^2 = oh + ol for the node s P_out = (xh + xl, yh + yl) (s = valley) and
+// the spinor a = (ar, ai), b = (br, bi), each component hi + lo:
+//   c+ = (a + conj(w) b)/sqrt(2),  w = s (P_x + i P_y)/|P|,
+//   cr = ar + wr br + wi bi,  ci = ai + wr bi - wi br.
+// Returns false (and leaves oh, ol unset) when E^2 < kProjTinyE2.
+__device__ __forceinline__ bool project_df(float xh, float xl, float yh, float yl, float arh,
+                                           float arl, float aih, float ail, float brh, float brl,
+                                           float bih, float bil, float &oh, float &ol)
+{
+    // E^2 = Px^2 + Py^2 to ~2^-46
+    const float x2 = __fmul_rn(xh, xh);
+    const float x2e = __fmaf_rn(__fadd_rn(xh, xh), xl, __fmaf_rn(xh, xh, -x2));
+    const float y2 = __fmul_rn(yh, yh);
+    const float y2e = __fmaf_rn(__fadd_rn(yh, yh), yl, __fmaf_rn(yh, yh, -y2));
+    float sh, se;
+    two_sum(x2, y2, sh, se);
+    se = __fadd_rn(se, __fadd_rn(x2e, y2e));
+    if (!(sh >= kProjTinyE2))
+        return false;
+    // r = 1/E = r0 + rc: one Newton step r0 (1 - t/2) from the FP32 estimate r0,
+    // with t = E^2 r0^2 - 1 evaluated to ~2^-46 (p - 1 is exact: p is near 1)
+    const float r0 = rsqrtf(sh);
+    const float q = __fmul_rn(r0, r0), qe = __fmaf_rn(r0, r0, -q);
+    const float p = __fmul_rn(sh, q), pe = __fmaf_rn(sh, q, -p);
+    const float t = __fadd_rn(__fadd_rn(p, -1.0f), __fmaf_rn(sh, qe, __fmaf_rn(se, q, pe)));
+    const float rc = __fmul_rn(__fmul_rn(-0.5f, r0), t);
+    // w = (wr + wre) + i (wi + wie) = s P / E
+    const float wr = __fmul_rn(xh, r0);
+    const float wre = __fmaf_rn(xh, rc, __fmaf_rn(xl, r0, __fmaf_rn(xh, r0, -wr)));
+    const float wi = __fmul_rn(yh, r0);
+    const float wie = __fmaf_rn(yh, rc, __fmaf_rn(yl, r0, __fmaf_rn(yh, r0, -wi)));
+    // cr: the three large terms ar, wr br, wi bi exactly (split products, TwoSum),
+    // then the small ones (lo parts, product errors, cross terms) in FP32
+    float crh, crl;
+    {
+        const float p1 = __fmul_rn(wr, brh), e1 = __fmaf_rn(wr, brh, -p1);
+        const float p2 = __fmul_rn(wi, bih), e2 = __fmaf_rn(wi, bih, -p2);
+        float t1, te, ce;
+        two_sum(p1, p2, t1, te);
+        two_sum(arh, t1, crh, ce);
+        float l = __fadd_rn(__fadd_rn(ce, te), __fadd_rn(arl, __fadd_rn(e1, e2)));
+        l = __fmaf_rn(wre, brh, __fmaf_rn(wr, brl, l));
+        crl = __fmaf_rn(wie, bih, __fmaf_rn(wi, bil, l));
+    }
+    float cih, cil;
+    {
+        const float p3 = __fmul_rn(wr, bih), e3 = __fmaf_rn(wr, bih, -p3);
+        const float p4 = __fmul_rn(-wi, brh), e4 = __fmaf_rn(-wi, brh, -p4);
+        float t2, te, ce;
+        two_sum(p3, p4, t2, te);
+        two_sum(aih, t2, cih, ce);
+        float l = __fadd_rn(__fadd_rn(ce, te), __fadd_rn(ail, __fadd_rn(e3, e4)));
+        l = __fmaf_rn(wre, bih, __fmaf_rn(wr, bil, l));
+        cil = __fmaf_rn(-wie, brh, __fmaf_rn(-wi, brl, l));
+    }
+    // |c|^2 = cr^2 + ci^2 after renormalising each pair (cancellation can leave
+    // the lo part as large as the hi part)
+    float ch, cl, dh, dl;
+    two_sum(crh, crl, ch, cl);
+    two_sum(cih, cil, dh, dl);
+    const float c2 = __fmul_rn(ch, ch);
+    const float c2e = __fmaf_rn(__fadd_rn(ch, ch), cl, __fmaf_rn(ch, ch, -c2));
+    const float d2 = __fmul_rn(dh, dh);
+    const float d2e = __fmaf_rn(__fadd_rn(dh, dh), dl, __fmaf_rn(dh, dh, -d2));
+    float nh, ne;
+    two_sum(c2, d2, nh, ne);
+    ne = __fadd_rn(ne, __fadd_rn(c2e, d2e));
+    oh = __fmul_rn(0.5f, nh);  // exact scalings
+    ol = __fmul_rn(0.5f, ne);
+    return true;
+}
+
+// |c+|^2 of point idx (global row row0 + idx / nx) as a double: the double-float
+// form above, or FP64 for the tiny-|P_out| points.  The spinor is given both
+// as hi/lo pairs and (for that FP64 form) as doubles.
+struct SpinorDF {
+    float arh, arl, aih, ail, brh, brl, bih, bil;
+};
+
+__device__ __forceinline__ double project_node(const ReqDesc &R, int64_t col, int64_t row,
+                                               const SpinorDF &v, double ar, double ai, double br,
+                                               double bi)
+{
+    const float2 cx = R.nodes_out[col], cy = R.nodes_out[R.nx + row];
+    float oh, ol;
+    if (project_df(cx.x, cx.y, cy.x, cy.y, v.arh, v.arl, v.aih, v.ail, v.brh, v.brl, v.bih,
+                   v.bil, oh, ol))
+        return __dadd_rn(static_cast<double>(oh), static_cast<double>(ol));
+    const double vs = R.valley > 0 ? 1.0 : -1.0;
+    const double px = grid_node(R.px_min, R.hx, col);
+    const double py = grid_node(R.py_min, R.hy, R.row0 + row);
+    return project_point(px + R.a_out[0], py + R.a_out[1], vs, ar, ai, br, bi);
 }
 
 // Fixed pairwise tree over kTilePoints doubles in shared memory (deterministic).
@@ -533,7 +677,7 @@ __device__ __forceinline__ void apply_f32(MixedPoint &s, float cm1, float qr, fl
 }
 
 // dt*P = dt p_hi + (dt A + dt p_lo), rounded in that order.
-__device__ __forceinline__ float momentum_f32(float ph, float a, float pl)
+[[maybe_unused]] __device__ __forceinline__ float momentum_f32(float ph, float a, float pl)
 {
     return __fadd_rn(ph, __fadd_rn(a, pl));
 }
@@ -932,7 +1076,7 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
         double px = 0.0, py = 0.0;
         if (valid) {
             px = grid_node(R.px_min, R.hx, idx % R.nx);
-            py = grid_node(R.py_min, R.hy, idx / R.nx);
+            py = grid_node(R.py_min, R.hy, R.row0 + idx / R.nx);
         }
         // valley K- is stepped as K+ on -P: the table holds -dt*A, here -dt*p
         const double tx = vs * (R.dt * px), ty = vs * (R.dt * py);
@@ -1157,16 +1301,18 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
         const int64_t idx = base + s * kMixedThreads + tid;
         cp2[s] = 0.0;
         if (idx < R.n_points) {
-            hi_plane[idx] = make_float4(pt[s].ar, pt[s].ai, pt[s].br, pt[s].bi);
-            lo_plane[idx] = make_float4(pt[s].lar, pt[s].lai, pt[s].lbr, pt[s].lbi);
+            if (R.store_state) {
+                hi_plane[idx] = make_float4(pt[s].ar, pt[s].ai, pt[s].br, pt[s].bi);
+                lo_plane[idx] = make_float4(pt[s].lar, pt[s].lai, pt[s].lbr, pt[s].lbi);
+            }
             if (R.project) {
-                const double px = grid_node(R.px_min, R.hx, idx % R.nx);
-                const double py = grid_node(R.py_min, R.hy, idx / R.nx);
-                const double ar = static_cast<double>(pt[s].ar) + pt[s].lar;
-                const double ai = static_cast<double>(pt[s].ai) + pt[s].lai;
-                const double br = static_cast<double>(pt[s].br) + pt[s].lbr;
-                const double bi = static_cast<double>(pt[s].bi) + pt[s].lbi;
-                cp2[s] = project_point(px + R.a_out[0], py + R.a_out[1], vs, ar, ai, br, bi);
+                const SpinorDF v{pt[s].ar, pt[s].lar, pt[s].ai, pt[s].lai,
+                                 pt[s].br, pt[s].lbr, pt[s].bi, pt[s].lbi};
+                cp2[s] = project_node(R, idx % R.nx, idx / R.nx, v,
+                                      static_cast<double>(pt[s].ar) + pt[s].lar,
+                                      static_cast<double>(pt[s].ai) + pt[s].lai,
+                                      static_cast<double>(pt[s].br) + pt[s].lbr,
+                                      static_cast<double>(pt[s].bi) + pt[s].lbi);
                 if (R.map)
                     static_cast<float *>(R.map)[idx] = static_cast<float>(cp2[s]);
             }
@@ -1253,7 +1399,7 @@ __device__ void body_f64(const ReqDesc &R, int tile, unsigned char *smem, uint64
         double px = 0.0, py = 0.0;
         if (valid) {
             px = grid_node(R.px_min, R.hx, idx % R.nx);
-            py = grid_node(R.py_min, R.hy, idx / R.nx);
+            py = grid_node(R.py_min, R.hy, R.row0 + idx / R.nx);
         }
         pt[s].tx = vs * (R.dt * px);  // valley K- is stepped as K+ on -P
         pt[s].ty = vs * (R.dt * py);
@@ -1293,13 +1439,18 @@ __device__ void body_f64(const ReqDesc &R, int tile, unsigned char *smem, uint64
         const int64_t idx = base + s * kThreads + tid;
         cp2[s] = 0.0;
         if (idx < R.n_points) {
-            a_plane[idx] = make_double2(pt[s].ar, pt[s].ai);
-            b_plane[idx] = make_double2(pt[s].br, pt[s].bi);
+            if (R.store_state) {
+                a_plane[idx] = make_double2(pt[s].ar, pt[s].ai);
+                b_plane[idx] = make_double2(pt[s].br, pt[s].bi);
+            }
             if (R.project) {
-                const double px = grid_node(R.px_min, R.hx, idx % R.nx);
-                const double py = grid_node(R.py_min, R.hy, idx / R.nx);
-                cp2[s] = project_point(px + R.a_out[0], py + R.a_out[1], vs, pt[s].ar, pt[s].ai,
-                                       pt[s].br, pt[s].bi);
+                SpinorDF v;
+                split_f64(pt[s].ar, v.arh, v.arl);
+                split_f64(pt[s].ai, v.aih, v.ail);
+                split_f64(pt[s].br, v.brh, v.brl);
+                split_f64(pt[s].bi, v.bih, v.bil);
+                cp2[s] = project_node(R, idx % R.nx, idx / R.nx, v, pt[s].ar, pt[s].ai, pt[s].br,
+                                      pt[s].bi);
                 if (R.map)
                     static_cast<double *>(R.map)[idx] = cp2[s];
             }
@@ -1356,14 +1507,14 @@ __global__ void __launch_bounds__(kMixedThreads, kMixedMinBlocks)
     const int r = find_request(args);
     const ReqDesc &R = args.r[r];
     const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
-    if (!tile_ok(R, tile, args.err))
+    if (!tile_ok(R, tile, R.err))
         return;
     if (R.scheme == 0)
-        dispatch_mixed<0, 0>(R, tile, smem, bars, args.err);
+        dispatch_mixed<0, 0>(R, tile, smem, bars, R.err);
     else if (R.scheme == 1)
-        dispatch_mixed<1, 0>(R, tile, smem, bars, args.err);
+        dispatch_mixed<1, 0>(R, tile, smem, bars, R.err);
     else
-        dispatch_mixed<2, 0>(R, tile, smem, bars, args.err);
+        dispatch_mixed<2, 0>(R, tile, smem, bars, R.err);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -1380,14 +1531,98 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r = find_request(args);
     const ReqDesc &R = args.r[r];
     const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
-    if (!tile_ok(R, tile, args.err))
+    if (!tile_ok(R, tile, R.err))
         return;
     if (R.scheme == 0)
-        dispatch_f64<0, 0>(R, tile, smem, bars, args.err);
+        dispatch_f64<0, 0>(R, tile, smem, bars, R.err);
     else if (R.scheme == 1)
-        dispatch_f64<1, 0>(R, tile, smem, bars, args.err);
+        dispatch_f64<1, 0>(R, tile, smem, bars, R.err);
     else
-        dispatch_f64<2, 0>(R, tile, smem, bars, args.err);
+        dispatch_f64<2, 0>(R, tile, smem, bars, R.err);
+}
+
+// Projection of a state already on the device (a launch with no steps): one CTA
+// per 1024-point tile, kProjThreads threads x kProjPoints points, loads of the
+// whole tile issued before any arithmetic.  The value of each point comes from
+// project_node and the tile sum from the same pairwise tree as the fused
+// projection of the evolve kernels (tile slot k holds point base + k; thread t
+// holds slots t, t + 256, t + 512, t + 768, so the tree's first two levels are
+// in registers), so both give the same bits.  HBM-bound: 32 bytes of state read
+// and 4 (FP32_MIXED) or 8 (FP64) bytes of map written per point.
+constexpr int kProjThreads = 256;
+constexpr int kProjPoints = kTilePoints / kProjThreads;
+static_assert(kProjPoints == 4, "the first two tree levels are taken in registers");
+
+template <int PREC>
+__global__ void __launch_bounds__(kProjThreads, 3)
+    project_kernel(const __grid_constant__ EvolveArgs args)
+{
+    __shared__ double red[kProjThreads];
+    const int r = find_request(args);
+    const ReqDesc &R = args.r[r];
+    const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
+    if (!tile_ok(R, tile, R.err))
+        return;
+    const int tid = threadIdx.x;
+    const int64_t base = static_cast<int64_t>(tile) * kTilePoints;
+    using Half = typename std::conditional<PREC == 1, float4, double2>::type;
+    const Half *p0 = static_cast<const Half *>(R.state);
+    const Half *p1 = p0 + R.n_points;
+    Half u[kProjPoints], w[kProjPoints];
+#pragma unroll
+    for (int s = 0; s < kProjPoints; ++s) {
+        const int64_t idx = base + s * kProjThreads + tid;
+        if (idx < R.n_points) {
+            u[s] = p0[idx];
+            w[s] = p1[idx];
+        }
+    }
+    // column and row of the first point, then stepped (no division per point)
+    int64_t col = (base + tid) % R.nx, row = (base + tid) / R.nx;
+    double v[kProjPoints];
+#pragma unroll
+    for (int s = 0; s < kProjPoints; ++s) {
+        const int64_t idx = base + s * kProjThreads + tid;
+        v[s] = 0.0;
+        if (idx < R.n_points) {
+            SpinorDF d;
+            double ar, ai, br, bi;
+            if constexpr (PREC == 1) {  // hi plane u, lo plane w
+                d = SpinorDF{u[s].x, w[s].x, u[s].y, w[s].y, u[s].z, w[s].z, u[s].w, w[s].w};
+                ar = static_cast<double>(u[s].x) + w[s].x;
+                ai = static_cast<double>(u[s].y) + w[s].y;
+                br = static_cast<double>(u[s].z) + w[s].z;
+                bi = static_cast<double>(u[s].w) + w[s].w;
+            } else {  // a plane u, b plane w
+                ar = u[s].x; ai = u[s].y; br = w[s].x; bi = w[s].y;
+                split_f64(ar, d.arh, d.arl);
+                split_f64(ai, d.aih, d.ail);
+                split_f64(br, d.brh, d.brl);
+                split_f64(bi, d.bih, d.bil);
+            }
+            v[s] = project_node(R, col, row, d, ar, ai, br, bi);
+            if (R.map) {
+                if constexpr (PREC == 1)
+                    static_cast<float *>(R.map)[idx] = static_cast<float>(v[s]);
+                else
+                    static_cast<double *>(R.map)[idx] = v[s];
+            }
+        }
+        col += kProjThreads;
+        while (col >= R.nx) {
+            col -= R.nx;
+            ++row;
+        }
+    }
+    red[tid] = (v[0] + v[2]) + (v[1] + v[3]);  // tree levels 512 and 256
+    __syncthreads();
+    for (int s = kProjThreads / 2; s > 0; s >>= 1) {
+        if (tid < s)
+            red[tid] += red[tid + s];
+        __syncthreads();
+    }
+    if (tid == 0)
+        R.partials[tile] = red[0];
 }
 
 // One CTA per density: fixed-order per-thread sums, then a pairwise tree.
@@ -1419,7 +1654,7 @@ __global__ void __launch_bounds__(128) combine_kernel(const __grid_constant__ Co
         return;
     const double vs = a.valley > 0 ? 1.0 : -1.0;
     const double px = grid_node(a.px_min, a.hx, idx % a.nx);
-    const double py = grid_node(a.py_min, a.hy, idx / a.nx);
+    const double py = grid_node(a.py_min, a.hy, a.row0 + idx / a.nx);
     double ar, ai, br, bi;
     initial_spinor(px + a.a_in[0], py + a.a_in[1], vs, ar, ai, br, bi);
     const size_t slab = static_cast<size_t>(a.n_points) * 32;
@@ -1482,6 +1717,17 @@ cudaError_t launch_evolve(const EvolveArgs &args, int precision, cudaStream_t st
         evolve_mixed_kernel<<<args.total_tiles, kMixedThreads, 0, stream>>>(args);
     else
         evolve_f64_kernel<<<args.total_tiles, kF64Threads, 0, stream>>>(args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project(const EvolveArgs &args, int precision, cudaStream_t stream)
+{
+    if (args.nreq <= 0 || args.total_tiles <= 0)
+        return cudaSuccess;
+    if (precision == 1)
+        project_kernel<1><<<args.total_tiles, kProjThreads, 0, stream>>>(args);
+    else
+        project_kernel<0><<<args.total_tiles, kProjThreads, 0, stream>>>(args);
     return cudaGetLastError();
 }
 

@@ -11,9 +11,10 @@
 // The scratch is a file-scope __device__ array of kStaticMaxTiles + 1 doubles
 // (about 512 KB); every GPU that loads the library holds it until the process
 // exits.  Its device address is looked up once per device with
-// cudaGetSymbolAddress on the first call made with that device current; the
-// kernels are given that address (in host code the array's name is only a
-// host-side stand-in, never a device address).
+// cudaGetSymbolAddress on the first call made with that device current and
+// cached for the rest of the process (a cudaDeviceReset afterwards is not
+// supported); the kernels are given that address (in host code the array's
+// name is only a host-side stand-in, never a device address).
 //
 // The arithmetic is the same as the reduction behind dsp_reduce_density: the
 // same 1024-point tiles, the same fixed pairwise tree per tile, the same
@@ -132,6 +133,9 @@ extern "C" dsp_status dsp_density_noalloc(const void *map_dev, int32_t precision
     const double scale = 4.0 / ((2.0 * 3.14159265358979323846) * (2.0 * 3.14159265358979323846)) *
                          hx * hy;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    // a non-sticky error left by the caller's earlier launches is cleared here,
+    // so the check after the launches reports this call's own
+    (void)cudaGetLastError();
     // Every partial and the result slot are overwritten, so nothing left over
     // from an earlier call is read.
     noalloc_tile_sums<<<n_tiles, dsp::kThreads, 0, stream>>>(map_dev, precision, n_points, scratch);

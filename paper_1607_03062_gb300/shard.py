@@ -1,6 +1,6 @@
 """Host-side work partitioning across ranks (one process per GPU).
 
-The momenta are independent (Sec. III: "each momentum is independent"), so the
+The momenta are independent (Sec. III: every momentum carries its own spinor), so the
 path shards without any data exchange: whole solves (independent pulse
 samples or requests) go to ranks round-robin, or one large grid is cut into
 bands of rows.  The only cross-rank steps are host-side: the max of the
@@ -23,12 +23,14 @@ def row_band(ny: int, rank: int, world: int) -> tuple[int, int]:
 
 
 def band_grid(grid: dict, rank: int, world: int) -> dict:
-    """The sub-grid of a rank's row band, with its own p_y range (cell-centred
-    nodes of the band coincide with the full grid's rows up to rounding)."""
+    """The band descriptor of a rank: the full grid (nx, ny, box) plus its rows
+    [r0, r1).  Nodes are never re-derived from the band: the library
+    (``dsp_create_band``, ``binding.Grid(..., rows=...)``) and the oracle both
+    compute the full grid's nodes of those global rows, so a band's points are
+    bitwise the full grid's."""
     r0, r1 = row_band(grid["ny"], rank, world)
-    lo, hi = grid["py"]
-    h = (hi - lo) / grid["ny"]
-    return {"nx": grid["nx"], "ny": r1 - r0, "px": grid["px"], "py": (lo + r0 * h, lo + r1 * h)}
+    return {"nx": grid["nx"], "ny": grid["ny"], "px": grid["px"], "py": grid["py"],
+            "rows": (r0, r1)}
 
 
 def combine_densities(parts: list[float]) -> float:

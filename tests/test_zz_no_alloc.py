@@ -59,6 +59,27 @@ def test_noalloc_matches_reduce_density_on_consecutive_calls():
         g.close()
 
 
+def test_noalloc_above_1024_tiles_and_at_the_maximum_size():
+    """2048 tiles (the final sum then strides: each of its 1024 threads adds two
+    tile sums before the tree) against dsp_reduce_density, bitwise for an FP64
+    map, on two calls in a row; and a map of exactly DSP_NOALLOC_MAX_POINTS
+    points (a 256 MB float map of zeros) is accepted and sums to 0."""
+    grid = {"nx": 2048, "ny": 1024, "px": (-5.0, 5.0), "py": (-4.0, 4.0)}
+    (g, n_ref), = [_solved(grid, W.sin2_pulse(1.5, 1.55, 2.0), 120, "fp64")]
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        n = B.density_noalloc(g.map.data_ptr(), "fp64", grid["nx"], grid["ny"], grid["px"],
+                              grid["py"], stream)
+        assert n == n_ref and n > 0
+    g.close()
+    side = 8192
+    assert side * side == 67108864  # DSP_NOALLOC_MAX_POINTS
+    zeros = torch.zeros(side * side, dtype=torch.float32, device="cuda")
+    assert B.density_noalloc(zeros.data_ptr(), "fp32_mixed", side, side, (-1, 1), (-1, 1),
+                             stream) == 0.0
+    del zeros
+
+
 def test_noalloc_refuses_maps_beyond_its_static_scratch():
     with pytest.raises(B.DSPError) as e:
         B.density_noalloc(16, "fp32_mixed", 8193, 8192, (-1, 1), (-1, 1))
