@@ -139,15 +139,16 @@ class ClockSampler:
 # SHA-256 of the kernel source the counters were taken on; a different source
 # means the counters are stale and the traffic is reported as null.
 KERNEL_TRAFFIC = {
-    "evolve_mixed_kernel": {"bytes": None, "source_sha256": None},
+    "evolve_strip_kernel": {"bytes": None, "source_sha256": None},
 }
 
 
 def kernel_source_sha256():
-    """SHA-256 over the kernel sources (the .cu file and the descriptor header)."""
+    """SHA-256 over the kernel sources (the .cu file and the headers it includes)."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("dsp_kernels.cu", "dsp_internal.h"):
+    for name in ("dsp_strip.cu", "dsp_mixed.cu", "dsp_kernels.cu", "dsp_device.cuh",
+                 "dsp_internal.h", "dsp_df.cuh"):
         with open(os.path.join(ROOT, "paper_1607_03062_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -188,16 +189,21 @@ def load_peaks():
 #   Re alpha - 1 rebuilt from unitarity (one Newton step)       8
 #   update and Fast2Sum as above                                28
 # i.e. 20 + dc + ds + 22/G per spinor-step.  Single steps (G = 1): 32 + dc + ds.
-# FP64 instructions per spinor-step of the FP64 EXACT step:
-#   P (2) + theta^2 (2) + cos (dc) + sinc (ds) + q (2) + U psi (12)
 # ------------------------------------------------------------------------------------------
 
-def ops_mixed(dc, ds, group=2):
+def ops_mixed(dc, ds, group=2, strips=False):
+    """FP32 lane instructions per spinor-step of the FP32-mixed EXACT path.  On row
+    strips (strips=True) the momentum work of a step is shared: each thread forms
+    dt P_x once for its 4 spinors (2 scalar adds: 0.5 per spinor) and reads dt P_y
+    and fl(dt P_y^2) from the strip's row table, so the per-step coefficients cost
+    theta^2 (1) + dc + ds + q (2) + 0.5 = 3.5 + dc + ds instead of 8 + dc + ds (the
+    table itself, 3 operations per row and step for 1024 spinors, is left out)."""
+    save = 4.5 if strips else 0.0
     if group == 1:
-        return 32 + dc + ds
+        return 32 + dc + ds - save
     if group == 2:
-        return 28.5 + dc + ds
-    return 20 + dc + ds + 22.0 / group
+        return 28.5 + dc + ds - save
+    return 20 + dc + ds + 22.0 / group - save
 
 
 def ops_magnus4(dc, ds, group=1):
@@ -210,18 +216,25 @@ def ops_magnus4(dc, ds, group=1):
     return 28 + dc + ds + 21.0 / group
 
 
-def ops_strang(dc, ds, group=1):
+def ops_strang(dc, ds, group=1, strips=False):
     """FP32 lane instructions per spinor-step of the STRANG_XY path.  Per step: 4 (P) +
     2 (P_x^2, P_y^2) + 2 dc + 2 ds (cos - 1 and sin/theta - 1 of both) + 5 (sin 2a, sin b,
     cos b sin 2a, m).  Single steps: + 28 (update, Fast2Sum).  Groups of G: the EXACT
-    chain, + 12 per further step, 10 to start it, 8 + 28 per group."""
+    chain, + 12 per further step, 10 to start it, 8 + 28 per group.  On row strips the
+    P_y parts come from the strip's row table and the P_x parts are formed once per
+    thread for its 4 spinors: 3 per spinor (cos b sin 2a, m) + (4 + dc + ds) / 4."""
+    coef = 3 + (4 + dc + ds) / 4.0 if strips else 11 + 2 * (dc + ds)
     if group == 1:
-        return 39 + 2 * (dc + ds)
-    return 23 + 2 * (dc + ds) + 22.0 / group
+        return coef + 28
+    return coef + 12 + 22.0 / group
 
 
-def ops_fp64(dc, ds):
-    return 18 + dc + ds
+def ops_fp64(dc, ds, strips=False):
+    """FP64 instructions per spinor-step of the FP64 EXACT step: P (2) + theta^2 (2) +
+    cos (dc) + sinc (ds) + q (2) + U psi (12).  On row strips dt P_x is formed once
+    per thread for its 4 spinors (0.25 each) and dt P_y, fl(dt P_y^2) come from the
+    strip's row table: 15.25 + dc + ds."""
+    return (15.25 if strips else 18) + dc + ds
 
 
 # ------------------------------------------------------------------------------------------
@@ -267,6 +280,8 @@ def run_gpu(args):
     kept = {}  # (precision, sample) -> host |c+|^2 map, for the accuracy check
     dens_by = {}  # (precision, sample) -> density
 
+    strips_seen = []
+
     def timed_solves(prec, warm, steps, sample_offset, keep_sample=None):
         h, state, mp = make(prec)
         dens = []
@@ -294,11 +309,13 @@ def run_gpu(args):
                 times.append(e0.elapsed_time(e1) / 1e3)
                 dens.append(B.reduce_density(h))
                 info = B.get_info(h)
+                strips_seen.append(bool(info["row_strips"]))
                 if prec == "fp64":
-                    ops.append(ops_fp64(info["cos_degree"], info["sinc_degree"]))
+                    ops.append(ops_fp64(info["cos_degree"], info["sinc_degree"],
+                                        bool(info["row_strips"])))
                 else:
                     ops.append(ops_mixed(info["cos_degree"], info["sinc_degree"],
-                                         info["group_steps"]))
+                                         info["group_steps"], bool(info["row_strips"])))
         B.destroy_grid(h)
         del state, mp
         return times, dens, ops
@@ -316,6 +333,7 @@ def run_gpu(args):
         tot = float(t.item())
     work_per_solve = float(n) * n * nsteps
     value = work_per_solve * args.steps * world / tot
+    strips_used = bool(strips_seen) and all(strips_seen)
 
     # ---- FP64 ----
     fp64 = None
@@ -395,10 +413,11 @@ def run_gpu(args):
     peaks = load_peaks()
     # achieved = algorithmic FP32 instructions of each timed launch / its event time
     achieved = statistics.mean(o * work_per_solve / t for o, t in zip(o_mixed, t_mixed)) / 1e12
+    kernel_name = "evolve_strip_kernel" if strips_used else "evolve_mixed_kernel"
     peak = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "Tinst/s (FP32 lane instructions)", "frac": achieved / peak,
-            "traffic": kernel_traffic("evolve_mixed_kernel"), "kernel": "evolve_mixed_kernel",
+            "traffic": kernel_traffic(kernel_name), "kernel": kernel_name,
             "ops_per_spinor_step": o_mixed,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts x max SM clock)"}
     roof["ceiling_spinor_steps_per_s"] = peak * 1e12 / statistics.mean(o_mixed)
@@ -493,7 +512,11 @@ def scheme_leg(args, cfgs, stream, world, rank, scheme, warm=1, reps=2):
         if k >= warm:
             times.append(e0.elapsed_time(e1) / 1e3)
             info = B.get_info(h)
-            ops.append(ops_fn(info["cos_degree"], info["sinc_degree"], info["group_steps"]))
+            if scheme == "strang_xy":
+                ops.append(ops_fn(info["cos_degree"], info["sinc_degree"], info["group_steps"],
+                                  bool(info["row_strips"])))
+            else:
+                ops.append(ops_fn(info["cos_degree"], info["sinc_degree"], info["group_steps"]))
     B.destroy_grid(h)
     work = float(n) * n * args.time_steps
     achieved = statistics.mean(o * work / t for o, t in zip(ops, times)) / 1e12
@@ -554,8 +577,8 @@ def projection_leg(args, stream, flush, reps=10, warm=3):
     """dsp_project of a state already on the device (a launch with no steps), on
     the 4096^2 two-colour grid after 512 steps, in both precisions: the
     projection kernel reads the 32-byte state of every point and writes its map
-    value (4 bytes FP32-mixed, 8 bytes FP64), plus one double per 1024-point
-    tile.  Algorithmic bytes / CUDA-event time of the launch, against the
+    value (4 bytes FP32-mixed, 8 bytes FP64), plus one double per 256-point
+    granule of the density sum.  Algorithmic bytes / CUDA-event time of the launch, against the
     measured HBM copy bandwidth; L2 flushed before every launch (the state alone
     is 537 MB, four times the L2)."""
     import torch
@@ -587,8 +610,8 @@ def projection_leg(args, stream, flush, reps=10, warm=3):
             if k >= warm:
                 times.append(e0.elapsed_time(e1) / 1e3)
         grid.close()
-        tiles = (n * n + 1023) // 1024
-        alg = n * n * (32 + map_bytes) + 8 * tiles
+        parts = (n * n + 255) // 256
+        alg = n * n * (32 + map_bytes) + 8 * parts
         t = statistics.median(times)
         gbs = alg / t / 1e9
         out[prec] = {"us": round(t * 1e6, 2), "algorithmic_bytes": alg,

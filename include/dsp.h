@@ -157,8 +157,10 @@ dsp_status dsp_evolve(dsp_grid *g, int64_t steps);
  * it back and writes the map (4 or 8 bytes per point).  Asynchronous. */
 dsp_status dsp_project(dsp_grid *g, void *map_dev);
 
-/* Reduces the last projection to the pair density n (eV^2) with a fixed-order
- * FP64 tree (deterministic: bitwise the same on every run), times
+/* Reduces the last projection to the pair density n (eV^2) in a fixed order
+ * (deterministic: bitwise the same on every run; double-float pairwise trees
+ * over granules of 256 consecutive points, then an FP64 sum of the granules),
+ * times
  * 4/(2 pi)^2 * hx * hy (Sec. II, Eq. (pair_prod_homo), degeneracy 4).  Needs a
  * projection since the last dsp_set_pulse (DSP_E_STATE otherwise).  Writes
  * *n_host; synchronises the grid's stream. */
@@ -176,8 +178,8 @@ dsp_status dsp_reduce_density(dsp_grid *g, double *n_host);
  *   dsp_reduce_density returns, summed in the same fixed order (bitwise equal
  *   to it for an FP64 map).
  * Scratch: a static device array inside the library sized for at most
- * DSP_NOALLOC_MAX_POINTS points (about 512 KB, held on every GPU that loads
- * the library until the process exits); larger maps are refused with
+ * DSP_NOALLOC_MAX_POINTS points (one double per 256 points, about 2 MB, held
+ * on every GPU that loads the library until the process exits); larger maps are refused with
  * DSP_E_INVALID before anything is queued.  The first call made with a given
  * device current looks up the array's device address (cudaGetSymbolAddress)
  * and caches it for the rest of the process; make that first call before any
@@ -239,7 +241,7 @@ dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps);
 
 /* What the library chose for the current pulse: the degrees (in theta^2) of
  * the cos(theta) and sin(theta)/theta series used per step (picked so their
- * truncation error over all n_steps stays below 2e-8 in FP32_MIXED, 1e-16 in
+ * truncation error over all n_steps stays below 1e-6 in FP32_MIXED, 1e-16 in
  * FP64), theta_max = dt * max|p + A_n| over the box, the tile count, and
  * group_steps G: the number of step operators multiplied into one before each
  * compensated update (FP32_MIXED, every scheme: the largest of 16, 8, 4, 2 with
@@ -253,9 +255,13 @@ typedef struct {
     int64_t n_steps, cursor;
     double dt, theta_max;
     int32_t group_steps;
-    int32_t row_begin; /* first global row (0 unless the grid is a band)      */
-    int32_t ny_total;  /* rows of the full grid (ny unless the grid is a band) */
-    int32_t reserved;
+    int32_t row_begin;  /* first global row (0 unless the grid is a band)      */
+    int32_t ny_total;   /* rows of the full grid (ny unless the grid is a band) */
+    int32_t row_strips; /* 1: evolve launches tile the grid in row strips of 4 rows
+                           x 256 columns (FP32_MIXED EXACT, nx a multiple of 256),
+                           sharing each step's momentum work across a strip;
+                           0: contiguous tiles of 1024 points.  n_tiles counts the
+                           tiles of the tiling in use. */
 } dsp_grid_info;
 dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info);
 
@@ -267,6 +273,14 @@ dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info);
  * the grid returns DSP_E_TIMEOUT, and the grid stays latched in that state.
  * Use it on small grids: the waits of successive CTA waves add up. */
 dsp_status dsp_test_withhold_next_copy(dsp_grid *g);
+
+/* Test hook (not in the paper): strips = 0 makes the grid's evolve launches use
+ * contiguous 1024-point tiles even where it would use row strips (FP32_MIXED
+ * EXACT grids whose nx is a multiple of 256: a CTA then owns 4 rows x 256
+ * columns and shares the per-step momentum work across them); strips = 1
+ * restores the automatic choice.  Both tilings give bitwise the same map and
+ * density; the hook exists so that a test can show it. */
+dsp_status dsp_test_tiling(dsp_grid *g, int32_t strips);
 
 /* Copies the raw spinor state (dsp_state_bytes bytes) to the host, or back
  * from the host, with the step cursor, for checkpoint / resume.  Synchronise. */

@@ -50,6 +50,9 @@ def main(argv=None):
                     help="seeded (omega, E0) draw of the LZS scan (lzs_2048 only), 0..7")
     ap.add_argument("--vs-fp64", action="store_true",
                     help="also solve in FP64 and report the map's error over every point")
+    ap.add_argument("--reproject", type=int, default=0, metavar="N",
+                    help="after the solve, project the final state N more times (the "
+                         "projection-only launch) and report its time and bytes per second")
     a = ap.parse_args(argv)
 
     import torch
@@ -83,7 +86,25 @@ def main(argv=None):
            "density_eV2": n, "max_cplus2": float(m.max().item()), "wall_s": wall,
            "spinor_steps_per_s": g["nx"] * g["ny"] * steps / wall,
            "series_degrees": [info["cos_degree"], info["sinc_degree"]],
-           "group_steps": info["group_steps"], "theta_max": info["theta_max"]}
+           "group_steps": info["group_steps"], "theta_max": info["theta_max"],
+           "row_strips": info["row_strips"]}
+    if a.reproject > 0:
+        # the standalone projection: reads the 32-byte state of every point, writes
+        # the map (4 or 8 bytes) and one double per 256-point granule
+        times = []
+        for _ in range(a.reproject):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            grid.project()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        pts = g["nx"] * g["ny"]
+        nbytes = pts * (32 + (8 if a.precision == "fp64" else 4)) + 8 * ((pts + 255) // 256)
+        t = float(np.median(times))
+        out["reproject"] = {"launches": a.reproject, "median_us": t * 1e6,
+                            "algorithmic_bytes": nbytes, "gbs": nbytes / t / 1e9}
     grid.close()
     if a.vs_fp64 and a.precision != "fp64":
         ref = B.Grid(g["nx"], g["ny"], g["px"], g["py"], "fp64", a.scheme, a.valley)

@@ -41,6 +41,7 @@ EXPORTS = (
     "dsp_server_query", "dsp_server_cancel", "dsp_server_destroy", "dsp_density_noalloc",
     "dsp_get_info", "dsp_solve_segmented", "dsp_sample_pulse_gauss",
     "dsp_test_withhold_next_copy", "dsp_create_band", "dsp_set_keep_final_state",
+    "dsp_test_tiling",
 )
 
 
@@ -62,7 +63,7 @@ class GridInfo(ctypes.Structure):
         ("n_steps", ctypes.c_int64), ("cursor", ctypes.c_int64), ("dt", ctypes.c_double),
         ("theta_max", ctypes.c_double),
         ("group_steps", ctypes.c_int32), ("row_begin", ctypes.c_int32),
-        ("ny_total", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+        ("ny_total", ctypes.c_int32), ("row_strips", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -125,6 +126,7 @@ def lib() -> ctypes.CDLL:
                 "dsp_solve_segmented": (i32, [p, i32, p, pd]),
                 "dsp_sample_pulse_gauss": (i32, [ctypes.POINTER(PulseSpec), i64, p, p, p, pd]),
                 "dsp_test_withhold_next_copy": (i32, [p]),
+                "dsp_test_tiling": (i32, [p, i32]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -303,6 +305,12 @@ def test_withhold_next_copy(h: int):
     """Failure-path test hook: the next launch's first table chunk is never
     copied, so its bounded device-side wait runs out (DSP_E_TIMEOUT)."""
     _check(lib().dsp_test_withhold_next_copy(ctypes.c_void_p(h)), "test_withhold_next_copy")
+
+
+def test_tiling(h: int, strips: bool):
+    """Test hook: False forces contiguous tiles on a grid that would use row
+    strips (the results are bitwise the same either way)."""
+    _check(lib().dsp_test_tiling(ctypes.c_void_p(h), 1 if strips else 0), "test_tiling")
 
 
 def status_string(code: int) -> str:

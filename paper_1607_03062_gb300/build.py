@@ -1,6 +1,7 @@
 """Builds the in-tree CUDA library ``_build/libdsp.so`` for sm_103a.
 
-Three translation units (kernels, host API, the allocation-free density) are
+Five translation units (the FP32-mixed evolve kernel on contiguous tiles and on
+row strips, the other kernels, the host API, the allocation-free density) are
 compiled in parallel with nvcc, then linked into one shared library with the
 CUDA runtime linked statically.  Host code is compiled without floating-point
 contraction, so the host-side arithmetic (pulse tables, projection nodes) rounds
@@ -32,14 +33,17 @@ def _nvcc() -> str:
 
 
 def sources() -> list[str]:
-    return [os.path.join(CSRC, f) for f in ("dsp_kernels.cu", "dsp_api.cpp", "dsp_noalloc.cu")]
+    return [os.path.join(CSRC, f) for f in ("dsp_mixed.cu", "dsp_strip.cu", "dsp_kernels.cu",
+                                            "dsp_api.cpp", "dsp_noalloc.cu")]
 
 
 def _stale(lib: str = LIB) -> bool:
     if not os.path.exists(lib):
         return True
     t = os.path.getmtime(lib)
-    deps = sources() + [os.path.join(CSRC, "dsp_internal.h"), os.path.join(INCLUDE, "dsp.h"),
+    deps = sources() + [os.path.join(CSRC, h) for h in ("dsp_internal.h", "dsp_df.cuh",
+                                                        "dsp_device.cuh")] + [
+                        os.path.join(INCLUDE, "dsp.h"),
                         os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 

@@ -1,0 +1,1127 @@
+// dsp_device.cuh -- device code shared by the kernels of the split-operator
+// massless-Dirac solver (sm_103a; not installed).  The kernels themselves are in
+// dsp_mixed.cu (FP32_MIXED, contiguous tiles), dsp_strip.cu (FP32_MIXED, row
+// strips) and dsp_kernels.cu (FP64, projection, density, time segments), compiled
+// as separate translation units.
+//
+// Method (arXiv 1607.03062):
+//   Sec. II Eq. (free_spin1..4)  initial state v(p + A_in), normalised;
+//   Sec. III Eq. (ev_op_dt)      product of N one-step operators, in time order;
+//   Sec. III Eq. (approx_time)   step n uses P_n = p + A(t_i + (n + 1/2) dt);
+//   Sec. III closed form         U_n = cos(theta) I - i sin(theta) valley sigma.P/|P|,
+//                                theta = dt |P_n|;
+//   Sec. II Eq. (pair_prod_homo) |c+|^2 = |u(p + A_out)^dag psi|^2, summed to n.
+//
+// GB300 design (one CTA = one tile of 1024 momenta; FP32-mixed: 256 threads x 4
+// spinors, FP64: 512 threads x 2 spinors):
+//   * the spinors stay in registers across all steps of a launch: one 16-byte
+//     read and one write per spinor plane per launch;
+//   * A(t) is staged in shared memory in 16 KB chunks (2048 FP32_MIXED steps,
+//     1024 FP64 ones) by 1-D bulk copies (cp.async.bulk) completing on an
+//     mbarrier, double buffered, so the step loop reads each entry with one
+//     broadcast shared-memory load;
+//   * cos(theta) - 1 and sin(theta)/theta are evaluated as their Taylor series
+//     in x = theta^2 = |dt P|^2 (no square root, no sin/cos call): the degree is
+//     chosen per request on the host from theta_max so truncation stays below
+//     the working precision;
+//   * FP32_MIXED: dt*p is split into hi + lo (two floats, the momentum of every
+//     point to ~1e-16 relative), dt*A(t_n) is one float per step, and
+//     P_n = p_hi + (A_n + p_lo): the FP32 roundings of P then change from step
+//     to step with A instead of shifting every step's momentum by the same
+//     amount, and the first one is at A's scale, not P's;
+//   * FP32_MIXED: the spinor is stored as hi + lo and each update adds the
+//     increment (U - I) psi with a Fast2Sum, so the FP32 rounding of psi does not
+//     random-walk over 1e5 steps; every scheme multiplies 2 to 16 steps into one
+//     SU(2) matrix first, so the compensated update is paid once per group, and
+//     two momenta share each packed FP32x2 instruction;
+//   * the projection and the per-tile partial sums of |c+|^2 are fused into the
+//     last launch; partial sums use a fixed pairwise tree, so the density is
+//     bitwise reproducible and independent of the batch a request ran in.
+// No tensor cores: the work is 2x2 complex arithmetic per momentum.
+
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "dsp_df.cuh"
+#include "dsp_internal.h"
+
+namespace dsp {
+namespace {
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk copy (inline PTX)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase with the given parity; gives up after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if (global_ns() - t0 > kWaitLimitNs)
+            return false;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Taylor series in x = theta^2 (written from the power series of cos and sin)
+//   cos(theta) - 1    = sum_{k>=1} (-x)^k / (2k)!
+//   sin(theta)/theta  = sum_{k>=0} (-x)^k / (2k+1)!
+// ---------------------------------------------------------------------------
+
+template <int N>
+__host__ __device__ constexpr double inv_factorial()
+{
+    if constexpr (N <= 1)
+        return 1.0;
+    else
+        return inv_factorial<N - 1>() / static_cast<double>(N);
+}
+
+// Horner tail sum_{k=K..D} c_k x^(k-K) with c_k = (-1)^k / (2k + ODD)!; every
+// coefficient is a compile-time constant rounded once to T.
+template <typename T, int D, int K, int ODD>
+__device__ __forceinline__ T horner(T x)
+{
+    constexpr T c = static_cast<T>(((K & 1) ? -1.0 : 1.0) * inv_factorial<2 * K + ODD>());
+    if constexpr (K == D)
+        return c;
+    else
+        return fma(horner<T, D, K + 1, ODD>(x), x, c);
+}
+
+template <int D>
+__device__ __forceinline__ float cosm1_f32(float x)
+{
+    return horner<float, D, 1, 0>(x) * x;
+}
+template <int D>
+__device__ __forceinline__ float sinc_f32(float x)
+{
+    return horner<float, D, 0, 1>(x);
+}
+template <int D>
+__device__ __forceinline__ double cos_f64(double x)
+{
+    return horner<double, D, 0, 0>(x);
+}
+template <int D>
+__device__ __forceinline__ double sinc_f64(double x)
+{
+    return horner<double, D, 0, 1>(x);
+}
+
+// ---------------------------------------------------------------------------
+// Per-point set-up shared by both precisions (all FP64, once per launch)
+// ---------------------------------------------------------------------------
+
+// Cell-centred node p = p_min + (i + 1/2) h, without contraction.
+__device__ __forceinline__ double grid_node(double lo, double h, int64_t i)
+{
+    return __dadd_rn(lo, __dmul_rn(static_cast<double>(i) + 0.5, h));
+}
+
+// Negative-energy spinor v(P) of valley * sigma.P, normalised (Sec. II Eq.
+// (free_spin1..4)); at P = 0 the limit P -> (0+, 0).
+__device__ __forceinline__ void initial_spinor(double Px, double Py, double sgn, double &ar,
+                                               double &ai, double &br, double &bi)
+{
+    const double r = 0.70710678118654752440;
+    const double E = sqrt(Px * Px + Py * Py);
+    if (E > 0.0) {
+        ar = sgn * (-Px / E) * r;
+        ai = sgn * (Py / E) * r;
+    } else {
+        ar = -sgn * r;
+        ai = 0.0;
+    }
+    br = r;
+    bi = 0.0;
+}
+
+// |u(P_out)^dag psi|^2 with u = [1, valley (Px + i Py)/E]/sqrt(2); 0 at P_out = 0.
+// FP64; used only for the rare points whose |P_out| is too small for the
+// double-float form below.
+__device__ __forceinline__ double project_point(double Px, double Py, double sgn, double ar,
+                                                double ai, double br, double bi)
+{
+    const double E = sqrt(Px * Px + Py * Py);
+    if (!(E > 0.0))
+        return 0.0;
+    const double wr = sgn * Px / E, wi = -sgn * Py / E;  // valley * conj(Px + i Py)/E
+    const double cr = ar + (wr * br - wi * bi);
+    const double ci = ai + (wr * bi + wi * br);
+    return 0.5 * (cr * cr + ci * ci);
+}
+
+// ---------------------------------------------------------------------------
+// The projection |c+|^2 = |u(P_out)^dag psi|^2 in double-float FP32 arithmetic.
+//
+// GB300 issues FP64 at about 1/64 of its FP32 rate, and an FP64 projection (a
+// square root and two divisions per point) would make a projection-only launch
+// FP64-bound at a small fraction of HBM speed.  Here every quantity is an
+// unevaluated pair hi + lo of floats (about 48 significant bits): products are
+// split exactly with FMA, the large terms of c+ are summed with TwoSum, so
+// |c+|^2 comes out to ~1e-14 absolute; only its conversion to double and the
+// tile tree use FP64.  The node P_out = p + A_out (valley-signed) comes from a
+// per-grid table of hi/lo pairs built on the host in FP64.  Written from the
+// definitions (TwoSum, the FMA product split, one Newton step for 1/sqrt);
+// all operations are non-contracting intrinsics, so every kernel that calls it
+// gets the same bits.
+// ---------------------------------------------------------------------------
+
+// Points with E^2 = |P_out|^2 below this (|P_out| < 2^-45 eV) take the FP64
+// form: their squares would lose bits near the bottom of the float range.
+constexpr float kProjTinyE2 = 0x1p-90f;
+
+// |c+|^2 = oh + ol for the node s P_out = (xh + xl, yh + yl) (s = valley) and
+// the spinor a = (ar, ai), b = (br, bi), each component hi + lo:
+//   c+ = (a + conj(w) b)/sqrt(2),  w = s (P_x + i P_y)/|P|,
+//   cr = ar + wr br + wi bi,  ci = ai + wr bi - wi br.
+// Returns false (and leaves oh, ol unset) when E^2 < kProjTinyE2.
+__device__ __forceinline__ bool project_df(float xh, float xl, float yh, float yl, float arh,
+                                           float arl, float aih, float ail, float brh, float brl,
+                                           float bih, float bil, float &oh, float &ol)
+{
+    // E^2 = Px^2 + Py^2 to ~2^-46
+    const float x2 = __fmul_rn(xh, xh);
+    const float x2e = __fmaf_rn(__fadd_rn(xh, xh), xl, __fmaf_rn(xh, xh, -x2));
+    const float y2 = __fmul_rn(yh, yh);
+    const float y2e = __fmaf_rn(__fadd_rn(yh, yh), yl, __fmaf_rn(yh, yh, -y2));
+    float sh, se;
+    two_sum(x2, y2, sh, se);
+    se = __fadd_rn(se, __fadd_rn(x2e, y2e));
+    if (!(sh >= kProjTinyE2))
+        return false;
+    // r = 1/E = r0 + rc: one Newton step r0 (1 - t/2) from the FP32 estimate r0,
+    // with t = E^2 r0^2 - 1 evaluated to ~2^-46 (p - 1 is exact: p is near 1)
+    const float r0 = rsqrtf(sh);
+    const float q = __fmul_rn(r0, r0), qe = __fmaf_rn(r0, r0, -q);
+    const float p = __fmul_rn(sh, q), pe = __fmaf_rn(sh, q, -p);
+    const float t = __fadd_rn(__fadd_rn(p, -1.0f), __fmaf_rn(sh, qe, __fmaf_rn(se, q, pe)));
+    const float rc = __fmul_rn(__fmul_rn(-0.5f, r0), t);
+    // w = (wr + wre) + i (wi + wie) = s P / E
+    const float wr = __fmul_rn(xh, r0);
+    const float wre = __fmaf_rn(xh, rc, __fmaf_rn(xl, r0, __fmaf_rn(xh, r0, -wr)));
+    const float wi = __fmul_rn(yh, r0);
+    const float wie = __fmaf_rn(yh, rc, __fmaf_rn(yl, r0, __fmaf_rn(yh, r0, -wi)));
+    // cr: the three large terms ar, wr br, wi bi exactly (split products, TwoSum),
+    // then the small ones (lo parts, product errors, cross terms) in FP32
+    float crh, crl;
+    {
+        const float p1 = __fmul_rn(wr, brh), e1 = __fmaf_rn(wr, brh, -p1);
+        const float p2 = __fmul_rn(wi, bih), e2 = __fmaf_rn(wi, bih, -p2);
+        float t1, te, ce;
+        two_sum(p1, p2, t1, te);
+        two_sum(arh, t1, crh, ce);
+        float l = __fadd_rn(__fadd_rn(ce, te), __fadd_rn(arl, __fadd_rn(e1, e2)));
+        l = __fmaf_rn(wre, brh, __fmaf_rn(wr, brl, l));
+        crl = __fmaf_rn(wie, bih, __fmaf_rn(wi, bil, l));
+    }
+    float cih, cil;
+    {
+        const float p3 = __fmul_rn(wr, bih), e3 = __fmaf_rn(wr, bih, -p3);
+        const float p4 = __fmul_rn(-wi, brh), e4 = __fmaf_rn(-wi, brh, -p4);
+        float t2, te, ce;
+        two_sum(p3, p4, t2, te);
+        two_sum(aih, t2, cih, ce);
+        float l = __fadd_rn(__fadd_rn(ce, te), __fadd_rn(ail, __fadd_rn(e3, e4)));
+        l = __fmaf_rn(wre, bih, __fmaf_rn(wr, bil, l));
+        cil = __fmaf_rn(-wie, brh, __fmaf_rn(-wi, brl, l));
+    }
+    // |c|^2 = cr^2 + ci^2 after renormalising each pair (cancellation can leave
+    // the lo part as large as the hi part)
+    float ch, cl, dh, dl;
+    two_sum(crh, crl, ch, cl);
+    two_sum(cih, cil, dh, dl);
+    const float c2 = __fmul_rn(ch, ch);
+    const float c2e = __fmaf_rn(__fadd_rn(ch, ch), cl, __fmaf_rn(ch, ch, -c2));
+    const float d2 = __fmul_rn(dh, dh);
+    const float d2e = __fmaf_rn(__fadd_rn(dh, dh), dl, __fmaf_rn(dh, dh, -d2));
+    float nh, ne;
+    two_sum(c2, d2, nh, ne);
+    ne = __fadd_rn(ne, __fadd_rn(c2e, d2e));
+    oh = __fmul_rn(0.5f, nh);  // exact scalings
+    ol = __fmul_rn(0.5f, ne);
+    return true;
+}
+
+// |c+|^2 in FP32 (FP32_MIXED, whose map is a float): from the hi parts of the
+// node and of the spinor, 1/|P| from rsqrtf and one Newton step.  The error is
+// below ~4e-7 |c+| (the FP32 rounding of the products around the cancellation in
+// a + conj(w) b), about the size of the float map's own rounding.  Returns false
+// when |P_out|^2 < 1e-30.
+__device__ __forceinline__ bool project_f32(float x, float y, float ar, float ai, float br,
+                                            float bi, float &out)
+{
+    const float e2 = __fmaf_rn(x, x, __fmul_rn(y, y));
+    if (!(e2 >= 1e-30f))
+        return false;
+    float r = rsqrtf(e2);
+    r = __fmaf_rn(__fmul_rn(0.5f, r), __fmaf_rn(-e2, __fmul_rn(r, r), 1.0f), r);  // Newton
+    const float wr = __fmul_rn(x, r), wi = __fmul_rn(y, r);
+    const float cr = __fmaf_rn(wr, br, __fmaf_rn(wi, bi, ar));
+    const float ci = __fmaf_rn(wr, bi, __fmaf_rn(-wi, br, ai));
+    out = __fmul_rn(0.5f, __fmaf_rn(cr, cr, __fmul_rn(ci, ci)));
+    return true;
+}
+
+// |c+|^2 of the point in column col and row row of the grid (global row row0 +
+// row) as a double-float pair: FP32_MIXED (PREC 1) in FP32 (project_f32), FP64
+// (PREC 0) in double-float (project_df); FP64 for the points whose |P_out| is too
+// small for either (their doubles are formed only there).
+struct SpinorDF {
+    float arh, arl, aih, ail, brh, brl, bih, bil;
+};
+
+template <int PREC>
+__device__ __forceinline__ float2 project_node(const ReqDesc &R, int64_t col, int64_t row,
+                                               const SpinorDF &v)
+{
+    const float2 cx = R.nodes_out[col], cy = R.nodes_out[R.nx + row];
+    if constexpr (PREC == 1) {
+        float o;
+        if (project_f32(cx.x, cy.x, v.arh, v.aih, v.brh, v.bih, o))
+            return make_float2(o, 0.0f);
+    } else {
+        float oh, ol;
+        if (project_df(cx.x, cx.y, cy.x, cy.y, v.arh, v.arl, v.aih, v.ail, v.brh, v.brl, v.bih,
+                       v.bil, oh, ol))
+            return make_float2(oh, ol);
+    }
+    const double vs = R.valley > 0 ? 1.0 : -1.0;
+    const double px = grid_node(R.px_min, R.hx, col);
+    const double py = grid_node(R.py_min, R.hy, R.row0 + row);
+    const double c2 = project_point(px + R.a_out[0], py + R.a_out[1], vs,
+                                    f32_to_f64(v.arh) + f32_to_f64(v.arl),
+                                    f32_to_f64(v.aih) + f32_to_f64(v.ail),
+                                    f32_to_f64(v.brh) + f32_to_f64(v.brl),
+                                    f32_to_f64(v.bih) + f32_to_f64(v.bil));
+    float h, l;
+    split_f64(c2, h, l);
+    return make_float2(h, l);
+}
+
+// The map value of a point and its term in the density sum, from |c+|^2 = c.x +
+// c.y: FP32_MIXED stores the float nearest the pair and sums the pair itself;
+// FP64 stores the double and sums that double (split into a pair), so that the
+// density is the sum of the FP64 map's values.
+template <int PREC>
+__device__ __forceinline__ float2 store_point(void *map, int64_t idx, float2 c)
+{
+    if constexpr (PREC == 1) {
+        if (map)
+            static_cast<float *>(map)[idx] = __fadd_rn(c.x, c.y);
+        return c;
+    } else {
+        const double d = df_to_f64(c.x, c.y);
+        if (map)
+            static_cast<double *>(map)[idx] = d;
+        float h, l;
+        split_f64(d, h, l);
+        return make_float2(h, l);
+    }
+}
+
+// Locates the request tile b (by default the CTA's own) belongs to (requests are
+// sorted by tile_begin).
+__device__ __forceinline__ int find_request(const EvolveArgs &a,
+                                            int b = static_cast<int>(blockIdx.x))
+{
+    int lo = 0, hi = a.nreq - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.r[mid].tile_begin <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Table staging: chunk c of the launch goes to stage c & 1 of shared memory.
+// ---------------------------------------------------------------------------
+
+constexpr int kStageBytes = 16384;  // per stage; two stages per CTA
+
+// Tuning constants: unroll factors of the step-pair loop and of the chain inside
+// a step group (measured fastest fully unrolled, although ptxas then keeps a few
+// values in local memory), and spinors per thread of the FP32-mixed kernel (a CTA
+// always owns one 1024-point tile).
+#ifndef DSP_PAIR_UNROLL
+#define DSP_PAIR_UNROLL 2
+#endif
+#ifndef DSP_MIXED_SPT
+#define DSP_MIXED_SPT 4
+#endif
+#ifndef DSP_MIXED_MINB
+#define DSP_MIXED_MINB 2
+#endif
+#ifndef DSP_PACKED_PAIRS
+#define DSP_PACKED_PAIRS 1
+#endif
+#ifndef DSP_GROUP_UNROLL
+#define DSP_GROUP_UNROLL 8
+#endif
+constexpr int kPairUnroll = DSP_PAIR_UNROLL;
+constexpr int kGroupUnroll = DSP_GROUP_UNROLL;  // chain loop inside one group (>= G - 2: whole)
+#ifndef DSP_MAGNUS_GROUP_UNROLL
+#define DSP_MAGNUS_GROUP_UNROLL 1
+#endif
+constexpr int kMagnusGroupUnroll = DSP_MAGNUS_GROUP_UNROLL;  // the MAGNUS4 chain's
+// Series levels that can run in step groups.  G >= 2 needs theta_max <= 0.1, where a
+// level above degree kGroupMaxDegree is chosen only for runs of more than ~3e8 steps;
+// the host keeps G = 1 at those levels (choose_group), and no group code is compiled
+// for them.
+template <int DC, int DS>
+constexpr bool kGroupedLevel = DC <= kGroupMaxDegree && DS <= kGroupMaxDegree;
+constexpr int kMixedSpt = DSP_MIXED_SPT;
+constexpr int kMixedThreads = kTilePoints / kMixedSpt;
+constexpr int kMixedMinBlocks = DSP_MIXED_MINB;  // resident CTAs per SM the registers allow
+constexpr bool kPackedPairs = DSP_PACKED_PAIRS != 0;  // FP32x2 form of the paired path
+constexpr int kF64Threads = kThreads;
+static_assert(kTilePoints % kMixedSpt == 0, "a CTA owns one whole tile");
+
+// MAGNUS4 table entries: the Gauss-point mean (dt*Abar, valley-signed) and the
+// commutator factor D = -(sqrt(3)/6) dt (A2 - A1) (valley-signed).  FP32_MIXED:
+// one float4 (Abar_x, Abar_y, D_x, D_y).
+struct F64G2 {
+    double2 a;  // Abar
+    double2 d;  // D
+};
+
+// Bounds-check builds (-DDSP_BOUNDS_CHECK) verify, uniformly per CTA, that the
+// table entries a launch stages, [first, step_end), lie inside the table (the
+// copy's rounding up to 16 bytes stays in the allocation's padding); a bad range
+// sets kErrBounds and the launch does nothing.  Otherwise a no-op.
+__device__ __forceinline__ bool table_range_ok(const ReqDesc &R, int64_t first, int *err)
+{
+#ifdef DSP_BOUNDS_CHECK
+    const bool ok = first >= 0 && R.step_end >= R.step_begin &&
+                    (R.step_end == R.step_begin || R.step_end <= R.table_steps);
+    if (!ok && threadIdx.x == 0)
+        atomicOr(err, kErrBounds);
+    return ok;
+#else
+    (void)R;
+    (void)first;
+    (void)err;
+    return true;
+#endif
+}
+
+// Bounds-check builds verify a CTA's tile index; a bad one sets kErrBounds.
+__device__ __forceinline__ bool tile_ok(const ReqDesc &R, int tile, int *err)
+{
+#ifdef DSP_BOUNDS_CHECK
+    const bool ok = tile >= 0 && tile < R.n_tiles;
+    if (!ok && threadIdx.x == 0)
+        atomicOr(err, kErrBounds);
+    return ok;
+#else
+    (void)R;
+    (void)tile;
+    (void)err;
+    return true;
+#endif
+}
+
+// Stages table entries [base, base + nsteps) in chunks of kCh.  A 1-D bulk copy
+// must start and end on 16-byte boundaries: base is a multiple of kAlign entries
+// (16 bytes), every chunk is a multiple of kAlign, and the last copy is rounded
+// up to whole 16 bytes, which stays inside the table's allocation (the library
+// pads it to a multiple of 16 bytes).
+template <typename E, int kBytes = kStageBytes>
+struct Stager {
+    unsigned char *smem;
+    uint64_t *bars;
+    const E *table;  // entry base is element 0 of chunk 0
+    int64_t nsteps;
+    int nchunks;
+    int withhold_first = 0;  // test hook (ReqDesc::withhold_first_copy)
+    static constexpr int kCh = kBytes / static_cast<int>(sizeof(E));
+    static constexpr int kAlign = sizeof(E) >= 16 ? 1 : static_cast<int>(16 / sizeof(E));
+    static_assert(16 % sizeof(E) == 0 || sizeof(E) % 16 == 0, "entries tile 16 bytes");
+    static_assert(kCh % kAlign == 0, "chunks start on 16-byte boundaries");
+
+    __device__ __forceinline__ const E *stage(int c) const
+    {
+        return reinterpret_cast<const E *>(smem + (c & 1) * kBytes);
+    }
+    __device__ __forceinline__ int chunk_len(int c) const
+    {
+        const int64_t rem = nsteps - static_cast<int64_t>(c) * kCh;
+        return rem < kCh ? static_cast<int>(rem) : kCh;
+    }
+    __device__ __forceinline__ void issue(int c) const  // one thread
+    {
+        const uint32_t bytes = (static_cast<uint32_t>(chunk_len(c)) * sizeof(E) + 15u) & ~15u;
+        mbar_arrive_expect_tx(&bars[c & 1], bytes);
+        if (c == 0 && withhold_first)
+            return;  // the phase cannot complete: its waiters time out
+        bulk_load(smem + (c & 1) * kBytes, table + static_cast<int64_t>(c) * kCh, bytes,
+                  &bars[c & 1]);
+    }
+    // After the wait for chunk c timed out (one thread): flags the error and gives
+    // the copy of chunk c + 1, if it was issued, a bounded chance to land first.
+    __device__ __forceinline__ void on_timeout(int c, int *err) const
+    {
+        atomicOr(err, kErrTimeout);
+        if (c + 1 < nchunks)
+            (void)mbar_wait_bounded(&bars[(c + 1) & 1], ((c + 1) >> 1) & 1);
+    }
+};
+
+// Runs the launch's steps with the table streamed through shared memory; STEP
+// is called as step(entry) for every step in order.  Returns false (and flags
+// err) if a staging wait timed out.
+template <typename E, typename StepFn>
+__device__ __forceinline__ bool run_steps(const ReqDesc &R, unsigned char *smem, uint64_t *bars,
+                                          int *err, StepFn step)
+{
+    const int64_t b_al = R.step_begin & ~static_cast<int64_t>(Stager<E>::kAlign - 1);
+    if (!table_range_ok(R, b_al, err))
+        return false;
+    Stager<E> st{smem, bars, static_cast<const E *>(R.table) + b_al, R.step_end - b_al, 0};
+    st.withhold_first = R.withhold_first_copy;
+    if (R.step_end <= R.step_begin)
+        st.nsteps = 0;
+    st.nchunks = static_cast<int>((st.nsteps + Stager<E>::kCh - 1) / Stager<E>::kCh);
+    if (threadIdx.x == 0) {
+        if (st.nchunks > 0) st.issue(0);
+        if (st.nchunks > 1) st.issue(1);
+    }
+    for (int c = 0; c < st.nchunks; ++c) {
+        const bool ok = mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0)
+                st.on_timeout(c, err);
+            return false;
+        }
+        const E *tb = st.stage(c);
+        const int len = st.chunk_len(c);
+        // entries before step_begin - b_al belong to earlier launches
+#pragma unroll 2
+        for (int j = c == 0 ? static_cast<int>(R.step_begin - b_al) : 0; j < len; ++j)
+            step(tb[j]);  // shared-memory broadcast
+        __syncthreads();  // everyone is done with stage c & 1
+        if (threadIdx.x == 0 && c + 2 < st.nchunks)
+            st.issue(c + 2);
+    }
+    return true;
+}
+
+// As run_steps, but steps are taken in groups (G j, ..., G j + G - 1) of ABSOLUTE
+// step index (a launch that starts or ends inside a group takes those steps one
+// by one), so any split of a run at multiples of G meets the same groups.  The
+// stages hold whole groups: staging starts at the multiple of G at or below
+// step_begin and the stage length is a multiple of G.  GROUP is called as
+// group(e) with e the group's G consecutive entries in shared memory.
+template <typename E, int G, typename SingleFn, typename GroupFn>
+__device__ __forceinline__ bool run_step_groups(const ReqDesc &R, unsigned char *smem,
+                                                uint64_t *bars, int *err, SingleFn single,
+                                                GroupFn group)
+{
+    static_assert(G >= 2 && (G & (G - 1)) == 0, "group size: a power of two");
+    static_assert(Stager<E>::kCh % G == 0, "stages must hold whole groups");
+    static_assert(G % Stager<E>::kAlign == 0, "groups start on 16-byte boundaries");
+    const int64_t b_al = R.step_begin & ~static_cast<int64_t>(G - 1);
+    if (!table_range_ok(R, b_al, err))
+        return false;
+    Stager<E> st{smem, bars, static_cast<const E *>(R.table) + b_al, R.step_end - b_al, 0};
+    st.withhold_first = R.withhold_first_copy;
+    if (R.step_end <= R.step_begin)
+        st.nsteps = 0;
+    st.nchunks = static_cast<int>((st.nsteps + Stager<E>::kCh - 1) / Stager<E>::kCh);
+    if (threadIdx.x == 0) {
+        if (st.nchunks > 0) st.issue(0);
+        if (st.nchunks > 1) st.issue(1);
+    }
+    for (int c = 0; c < st.nchunks; ++c) {
+        const bool ok = mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0)
+                st.on_timeout(c, err);
+            return false;
+        }
+        const E *tb = st.stage(c);
+        const int len = st.chunk_len(c);
+        // entries before step_begin - b_al belong to earlier launches
+        int j = c == 0 ? static_cast<int>(R.step_begin - b_al) : 0;
+        for (; j < len && (j & (G - 1)) != 0; ++j)  // ragged start
+            single(tb[j]);
+        if constexpr (G == 2) {
+#pragma unroll kPairUnroll
+            for (; j + G <= len; j += G)
+                group(tb + j);
+        } else {
+#pragma unroll 1
+            for (; j + G <= len; j += G)
+                group(tb + j);
+        }
+        for (; j < len; ++j)  // ragged end (last stage only)
+            single(tb[j]);
+        __syncthreads();  // everyone is done with stage c & 1
+        if (threadIdx.x == 0 && c + 2 < st.nchunks)
+            st.issue(c + 2);
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// FP32_MIXED step
+// ---------------------------------------------------------------------------
+
+struct MixedPoint {
+    float ar, ai, br, bi;      // hi parts of psi = (a, b)
+    float lar, lai, lbr, lbi;  // lo parts
+    float pxh, pxl, pyh, pyl;  // dt * p as hi + lo
+};
+
+// Coefficients of U - I = [[cm1 - i qz, -q], [conj(q), cm1 + i qz]], q = qr + i qi,
+// for the step with kinematic momentum dt*P = (Px, Py).  EXACT and STRANG_XY have
+// qz = 0.
+template <int SCHEME, int DC, int DS>
+__device__ __forceinline__ void step_coeffs_f32(float Px, float Py, float2 d, float &cm1,
+                                                float &qr, float &qi, float &qz)
+{
+    if constexpr (SCHEME == 0) {
+        const float x = fmaf(Px, Px, Py * Py);  // theta^2
+        cm1 = cosm1_f32<DC>(x);
+        const float sn = sinc_f32<DS>(x);
+        qr = sn * Py;
+        qi = sn * Px;
+        qz = 0.0f;
+    } else if constexpr (SCHEME == 1) {
+        // e^{-i a sx} e^{-i b sy} e^{-i a sx}, a = dt Px / 2, b = dt Py:
+        //   = [[cos b cos 2a, -(sin b + i cos b sin 2a)], [sin b - i cos b sin 2a, cos b cos 2a]]
+        const float xx = Px * Px, xy = Py * Py;
+        const float cmx = cosm1_f32<DC>(xx), cmy = cosm1_f32<DC>(xy);
+        const float sx = Px * sinc_f32<DS>(xx);
+        cm1 = fmaf(cmx, cmy, cmx) + cmy;
+        qr = Py * sinc_f32<DS>(xy);
+        qi = fmaf(cmy, sx, sx);
+        qz = 0.0f;
+    } else {
+        // MAGNUS4: exp(-i n.sigma), n = (dt Pbar, n_z), n_z = -(sqrt 3/6) (dt P1 x dt P2)_z
+        // = (dt Pbar x D')_z with D' = -(sqrt 3/6) dt (A2 - A1) from the table (the
+        // cross product of the two nearly parallel momenta is never formed).
+        const float nz = fmaf(Px, d.y, -(Py * d.x));
+        const float x = fmaf(Px, Px, fmaf(Py, Py, nz * nz));
+        cm1 = cosm1_f32<DC>(x);
+        const float sn = sinc_f32<DS>(x);
+        qr = sn * Py;
+        qi = sn * Px;
+        qz = sn * nz;
+    }
+}
+
+// psi <- U psi as psi_hi + (U - I) psi_hi + psi_lo, the rounding error of the
+// hi update carried into lo (Fast2Sum).
+template <int SCHEME>
+__device__ __forceinline__ void apply_f32(MixedPoint &s, float cm1, float qr, float qi, float qz)
+{
+    float dar, dai, dbr, dbi;
+    if constexpr (SCHEME == 2) {
+        dar = fmaf(cm1, s.ar, fmaf(qz, s.ai, fmaf(-qr, s.br, fmaf(qi, s.bi, s.lar))));
+        dai = fmaf(cm1, s.ai, fmaf(-qz, s.ar, fmaf(-qr, s.bi, fmaf(-qi, s.br, s.lai))));
+        dbr = fmaf(cm1, s.br, fmaf(-qz, s.bi, fmaf(qr, s.ar, fmaf(qi, s.ai, s.lbr))));
+        dbi = fmaf(cm1, s.bi, fmaf(qz, s.br, fmaf(qr, s.ai, fmaf(-qi, s.ar, s.lbi))));
+    } else {
+        dar = fmaf(cm1, s.ar, fmaf(-qr, s.br, fmaf(qi, s.bi, s.lar)));
+        dai = fmaf(cm1, s.ai, fmaf(-qr, s.bi, fmaf(-qi, s.br, s.lai)));
+        dbr = fmaf(cm1, s.br, fmaf(qr, s.ar, fmaf(qi, s.ai, s.lbr)));
+        dbi = fmaf(cm1, s.bi, fmaf(qr, s.ai, fmaf(-qi, s.ar, s.lbi)));
+    }
+    float t;
+    t = s.ar + dar; s.lar = dar - (t - s.ar); s.ar = t;
+    t = s.ai + dai; s.lai = dai - (t - s.ai); s.ai = t;
+    t = s.br + dbr; s.lbr = dbr - (t - s.br); s.br = t;
+    t = s.bi + dbi; s.lbi = dbi - (t - s.bi); s.bi = t;
+}
+
+// dt*P = dt p_hi + (dt A + dt p_lo), rounded in that order.
+[[maybe_unused]] __device__ __forceinline__ float momentum_f32(float ph, float a, float pl)
+{
+    return __fadd_rn(ph, __fadd_rn(a, pl));
+}
+
+template <int SCHEME, int DC, int DS>
+__device__ __forceinline__ void step_mixed(MixedPoint &p, const float2 &a, float2 d)
+{
+    float cm1, qr, qi, qz;
+    step_coeffs_f32<SCHEME, DC, DS>(momentum_f32(p.pxh, a.x, p.pxl),
+                                    momentum_f32(p.pyh, a.y, p.pyl), d, cm1, qr, qi, qz);
+    apply_f32<SCHEME>(p, cm1, qr, qi, qz);
+}
+
+// Two EXACT steps at once: with U_k = I + [[m_k, -q_k], [conj(q_k), m_k]],
+//   U_2 U_1 - I = [[al - 1, -Q], [conj(Q), conj(al) - 1]],
+//   al - 1 = m1 + m2 + m1 m2 - q2 conj(q1),  Q = q1 + q2 + m2 q1 + m1 q2,
+// applied with one compensated update (the product of two SU(2) steps is SU(2)).
+template <int DC, int DS>
+__device__ __forceinline__ void step_pair_mixed(MixedPoint &p, const float2 &a0, const float2 &a1)
+{
+    float m1, q1r, q1i, m2, q2r, q2i, z;
+    step_coeffs_f32<0, DC, DS>(momentum_f32(p.pxh, a0.x, p.pxl), momentum_f32(p.pyh, a0.y, p.pyl),
+                               make_float2(0.0f, 0.0f), m1, q1r, q1i, z);
+    step_coeffs_f32<0, DC, DS>(momentum_f32(p.pxh, a1.x, p.pxl), momentum_f32(p.pyh, a1.y, p.pyl),
+                               make_float2(0.0f, 0.0f), m2, q2r, q2i, z);
+    const float alm1 = fmaf(m1, m2, m1 + m2) - fmaf(q2r, q1r, q2i * q1i);
+    const float ali = fmaf(q2r, q1i, -(q2i * q1r));
+    const float Qr = fmaf(m2, q1r, q1r) + fmaf(m1, q2r, q2r);
+    const float Qi = fmaf(m2, q1i, q1i) + fmaf(m1, q2i, q2i);
+    const float dar = fmaf(alm1, p.ar, fmaf(-ali, p.ai, fmaf(-Qr, p.br, fmaf(Qi, p.bi, p.lar))));
+    const float dai = fmaf(alm1, p.ai, fmaf(ali, p.ar, fmaf(-Qr, p.bi, fmaf(-Qi, p.br, p.lai))));
+    const float dbr = fmaf(alm1, p.br, fmaf(ali, p.bi, fmaf(Qr, p.ar, fmaf(Qi, p.ai, p.lbr))));
+    const float dbi = fmaf(alm1, p.bi, fmaf(-ali, p.br, fmaf(Qr, p.ai, fmaf(-Qi, p.ar, p.lbi))));
+    float t;
+    t = p.ar + dar; p.lar = dar - (t - p.ar); p.ar = t;
+    t = p.ai + dai; p.lai = dai - (t - p.ai); p.ai = t;
+    t = p.br + dbr; p.lbr = dbr - (t - p.br); p.br = t;
+    t = p.bi + dbi; p.lbi = dbi - (t - p.bi); p.bi = t;
+}
+
+// ---------------------------------------------------------------------------
+// Packed FP32x2 form of the paired EXACT path: lane 0 and lane 1 of every
+// float2 belong to two different momenta, and every operation is the scalar
+// path's operation, in the same order, so each lane's result is bitwise the
+// scalar result (the packed instructions round each lane like the scalar ones).
+// One instruction then issues the arithmetic of two spinors.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <int D, int K, int ODD>
+__device__ __forceinline__ float2 horner2(float2 x)
+{
+    constexpr float c = static_cast<float>(((K & 1) ? -1.0 : 1.0) * inv_factorial<2 * K + ODD>());
+    if constexpr (K == D)
+        return bc2(c);
+    else
+        return fma2(horner2<D, K + 1, ODD>(x), x, bc2(c));
+}
+
+struct MixedPack {
+    float2 ar, ai, br, bi, lar, lai, lbr, lbi, pxh, pxl, pyh, pyl;
+};
+
+__device__ __forceinline__ MixedPack pack_points(const MixedPoint &u, const MixedPoint &v)
+{
+    MixedPack p;
+    p.ar = make_float2(u.ar, v.ar); p.ai = make_float2(u.ai, v.ai);
+    p.br = make_float2(u.br, v.br); p.bi = make_float2(u.bi, v.bi);
+    p.lar = make_float2(u.lar, v.lar); p.lai = make_float2(u.lai, v.lai);
+    p.lbr = make_float2(u.lbr, v.lbr); p.lbi = make_float2(u.lbi, v.lbi);
+    p.pxh = make_float2(u.pxh, v.pxh); p.pxl = make_float2(u.pxl, v.pxl);
+    p.pyh = make_float2(u.pyh, v.pyh); p.pyl = make_float2(u.pyl, v.pyl);
+    return p;
+}
+
+__device__ __forceinline__ void unpack_points(const MixedPack &p, MixedPoint &u, MixedPoint &v)
+{
+    u.ar = p.ar.x; v.ar = p.ar.y; u.ai = p.ai.x; v.ai = p.ai.y;
+    u.br = p.br.x; v.br = p.br.y; u.bi = p.bi.x; v.bi = p.bi.y;
+    u.lar = p.lar.x; v.lar = p.lar.y; u.lai = p.lai.x; v.lai = p.lai.y;
+    u.lbr = p.lbr.x; v.lbr = p.lbr.y; u.lbi = p.lbi.x; v.lbi = p.lbi.y;
+}
+
+// step_coeffs_f32<0> on two momenta at once
+template <int DC, int DS>
+__device__ __forceinline__ void coeffs_exact2(const MixedPack &p, const float2 &a, float2 &m,
+                                              float2 &qr, float2 &qi)
+{
+    const float2 Px = add2(p.pxh, add2(bc2(a.x), p.pxl));
+    const float2 Py = add2(p.pyh, add2(bc2(a.y), p.pyl));
+    const float2 x = fma2(Px, Px, mul2(Py, Py));
+    m = mul2(horner2<DC, 1, 0>(x), x);
+    const float2 sn = horner2<DS, 0, 1>(x);
+    qr = mul2(sn, Py);
+    qi = mul2(sn, Px);
+}
+
+// Compensated update psi <- psi + d, d = (M - I) psi_hi + psi_lo, for
+// M - I = [[am + i ai, -Q], [conj(Q), am - i ai]] (ai = 0 for one step).
+__device__ __forceinline__ void apply2(MixedPack &p, float2 am, float2 ai, float2 Qr, float2 Qi)
+{
+    const float2 nai = neg2(ai), nQr = neg2(Qr), nQi = neg2(Qi);
+    const float2 dar = fma2(am, p.ar, fma2(nai, p.ai, fma2(nQr, p.br, fma2(Qi, p.bi, p.lar))));
+    const float2 dai = fma2(am, p.ai, fma2(ai, p.ar, fma2(nQr, p.bi, fma2(nQi, p.br, p.lai))));
+    const float2 dbr = fma2(am, p.br, fma2(ai, p.bi, fma2(Qr, p.ar, fma2(Qi, p.ai, p.lbr))));
+    const float2 dbi = fma2(am, p.bi, fma2(nai, p.br, fma2(Qr, p.ai, fma2(nQi, p.ar, p.lbi))));
+    float2 t;
+    t = add2(p.ar, dar); p.lar = sub2(dar, sub2(t, p.ar)); p.ar = t;
+    t = add2(p.ai, dai); p.lai = sub2(dai, sub2(t, p.ai)); p.ai = t;
+    t = add2(p.br, dbr); p.lbr = sub2(dbr, sub2(t, p.br)); p.br = t;
+    t = add2(p.bi, dbi); p.lbi = sub2(dbi, sub2(t, p.bi)); p.bi = t;
+}
+
+// psi <- U psi for one EXACT step, U - I = [[m, -q], [conj(q), m]] (apply_f32<0>).
+__device__ __forceinline__ void apply_exact2(MixedPack &p, float2 m, float2 qr, float2 qi)
+{
+    const float2 nqr = neg2(qr), nqi = neg2(qi);
+    const float2 dar = fma2(m, p.ar, fma2(nqr, p.br, fma2(qi, p.bi, p.lar)));
+    const float2 dai = fma2(m, p.ai, fma2(nqr, p.bi, fma2(nqi, p.br, p.lai)));
+    const float2 dbr = fma2(m, p.br, fma2(qr, p.ar, fma2(qi, p.ai, p.lbr)));
+    const float2 dbi = fma2(m, p.bi, fma2(qr, p.ai, fma2(nqi, p.ar, p.lbi)));
+    float2 t;
+    t = add2(p.ar, dar); p.lar = sub2(dar, sub2(t, p.ar)); p.ar = t;
+    t = add2(p.ai, dai); p.lai = sub2(dai, sub2(t, p.ai)); p.ai = t;
+    t = add2(p.br, dbr); p.lbr = sub2(dbr, sub2(t, p.br)); p.br = t;
+    t = add2(p.bi, dbi); p.lbi = sub2(dbi, sub2(t, p.bi)); p.bi = t;
+}
+
+// One EXACT step (apply_f32<0> with cm1 = m, q = (qr, qi)).
+template <int DC, int DS>
+__device__ __forceinline__ void step_exact2(MixedPack &p, const float2 &a)
+{
+    float2 m, qr, qi;
+    coeffs_exact2<DC, DS>(p, a, m, qr, qi);
+    apply_exact2(p, m, qr, qi);
+}
+
+// One MAGNUS4 step (step_coeffs_f32<2> + apply_f32<2> on two momenta):
+// U - I = [[m - i qz, -q], [conj(q), m + i qz]].
+template <int DC, int DS>
+__device__ __forceinline__ void step_magnus2(MixedPack &p, const float4 &e)
+{
+    const float2 Px = add2(p.pxh, add2(bc2(e.x), p.pxl));
+    const float2 Py = add2(p.pyh, add2(bc2(e.y), p.pyl));
+    const float2 nz = fma2(Px, bc2(e.w), neg2(mul2(Py, bc2(e.z))));
+    const float2 x = fma2(Px, Px, fma2(Py, Py, mul2(nz, nz)));
+    const float2 m = mul2(horner2<DC, 1, 0>(x), x);
+    const float2 sn = horner2<DS, 0, 1>(x);
+    apply2(p, m, neg2(mul2(sn, nz)), mul2(sn, Py), mul2(sn, Px));
+}
+
+// The product of two EXACT steps, then one update (step_pair_mixed on two momenta).
+__device__ __forceinline__ void pair_apply2(MixedPack &p, float2 m1, float2 q1r, float2 q1i,
+                                            float2 m2, float2 q2r, float2 q2i)
+{
+    const float2 alm1 = sub2(fma2(m1, m2, add2(m1, m2)), fma2(q2r, q1r, mul2(q2i, q1i)));
+    const float2 ali = fma2(q2r, q1i, neg2(mul2(q2i, q1r)));
+    const float2 Qr = add2(fma2(m2, q1r, q1r), fma2(m1, q2r, q2r));
+    const float2 Qi = add2(fma2(m2, q1i, q1i), fma2(m1, q2i, q2i));
+    apply2(p, alm1, ali, Qr, Qi);
+}
+
+template <int DC, int DS>
+__device__ __forceinline__ void step_pair2(MixedPack &p, const float2 &a0, const float2 &a1)
+{
+    float2 m1, q1r, q1i, m2, q2r, q2i;
+    coeffs_exact2<DC, DS>(p, a0, m1, q1r, q1i);
+    coeffs_exact2<DC, DS>(p, a1, m2, q2r, q2i);
+    pair_apply2(p, m1, q1r, q1i, m2, q2r, q2i);
+}
+
+// ---------------------------------------------------------------------------
+// Groups of G EXACT steps (G = 4, 8), written once for one momentum (V = float,
+// MixedPoint) and for two (V = float2, MixedPack) with non-contracting
+// intrinsics, so both forms perform the same roundings.
+//
+// The product U_k ... U_1 = [[alpha, -Q], [conj(Q), conj(alpha)]] is carried as
+// (Re alpha, Im alpha, Q).  With U_k = [[1 + m, -q], [conj(q), 1 + m]],
+// m = cos(theta_k) - 1, q = sin(theta_k)/theta_k (dt P_y + i dt P_x):
+//   alpha' = alpha + m alpha - q conj(Q),   Q' = Q + m Q + q conj(alpha).
+// No coefficient of the form 1 + (small) is ever rounded: cos(theta) enters as
+// X + m X and sin(theta)/theta as P + (sinc - 1) P, both accurate to the
+// rounding of the small part.  (Rounding cos(theta) itself to FP32 next to 1
+// errs by up to 3e-8 absolute, the same for every step while theta barely
+// changes, and the step angle then carries a relative bias of that size, which
+// grows along the whole evolution.)  Re alpha is held near 1, where FP32
+// resolves it only to ~6e-8; Re alpha - 1 is rebuilt at the end of the group
+// from the other three entries and unitarity, (1 + am)^2 + ai^2 + |Q|^2 = 1, by
+// one Newton step, so the operator applied is unitary to the rounding of its
+// entries.
+// ---------------------------------------------------------------------------
+
+// Either set of forms can go unused, depending on the build (the float forms serve
+// builds without the packed path: DSP_PACKED_PAIRS=0 or an odd DSP_MIXED_SPT).
+[[maybe_unused]] __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+[[maybe_unused]] __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+[[maybe_unused]] __device__ __forceinline__ float vfma(float a, float b, float c)
+{
+    return __fmaf_rn(a, b, c);
+}
+[[maybe_unused]] __device__ __forceinline__ float vneg(float a) { return -a; }
+[[maybe_unused]] __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return add2(a, b); }
+[[maybe_unused]] __device__ __forceinline__ float2 vmul(float2 a, float2 b) { return mul2(a, b); }
+[[maybe_unused]] __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c)
+{
+    return fma2(a, b, c);
+}
+[[maybe_unused]] __device__ __forceinline__ float2 vneg(float2 a) { return neg2(a); }
+template <typename V>
+__device__ __forceinline__ V vbc(float v);
+template <>
+[[maybe_unused]] __device__ __forceinline__ float vbc<float>(float v) { return v; }
+template <>
+[[maybe_unused]] __device__ __forceinline__ float2 vbc<float2>(float v) { return bc2(v); }
+
+template <typename V, int D, int K, int ODD>
+__device__ __forceinline__ V vhorner(V x)
+{
+    constexpr float c = static_cast<float>(((K & 1) ? -1.0 : 1.0) * inv_factorial<2 * K + ODD>());
+    if constexpr (K == D)
+        return vbc<V>(c);
+    else
+        return vfma(vhorner<V, D, K + 1, ODD>(x), x, vbc<V>(c));
+}
+
+// m = cos(theta) - 1 and q = (qr, qi) of one EXACT step at dt P = dt p + table
+// entry a, with q = P + (sinc - 1) P.
+template <int DC, int DS, typename Pt, typename V>
+__device__ __forceinline__ void coeffs_group(const Pt &p, const float2 &a, V &m, V &qr, V &qi)
+{
+    const V Px = vadd(p.pxh, vadd(vbc<V>(a.x), p.pxl));
+    const V Py = vadd(p.pyh, vadd(vbc<V>(a.y), p.pyl));
+    const V x = vfma(Px, Px, vmul(Py, Py));
+    m = vmul(vhorner<V, DC, 1, 0>(x), x);
+    const V s1 = vmul(vhorner<V, DS, 1, 1>(x), x);  // sin(theta)/theta - 1
+    qr = vfma(s1, Py, Py);
+    qi = vfma(s1, Px, Px);
+}
+
+// Compensated update psi <- psi + d, d = (M - I) psi_hi + psi_lo, for
+// M - I = [[am + i ai, -Q], [conj(Q), am - i ai]]: the operations of apply2.
+template <typename Pt, typename V>
+__device__ __forceinline__ void apply_group(Pt &p, V am, V ai, V Qr, V Qi)
+{
+    const V nai = vneg(ai), nQr = vneg(Qr), nQi = vneg(Qi);
+    const V dar = vfma(am, p.ar, vfma(nai, p.ai, vfma(nQr, p.br, vfma(Qi, p.bi, p.lar))));
+    const V dai = vfma(am, p.ai, vfma(ai, p.ar, vfma(nQr, p.bi, vfma(nQi, p.br, p.lai))));
+    const V dbr = vfma(am, p.br, vfma(ai, p.bi, vfma(Qr, p.ar, vfma(Qi, p.ai, p.lbr))));
+    const V dbi = vfma(am, p.bi, vfma(nai, p.br, vfma(Qr, p.ai, vfma(nQi, p.ar, p.lbi))));
+    V t;
+    t = vadd(p.ar, dar); p.lar = vadd(dar, vneg(vadd(t, vneg(p.ar)))); p.ar = t;
+    t = vadd(p.ai, dai); p.lai = vadd(dai, vneg(vadd(t, vneg(p.ai)))); p.ai = t;
+    t = vadd(p.br, dbr); p.lbr = vadd(dbr, vneg(vadd(t, vneg(p.br)))); p.br = t;
+    t = vadd(p.bi, dbi); p.lbi = vadd(dbi, vneg(vadd(t, vneg(p.bi)))); p.bi = t;
+}
+
+// STRANG_XY's merged step X(a) Y(b) X(a), 2a = dt Px, b = dt Py, as m = cos b
+// cos 2a - 1 and q = sin b + i cos b sin 2a, from small parts only:
+// m = cx + cy + cx cy (cx = cos 2a - 1, cy = cos b - 1), sin 2a = Px + (sinc - 1) Px,
+// sin b likewise, cos b sin 2a = sin 2a + cy sin 2a.
+template <int DC, int DS, typename Pt, typename V>
+__device__ __forceinline__ void coeffs_strang_group(const Pt &p, const float2 &a, V &m, V &qr,
+                                                    V &qi)
+{
+    const V Px = vadd(p.pxh, vadd(vbc<V>(a.x), p.pxl));
+    const V Py = vadd(p.pyh, vadd(vbc<V>(a.y), p.pyl));
+    const V xx = vmul(Px, Px), xy = vmul(Py, Py);
+    const V cx = vmul(vhorner<V, DC, 1, 0>(xx), xx), cy = vmul(vhorner<V, DC, 1, 0>(xy), xy);
+    const V sx = vfma(vmul(vhorner<V, DS, 1, 1>(xx), xx), Px, Px);
+    qr = vfma(vmul(vhorner<V, DS, 1, 1>(xy), xy), Py, Py);
+    qi = vfma(cy, sx, sx);
+    m = vfma(cx, cy, vadd(cx, cy));
+}
+
+// (m, q) of one step of an EXACT-structured scheme: 0 = EXACT, 1 = STRANG_XY.
+template <int SCHEME, int DC, int DS, typename Pt, typename V>
+__device__ __forceinline__ void coeffs_scheme(const Pt &p, const float2 &a, V &m, V &qr, V &qi)
+{
+    if constexpr (SCHEME == 1)
+        coeffs_strang_group<DC, DS>(p, a, m, qr, qi);
+    else
+        coeffs_group<DC, DS>(p, a, m, qr, qi);
+}
+
+// One step alone through the group update (ragged ends of a grouped STRANG_XY
+// run, or all of an ungrouped one): U - I = [[m, -q], [conj(q), m]].
+template <int SCHEME, int DC, int DS, typename Pt>
+__device__ __forceinline__ void step_single_scheme(Pt &p, const float2 &a)
+{
+    using V = decltype(p.ar);
+    V m, qr, qi;
+    coeffs_scheme<SCHEME, DC, DS>(p, a, m, qr, qi);
+    apply_group(p, m, vbc<V>(0.0f), qr, qi);
+}
+
+// The chain, one step k >= 2 at a time (the second step, with Im alpha still 0,
+// drops its terms):
+//   Re alpha' = Re alpha + m Re alpha - (qr Qr + qi Qi)
+//   Im alpha' = Im alpha + m Im alpha - (qi Qr - qr Qi)
+//   Qr'       = Qr + m Qr + qr Re alpha + qi Im alpha
+//   Qi'       = Qi + m Qi + qi Re alpha - qr Im alpha
+// then Re alpha - 1 rebuilt from unitarity and one compensated update.  Every
+// EXACT-structured group (either tiling) goes through these operations.
+template <typename V>
+struct Chain {
+    V Ar, ai, Qr, Qi;
+
+    __device__ __forceinline__ void first(V m, V qr, V qi)
+    {
+        Ar = vadd(m, vbc<V>(1.0f));
+        Qr = qr;
+        Qi = qi;
+    }
+    __device__ __forceinline__ void second(V m, V qr, V qi)
+    {
+        ai = vfma(vneg(qi), Qr, vmul(qr, Qi));
+        const V nAr = vfma(m, Ar, vfma(vneg(qr), Qr, vfma(vneg(qi), Qi, Ar)));
+        const V nQr = vfma(m, Qr, vfma(qr, Ar, Qr));
+        const V nQi = vfma(m, Qi, vfma(qi, Ar, Qi));
+        Ar = nAr;
+        Qr = nQr;
+        Qi = nQi;
+    }
+    __device__ __forceinline__ void next(V m, V qr, V qi)
+    {
+        const V nAr = vfma(m, Ar, vfma(vneg(qr), Qr, vfma(vneg(qi), Qi, Ar)));
+        const V nai = vfma(m, ai, vfma(vneg(qi), Qr, vfma(qr, Qi, ai)));
+        const V nQr = vfma(m, Qr, vfma(qr, Ar, vfma(qi, ai, Qr)));
+        const V nQi = vfma(m, Qi, vfma(qi, Ar, vfma(vneg(qr), ai, Qi)));
+        Ar = nAr;
+        ai = nai;
+        Qr = nQr;
+        Qi = nQi;
+    }
+    template <typename Pt>
+    __device__ __forceinline__ void finish(Pt &p) const
+    {
+        V am = vadd(Ar, vbc<V>(-1.0f));  // exact: Re alpha is within [1/2, 2]
+        const V u = vfma(am, am, vfma(Qi, Qi, vfma(Qr, Qr, vfma(ai, ai, vadd(am, am)))));
+        am = vfma(vneg(u), vfma(vbc<V>(-0.5f), am, vbc<V>(0.5f)), am);  // am -= u / (2 (1 + am))
+        apply_group(p, am, ai, Qr, Qi);
+    }
+};
+
+template <int G, int DC, int DS, int SCHEME = 0, typename Pt>
+__device__ __forceinline__ void step_group(Pt &p, const float2 *e)
+{
+    using V = decltype(p.ar);
+    Chain<V> c;
+    V m, qr, qi;
+    coeffs_scheme<SCHEME, DC, DS>(p, e[0], m, qr, qi);
+    c.first(m, qr, qi);
+    coeffs_scheme<SCHEME, DC, DS>(p, e[1], m, qr, qi);
+    c.second(m, qr, qi);
+#pragma unroll kGroupUnroll
+    for (int k = 2; k < G; ++k) {
+        coeffs_scheme<SCHEME, DC, DS>(p, e[k], m, qr, qi);
+        c.next(m, qr, qi);
+    }
+    c.finish(p);
+}
+
+// MAGNUS4 steps in groups (G = 2, 4, 8, 16).  One step is exp(-i n.sigma) with
+// n = (dt Pbar, n_z): U = [[1 + m - i qz, -q], [conj(q), 1 + m + i qz]], m =
+// cos|n| - 1, (q, qz) = sin|n|/|n| (n_y + i n_x, n_z), formed as n + (sinc - 1) n.
+// The chain is the EXACT one with the sigma_z terms added:
+//   Re alpha' = Re alpha + m Re alpha + qz Im alpha - (qr Qr + qi Qi)
+//   Im alpha' = Im alpha + m Im alpha - qz Re alpha - (qi Qr - qr Qi)
+//   Qr'       = Qr + m Qr + qz Qi + qr Re alpha + qi Im alpha
+//   Qi'       = Qi + m Qi - qz Qr + qi Re alpha - qr Im alpha
+// starting from alpha = 1 + m - i qz, Q = q of the group's first step, then the
+// same unitarity rebuild of Re alpha - 1 and compensated update as EXACT groups.
+template <int DC, int DS, typename Pt, typename V>
+__device__ __forceinline__ void coeffs_magnus_group(const Pt &p, const float4 &e, V &m, V &qr,
+                                                    V &qi, V &qz)
+{
+    const V Px = vadd(p.pxh, vadd(vbc<V>(e.x), p.pxl));
+    const V Py = vadd(p.pyh, vadd(vbc<V>(e.y), p.pyl));
+    const V nz = vfma(Px, vbc<V>(e.w), vneg(vmul(Py, vbc<V>(e.z))));
+    const V x = vfma(Px, Px, vfma(Py, Py, vmul(nz, nz)));
+    m = vmul(vhorner<V, DC, 1, 0>(x), x);
+    const V s1 = vmul(vhorner<V, DS, 1, 1>(x), x);  // sin|n|/|n| - 1
+    qr = vfma(s1, Py, Py);
+    qi = vfma(s1, Px, Px);
+    qz = vfma(s1, nz, nz);
+}
+
+template <int G, int DC, int DS, typename Pt>
+__device__ __forceinline__ void step_group_magnus(Pt &p, const float4 *e)
+{
+    using V = decltype(p.ar);
+    V m, qr, qi, qz, Qr, Qi;
+    coeffs_magnus_group<DC, DS>(p, e[0], m, Qr, Qi, qz);
+    V Ar = vadd(m, vbc<V>(1.0f));
+    V ai = vneg(qz);
+#pragma unroll kMagnusGroupUnroll
+    for (int k = 1; k < G; ++k) {
+        coeffs_magnus_group<DC, DS>(p, e[k], m, qr, qi, qz);
+        const V nAr = vfma(m, Ar, vfma(qz, ai, vfma(vneg(qr), Qr, vfma(vneg(qi), Qi, Ar))));
+        const V nai = vfma(m, ai, vfma(vneg(qz), Ar, vfma(vneg(qi), Qr, vfma(qr, Qi, ai))));
+        const V nQr = vfma(m, Qr, vfma(qz, Qi, vfma(qr, Ar, vfma(qi, ai, Qr))));
+        const V nQi = vfma(m, Qi, vfma(vneg(qz), Qr, vfma(qi, Ar, vfma(vneg(qr), ai, Qi))));
+        Ar = nAr;
+        ai = nai;
+        Qr = nQr;
+        Qi = nQi;
+    }
+    V am = vadd(Ar, vbc<V>(-1.0f));  // exact: Re alpha is within [1/2, 2]
+    const V u = vfma(am, am, vfma(Qi, Qi, vfma(Qr, Qr, vfma(ai, ai, vadd(am, am)))));
+    am = vfma(vneg(u), vfma(vbc<V>(-0.5f), am, vbc<V>(0.5f)), am);  // am -= u / (2 (1 + am))
+    apply_group(p, am, ai, Qr, Qi);
+}
+
+}  // namespace
+}  // namespace dsp

@@ -9,12 +9,18 @@
 
 namespace dsp {
 
-// Points per CTA, and per FP64 partial sum of |c+|^2 (the reduction tile).
+// Points per CTA tile of the evolve kernels.
 constexpr int kTilePoints = 1024;
+// Row-strip tiles (ReqDesc::strips): columns per strip and rows per strip.
+constexpr int kStripWidth = 256;
+constexpr int kStripHeight = 4;
+// Points per density partial sum (a granule: point index / kGranule); every CTA
+// shape covers whole granules.
+constexpr int kGranule = 256;
 // Spinors per thread (independent momenta advanced together for ILP).
 constexpr int kSpinorsPerThread = 2;
 constexpr int kThreads = kTilePoints / kSpinorsPerThread;
-// Requests one evolve launch can carry in its parameter block (96 x 208 bytes:
+// Requests one evolve launch can carry in its parameter block (96 x 216 bytes:
 // within the 32 KB kernel-parameter limit).
 constexpr int kMaxReqPerLaunch = 96;
 // Device-side error bits (the launch's error word).
@@ -46,7 +52,7 @@ struct ReqDesc {
     const void *table;
     void *state;        // planes: FP32_MIXED float4 hi[n], float4 lo[n]; FP64 double2 a[n], double2 b[n]
     void *map;          // |c+|^2 output (float or double), or nullptr
-    double *partials;   // one double per tile (written when projecting)
+    double *partials;   // one double per granule of kGranule points (written when projecting)
     int *err;           // the request's device error word (bits kErr*)
     const float2 *nodes_out;  // projection nodes p + A_out as FP32 hi/lo pairs: nx
                               // columns, then the grid's ny rows (see node_tables)
@@ -71,6 +77,10 @@ struct ReqDesc {
                      // compensated update; G = 1 (every step alone), 2, 4, 8 or kGroupMax
     int32_t withhold_first_copy;  // test hook: announce chunk 0 but never copy it, so the
                                   // bounded wait for it runs out (no fault, no hang)
+    int32_t strips;  // EXACT or STRANG_XY with nx a multiple of kStripWidth: CTA tile b is
+                     // rows 4 (b / (nx / 256)) .. + 3, columns 256 (b % (nx / 256)) .. + 255
+                     // (the row-strip path); 0: CTA tile b is points 1024 b .. 1024 b + 1023
+    int32_t pad_;
     int64_t table_steps;          // entries in the table (checked by bounds-check builds)
 };
 
@@ -92,10 +102,9 @@ struct EvolveArgs {
 
 struct FinDesc {
     const double *partials;
-    int32_t n_tiles;
-    int32_t pad;
-    double scale;  // 4/(2 pi)^2 * hx * hy
-    double *out;   // device double
+    int64_t n_parts;  // granule partial sums
+    double scale;     // 4/(2 pi)^2 * hx * hy
+    double *out;      // device double
 };
 
 constexpr int kMaxFinPerLaunch = 64;
@@ -121,8 +130,13 @@ struct CombineArgs {
     int32_t row0;  // global row index of the grid's first row
 };
 
-// precision: 0 = FP64, 1 = FP32_MIXED.  Every request in args must have that precision.
-cudaError_t launch_evolve(const EvolveArgs &args, int precision, cudaStream_t stream);
+// Evolve launches, one kernel per kind of request: FP64 or FP32_MIXED, on
+// contiguous tiles (strips == 0) or on row strips (strips == 1).  Every request
+// in args must be of that kind.
+cudaError_t launch_evolve_f64(const EvolveArgs &args, cudaStream_t stream);
+cudaError_t launch_evolve_f64_strip(const EvolveArgs &args, cudaStream_t stream);
+cudaError_t launch_evolve_mixed(const EvolveArgs &args, cudaStream_t stream);
+cudaError_t launch_evolve_strip(const EvolveArgs &args, cudaStream_t stream);
 // Projection only, of states already on the device: every request in args has
 // step_begin == step_end, project == 1, fresh == 0 and a node table.
 cudaError_t launch_project(const EvolveArgs &args, int precision, cudaStream_t stream);

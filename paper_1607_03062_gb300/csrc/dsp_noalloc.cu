@@ -8,8 +8,8 @@
 // map they already hold in device memory to the pair density using only a
 // fixed scratch array that lives in this library's static device memory.
 //
-// The scratch is a file-scope __device__ array of kStaticMaxTiles + 1 doubles
-// (about 512 KB); every GPU that loads the library holds it until the process
+// The scratch is a file-scope __device__ array of kStaticMaxParts + 1 doubles
+// (about 2 MB); every GPU that loads the library holds it until the process
 // exits.  Its device address is looked up once per device with
 // cudaGetSymbolAddress on the first call made with that device current and
 // cached for the rest of the process (a cudaDeviceReset afterwards is not
@@ -17,8 +17,11 @@
 // name is only a host-side stand-in, never a device address).
 //
 // The arithmetic is the same as the reduction behind dsp_reduce_density: the
-// same 1024-point tiles, the same fixed pairwise tree per tile, the same
-// fixed-order final sum and the same 4/(2 pi)^2 hx hy prefactor.
+// same granules of 256 points, the same double-float pairwise tree per granule
+// (granule_sums), the same fixed-order final sum and the same 4/(2 pi)^2 hx hy
+// prefactor.  Each point's term is its map value: a double of an FP64 map split
+// into a pair exactly as the projection splits it, a float of an FP32_MIXED
+// map as (value, 0).
 
 #include <cuda_runtime.h>
 
@@ -26,55 +29,55 @@
 #include <mutex>
 
 #include "dsp.h"
+#include "dsp_df.cuh"
 #include "dsp_internal.h"
 
 namespace {
 
-// Up to 65536 tiles of 1024 points: DSP_NOALLOC_MAX_POINTS = 67,108,864 points.
-constexpr int kStaticMaxTiles = DSP_NOALLOC_MAX_POINTS / dsp::kTilePoints;
-static_assert(static_cast<long long>(kStaticMaxTiles) * dsp::kTilePoints == DSP_NOALLOC_MAX_POINTS,
-              "the static scratch must hold one partial sum per tile");
+// Up to 262144 granules of 256 points: DSP_NOALLOC_MAX_POINTS = 67,108,864 points.
+constexpr int kStaticMaxParts = DSP_NOALLOC_MAX_POINTS / dsp::kGranule;
+static_assert(static_cast<long long>(kStaticMaxParts) * dsp::kGranule == DSP_NOALLOC_MAX_POINTS,
+              "the static scratch must hold one partial sum per granule");
 constexpr int kMaxDevices = 64;
+constexpr int kThreads = 256;
+constexpr int kPoints = dsp::kTilePoints / kThreads;  // points per thread
 
-// [0, kStaticMaxTiles): per-tile partial sums; [kStaticMaxTiles]: the density.
-static __device__ __align__(256) double g_noalloc_scratch[kStaticMaxTiles + 1];
+// [0, kStaticMaxParts): per-granule partial sums; [kStaticMaxParts]: the density.
+static __device__ __align__(256) double g_noalloc_scratch[kStaticMaxParts + 1];
 
 std::mutex g_setup_mutex;
 double *g_scratch_addr[kMaxDevices] = {nullptr};
 
-// Per-tile FP64 sums of the map, in the tile layout and tree order of the
-// fused projection (point base + s * kThreads + t sits at red[s * kThreads + t]).
-__global__ void __launch_bounds__(dsp::kThreads)
-    noalloc_tile_sums(const void *map, int precision, int64_t n_points, double *partials)
+// Granule partial sums of the map, one CTA per 1024 points (4 granules).
+__global__ void __launch_bounds__(kThreads)
+    noalloc_granule_sums(const void *map, int precision, int64_t n_points, double *partials)
 {
-    __shared__ double red[dsp::kTilePoints];
+    __shared__ float2 red[dsp::kTilePoints];
     const int64_t base = static_cast<int64_t>(blockIdx.x) * dsp::kTilePoints;
 #pragma unroll
-    for (int s = 0; s < dsp::kSpinorsPerThread; ++s) {
-        const int64_t idx = base + s * dsp::kThreads + threadIdx.x;
-        double v = 0.0;
-        if (idx < n_points)
-            v = precision == DSP_FP64 ? static_cast<const double *>(map)[idx]
-                                      : static_cast<double>(static_cast<const float *>(map)[idx]);
-        red[s * dsp::kThreads + threadIdx.x] = v;
+    for (int s = 0; s < kPoints; ++s) {
+        const int64_t idx = base + s * kThreads + threadIdx.x;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (idx < n_points) {
+            if (precision == DSP_FP64)
+                dsp::split_f64(static_cast<const double *>(map)[idx], v.x, v.y);
+            else
+                v.x = static_cast<const float *>(map)[idx];
+        }
+        red[s * kThreads + threadIdx.x] = v;
     }
-    __syncthreads();
-    for (int s = dsp::kTilePoints / 2; s > 0; s >>= 1) {
-        for (int t = threadIdx.x; t < s; t += blockDim.x)
-            red[t] += red[t + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-        partials[blockIdx.x] = red[0];
+    dsp::granule_sums(red, dsp::kTilePoints / dsp::kGranule, partials,
+                      (n_points + dsp::kGranule - 1) / dsp::kGranule,
+                      [&](int g) { return base / dsp::kGranule + g; });
 }
 
 // Fixed-order sum of the partials (per-thread strided sums, then a tree).
 __global__ void __launch_bounds__(1024)
-    noalloc_finalize(const double *partials, int n_tiles, double scale, double *out)
+    noalloc_finalize(const double *partials, int64_t n_parts, double scale, double *out)
 {
     __shared__ double red[1024];
     double acc = 0.0;
-    for (int i = threadIdx.x; i < n_tiles; i += blockDim.x)
+    for (int64_t i = threadIdx.x; i < n_parts; i += blockDim.x)
         acc += partials[i];
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -129,6 +132,7 @@ extern "C" dsp_status dsp_density_noalloc(const void *map_dev, int32_t precision
     if (s != DSP_OK)
         return s;
     const int n_tiles = static_cast<int>((n_points + dsp::kTilePoints - 1) / dsp::kTilePoints);
+    const int64_t n_parts = (n_points + dsp::kGranule - 1) / dsp::kGranule;
     const double hx = (px_max - px_min) / nx, hy = (py_max - py_min) / ny;
     const double scale = 4.0 / ((2.0 * 3.14159265358979323846) * (2.0 * 3.14159265358979323846)) *
                          hx * hy;
@@ -138,11 +142,11 @@ extern "C" dsp_status dsp_density_noalloc(const void *map_dev, int32_t precision
     (void)cudaGetLastError();
     // Every partial and the result slot are overwritten, so nothing left over
     // from an earlier call is read.
-    noalloc_tile_sums<<<n_tiles, dsp::kThreads, 0, stream>>>(map_dev, precision, n_points, scratch);
-    noalloc_finalize<<<1, 1024, 0, stream>>>(scratch, n_tiles, scale, scratch + kStaticMaxTiles);
+    noalloc_granule_sums<<<n_tiles, kThreads, 0, stream>>>(map_dev, precision, n_points, scratch);
+    noalloc_finalize<<<1, 1024, 0, stream>>>(scratch, n_parts, scale, scratch + kStaticMaxParts);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(n_host, scratch + kStaticMaxTiles, sizeof(double),
+        e = cudaMemcpyAsync(n_host, scratch + kStaticMaxParts, sizeof(double),
                             cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(stream);

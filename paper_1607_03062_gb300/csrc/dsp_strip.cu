@@ -1,0 +1,402 @@
+// dsp_strip.cu -- the FP32_MIXED evolve kernel on row strips (schemes EXACT and
+// STRANG_XY, grids whose nx is a multiple of 256).  Shared device code is in
+// dsp_device.cuh.
+
+#include "dsp_device.cuh"
+
+namespace dsp {
+namespace {
+
+// ---------------------------------------------------------------------------
+// FP32_MIXED EXACT and STRANG_XY on row strips (grids whose nx is a multiple
+// of 256)
+//
+// A CTA owns kStripRows = 4 rows x kStripThreads = 256 columns; thread t holds
+// column c0 + t of each of the 4 rows, as 2 packs (rows 0, 1 and rows 2, 3).  A
+// thread's spinors share p_x and the CTA's threads share the 4 p_y, so the part
+// of a step's coefficients that depends on dt P_y alone is computed once per row
+// and step into a table in shared memory (built for each chunk of steps), and
+// the part that depends on dt P_x alone once per thread and step, as scalars:
+//   EXACT:     rows dt P_y and fl(dt P_y^2); column dt P_x;
+//   STRANG_XY: rows cos(dt P_y) - 1 and sin(dt P_y); column cos(dt P_x) - 1 and
+//              sin(dt P_x) (with dt P_x = 2a of the split).
+// Every operation on a point is the contiguous path's (same operands, same
+// order, same rounding), so each point's result is bitwise the same on either
+// tiling; only the work per step shrinks (EXACT: 3.5 + dc + ds coefficient
+// lane-ops per spinor-step instead of 8 + dc + ds; STRANG_XY: 3 per spinor plus
+// (4 + dc + ds)/4 per thread instead of 12 + 2 (dc + ds)).
+// ---------------------------------------------------------------------------
+
+constexpr int kStripThreads = 256;
+constexpr int kStripRows = 4;
+constexpr int kStripStage = 4096;             // bytes per staged table chunk
+constexpr int kStripChunk = kStripStage / 8;  // steps per chunk (float2 entries)
+static_assert(kStripThreads * kStripRows == kTilePoints, "a strip tile holds kTilePoints points");
+static_assert(kStripThreads == kGranule, "a strip row is one density granule");
+static_assert(kStripThreads == kStripWidth && kStripRows == kStripHeight, "the host's tiling");
+
+struct StripSmem {
+    unsigned char stage[2][kStripStage];  // bulk-copied table entries (dt A_x, dt A_y)
+    float4 rows[kStripChunk][2];          // per step, per pack (rows 0, 1 and 2, 3): see StripRows
+    float ax[kStripChunk];                // per step: dt A_x
+};
+static_assert(sizeof(StripSmem) <= 48 * 1024, "static shared memory of one CTA");
+
+// The row part of a step for the two rows of a pack, from dt P_y of each:
+//   EXACT     {P_y(r0), P_y(r1), fl(P_y(r0)^2), fl(P_y(r1)^2)}
+//   STRANG_XY {cy(r0), cy(r1), sb(r0), sb(r1)}, cy = cos b - 1, sb = sin b, b = dt P_y,
+// each as coeffs_group / coeffs_strang_group form it for one lane.
+template <int SCHEME, int DC, int DS>
+__device__ __forceinline__ float4 strip_row(float y0, float y1)
+{
+    if constexpr (SCHEME == 0) {
+        return make_float4(y0, y1, __fmul_rn(y0, y0), __fmul_rn(y1, y1));
+    } else {
+        const float x0 = vmul(y0, y0), x1 = vmul(y1, y1);
+        const float c0 = vmul(vhorner<float, DC, 1, 0>(x0), x0);
+        const float c1 = vmul(vhorner<float, DC, 1, 0>(x1), x1);
+        const float s0 = vfma(vmul(vhorner<float, DS, 1, 1>(x0), x0), y0, y0);
+        const float s1 = vfma(vmul(vhorner<float, DS, 1, 1>(x1), x1), y1, y1);
+        return make_float4(c0, c1, s0, s1);
+    }
+}
+
+// The column part of a step, from dt P_x = dt p_hi + (dt A_x + dt p_lo):
+//   EXACT     a = (P_x, P_x);
+//   STRANG_XY a = (cx, cx), b = (sa, sa): cx = cos 2a - 1, sa = sin 2a, 2a = dt P_x.
+struct StripCol {
+    float2 a, b;
+};
+
+template <int SCHEME, int DC, int DS>
+__device__ __forceinline__ StripCol strip_col(float pxh, float pxl, float ax)
+{
+    const float px = __fadd_rn(pxh, __fadd_rn(ax, pxl));
+    if constexpr (SCHEME == 0) {
+        return StripCol{make_float2(px, px), make_float2(0.0f, 0.0f)};
+    } else {
+        const float xx = vmul(px, px);
+        const float cx = vmul(vhorner<float, DC, 1, 0>(xx), xx);
+        const float sa = vfma(vmul(vhorner<float, DS, 1, 1>(xx), xx), px, px);
+        return StripCol{make_float2(cx, cx), make_float2(sa, sa)};
+    }
+}
+
+// (m, q) of a step for a pack in the small-part form of the groups
+// (coeffs_group / coeffs_strang_group).
+template <int SCHEME, int DC, int DS>
+__device__ __forceinline__ void strip_coeffs_group(const StripCol &c, float4 r, float2 &m,
+                                                   float2 &qr, float2 &qi)
+{
+    if constexpr (SCHEME == 0) {
+        const float2 Py = make_float2(r.x, r.y), Py2 = make_float2(r.z, r.w);
+        const float2 x = vfma(c.a, c.a, Py2);
+        m = vmul(vhorner<float2, DC, 1, 0>(x), x);
+        const float2 s1 = vmul(vhorner<float2, DS, 1, 1>(x), x);
+        qr = vfma(s1, Py, Py);
+        qi = vfma(s1, c.a, c.a);
+    } else {
+        const float2 cy = make_float2(r.x, r.y);
+        qr = make_float2(r.z, r.w);
+        qi = vfma(cy, c.b, c.b);
+        m = vfma(c.a, cy, vadd(c.a, cy));
+    }
+}
+
+// (m, q) of an EXACT step alone, in coeffs_exact2's form.
+template <int DC, int DS>
+__device__ __forceinline__ void strip_coeffs_exact(const StripCol &c, float4 r, float2 &m,
+                                                   float2 &qr, float2 &qi)
+{
+    const float2 Py = make_float2(r.x, r.y), Py2 = make_float2(r.z, r.w);
+    const float2 x = fma2(c.a, c.a, Py2);
+    m = mul2(horner2<DC, 1, 0>(x), x);
+    const float2 sn = horner2<DS, 0, 1>(x);
+    qr = mul2(sn, Py);
+    qi = mul2(sn, c.a);
+}
+
+template <int SCHEME, int DC, int DS>
+struct StripThread {
+    float pxh, pxl;  // dt p_x of the column, hi + lo
+    const StripSmem *sm;
+
+    __device__ __forceinline__ StripCol col(int j) const
+    {
+        return strip_col<SCHEME, DC, DS>(pxh, pxl, sm->ax[j]);
+    }
+    // one step alone: step_exact2 (EXACT) or step_single_scheme (STRANG_XY)
+    __device__ __forceinline__ void single(MixedPack (&pk)[2], int j) const
+    {
+        const StripCol c = col(j);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            float2 m, qr, qi;
+            if constexpr (SCHEME == 0) {
+                strip_coeffs_exact<DC, DS>(c, sm->rows[j][q], m, qr, qi);
+                apply_exact2(pk[q], m, qr, qi);
+            } else {
+                strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j][q], m, qr, qi);
+                apply_group(pk[q], m, bc2(0.0f), qr, qi);
+            }
+        }
+    }
+    // two EXACT steps multiplied (step_pair2)
+    __device__ __forceinline__ void pair(MixedPack (&pk)[2], int j) const
+    {
+        const StripCol c0 = col(j), c1 = col(j + 1);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            float2 m1, q1r, q1i, m2, q2r, q2i;
+            strip_coeffs_exact<DC, DS>(c0, sm->rows[j][q], m1, q1r, q1i);
+            strip_coeffs_exact<DC, DS>(c1, sm->rows[j + 1][q], m2, q2r, q2i);
+            pair_apply2(pk[q], m1, q1r, q1i, m2, q2r, q2i);
+        }
+    }
+    // step_group's chain, both packs advanced step by step
+    template <int G>
+    __device__ __forceinline__ void group(MixedPack (&pk)[2], int j) const
+    {
+        Chain<float2> ch[2];
+        float2 m, qr, qi;
+        StripCol c = col(j);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j][q], m, qr, qi);
+            ch[q].first(m, qr, qi);
+        }
+        c = col(j + 1);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j + 1][q], m, qr, qi);
+            ch[q].second(m, qr, qi);
+        }
+#pragma unroll kGroupUnroll
+        for (int k = 2; k < G; ++k) {
+            c = col(j + k);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j + k][q], m, qr, qi);
+                ch[q].next(m, qr, qi);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            ch[q].finish(pk[q]);
+    }
+};
+
+// The launch's steps on a strip tile: each chunk of table entries is staged by
+// bulk copy (double buffered, bounded waits), expanded into the row table,
+// then stepped in groups of G aligned to absolute step indices (ragged ends one
+// step at a time, as run_step_groups).  G = 1: every step alone.  EXACT pairs
+// (G = 2) take step_pair2's form; STRANG_XY pairs take the chain, as on the
+// contiguous tiles.
+template <int SCHEME, int G, int DC, int DS>
+__device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint64_t *bars, int *err,
+                                          const StripThread<SCHEME, DC, DS> &th,
+                                          const float (&pyh)[kStripRows],
+                                          const float (&pyl)[kStripRows], MixedPack (&pk)[2])
+{
+    using St = Stager<float2, kStripStage>;
+    constexpr int GA = G > St::kAlign ? G : St::kAlign;  // staging starts on a group and 16 bytes
+    static_assert(St::kCh % GA == 0, "chunks hold whole groups");
+    const int64_t b_al = R.step_begin & ~static_cast<int64_t>(GA - 1);
+    if (!table_range_ok(R, b_al, err))
+        return false;
+    St st{&sm.stage[0][0], bars, static_cast<const float2 *>(R.table) + b_al, R.step_end - b_al, 0};
+    st.withhold_first = R.withhold_first_copy;
+    if (R.step_end <= R.step_begin)
+        st.nsteps = 0;
+    st.nchunks = static_cast<int>((st.nsteps + St::kCh - 1) / St::kCh);
+    if (threadIdx.x == 0) {
+        if (st.nchunks > 0) st.issue(0);
+        if (st.nchunks > 1) st.issue(1);
+    }
+    for (int c = 0; c < st.nchunks; ++c) {
+        const bool ok = mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0)
+                st.on_timeout(c, err);
+            return false;
+        }
+        const float2 *tb = st.stage(c);
+        const int len = st.chunk_len(c);
+        // the row table of this chunk, from dt P_y = dt p_hi + (dt A_y + dt p_lo)
+        for (int j = threadIdx.x; j < len; j += blockDim.x) {
+            const float2 a = tb[j];
+            sm.ax[j] = a.x;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float y0 = __fadd_rn(pyh[2 * q], __fadd_rn(a.y, pyl[2 * q]));
+                const float y1 = __fadd_rn(pyh[2 * q + 1], __fadd_rn(a.y, pyl[2 * q + 1]));
+                sm.rows[j][q] = strip_row<SCHEME, DC, DS>(y0, y1);
+            }
+        }
+        __syncthreads();  // the table is built and stage c & 1 is free again
+        if (threadIdx.x == 0 && c + 2 < st.nchunks)
+            st.issue(c + 2);
+        // entries before step_begin - b_al belong to earlier launches
+        int j = c == 0 ? static_cast<int>(R.step_begin - b_al) : 0;
+        if constexpr (G == 1) {
+#pragma unroll 2
+            for (; j < len; ++j)
+                th.single(pk, j);
+        } else {
+            for (; j < len && (j & (G - 1)) != 0; ++j)  // ragged start
+                th.single(pk, j);
+            if constexpr (G == 2 && SCHEME == 0) {
+#pragma unroll kPairUnroll
+                for (; j + G <= len; j += G)
+                    th.pair(pk, j);
+            } else {
+#pragma unroll 1
+                for (; j + G <= len; j += G)
+                    th.template group<G>(pk, j);
+            }
+            for (; j < len; ++j)  // ragged end (last chunk only)
+                th.single(pk, j);
+        }
+        __syncthreads();  // everyone is done with the row table
+    }
+    return true;
+}
+
+template <int SCHEME, int DC, int DS>
+__device__ void body_strip(const ReqDesc &R, int tile, unsigned char *smem, uint64_t *bars,
+                           int *err)
+{
+    StripSmem &sm = *reinterpret_cast<StripSmem *>(smem);
+    const int tid = threadIdx.x;
+    const int ncb = R.nx / kStripThreads;
+    const int rb = tile / ncb, cb = tile - rb * ncb;
+    const int64_t col = static_cast<int64_t>(cb) * kStripThreads + tid;
+    const double vs = R.valley > 0 ? 1.0 : -1.0;
+    float4 *hi_plane = static_cast<float4 *>(R.state);
+    float4 *lo_plane = hi_plane + R.n_points;
+    // valley K- is stepped as K+ on -P: the table holds -dt*A, here -dt*p
+    const double px = grid_node(R.px_min, R.hx, col);
+    const double tx = vs * (R.dt * px);
+    StripThread<SCHEME, DC, DS> th;
+    th.pxh = static_cast<float>(tx);
+    th.pxl = static_cast<float>(tx - static_cast<double>(th.pxh));
+    th.sm = &sm;
+    float pyh[kStripRows], pyl[kStripRows];
+    MixedPoint pt[kStripRows];
+#pragma unroll
+    for (int k = 0; k < kStripRows; ++k) {
+        const int64_t row = static_cast<int64_t>(rb) * kStripRows + k;
+        const bool valid = row < R.ny;  // the last strip of a grid may hang over its end
+        const int64_t idx = row * R.nx + col;
+        const double py = grid_node(R.py_min, R.hy, R.row0 + row);
+        const double ty = vs * (R.dt * py);
+        pyh[k] = static_cast<float>(ty);
+        pyl[k] = static_cast<float>(ty - static_cast<double>(pyh[k]));
+        pt[k].pxh = th.pxh; pt[k].pxl = th.pxl; pt[k].pyh = pyh[k]; pt[k].pyl = pyl[k];
+        if (R.fresh || !valid) {
+            double ar = 1.0, ai = 0.0, br = 0.0, bi = 0.0;  // identity column
+            if (!R.init_identity)
+                initial_spinor(px + R.a_in[0], py + R.a_in[1], vs, ar, ai, br, bi);
+            pt[k].ar = static_cast<float>(ar);
+            pt[k].lar = static_cast<float>(ar - static_cast<double>(pt[k].ar));
+            pt[k].ai = static_cast<float>(ai);
+            pt[k].lai = static_cast<float>(ai - static_cast<double>(pt[k].ai));
+            pt[k].br = static_cast<float>(br);
+            pt[k].lbr = static_cast<float>(br - static_cast<double>(pt[k].br));
+            pt[k].bi = static_cast<float>(bi);
+            pt[k].lbi = static_cast<float>(bi - static_cast<double>(pt[k].bi));
+        } else {
+            const float4 h = hi_plane[idx], l = lo_plane[idx];
+            pt[k].ar = h.x; pt[k].ai = h.y; pt[k].br = h.z; pt[k].bi = h.w;
+            pt[k].lar = l.x; pt[k].lai = l.y; pt[k].lbr = l.z; pt[k].lbi = l.w;
+        }
+    }
+    MixedPack pk[2] = {pack_points(pt[0], pt[1]), pack_points(pt[2], pt[3])};
+    bool ok;
+    if constexpr (kGroupedLevel<DC, DS>) {
+        if (R.group == kGroupMax)
+            ok = run_strip<SCHEME, kGroupMax>(R, sm, bars, err, th, pyh, pyl, pk);
+        else if (R.group == 8)
+            ok = run_strip<SCHEME, 8>(R, sm, bars, err, th, pyh, pyl, pk);
+        else if (R.group == 4)
+            ok = run_strip<SCHEME, 4>(R, sm, bars, err, th, pyh, pyl, pk);
+        else if (R.group == 2)
+            ok = run_strip<SCHEME, 2>(R, sm, bars, err, th, pyh, pyl, pk);
+        else
+            ok = run_strip<SCHEME, 1>(R, sm, bars, err, th, pyh, pyl, pk);
+    } else {  // no group paths at this level (the host keeps G = 1)
+        ok = run_strip<SCHEME, 1>(R, sm, bars, err, th, pyh, pyl, pk);
+    }
+    unpack_points(pk[0], pt[0], pt[1]);
+    unpack_points(pk[1], pt[2], pt[3]);
+    if (!ok)
+        return;
+
+    float2 *red = reinterpret_cast<float2 *>(smem);  // the staging memory is free now
+#pragma unroll
+    for (int k = 0; k < kStripRows; ++k) {
+        const int64_t row = static_cast<int64_t>(rb) * kStripRows + k;
+        const int64_t idx = row * R.nx + col;
+        float2 c = make_float2(0.0f, 0.0f);
+        if (row < R.ny) {
+            if (R.store_state) {
+                hi_plane[idx] = make_float4(pt[k].ar, pt[k].ai, pt[k].br, pt[k].bi);
+                lo_plane[idx] = make_float4(pt[k].lar, pt[k].lai, pt[k].lbr, pt[k].lbi);
+            }
+            if (R.project) {
+                const SpinorDF v{pt[k].ar, pt[k].lar, pt[k].ai, pt[k].lai,
+                                 pt[k].br, pt[k].lbr, pt[k].bi, pt[k].lbi};
+                c = store_point<1>(R.map, idx, project_node<1>(R, col, row, v));
+            }
+        }
+        if (R.project)
+            red[k * kGranule + tid] = c;
+    }
+    if (R.project)  // granule of strip row k: row (rb * 4 + k), columns from cb * 256
+        granule_sums(red, kStripRows, R.partials, (R.n_points + kGranule - 1) / kGranule,
+                     [&](int g) { return (static_cast<int64_t>(rb) * kStripRows + g) * ncb + cb; });
+}
+
+template <int SCHEME, int L>
+__device__ __forceinline__ void dispatch_strip(const ReqDesc &R, int tile, unsigned char *smem,
+                                               uint64_t *bars, int *err)
+{
+    if (R.level == L || L + 1 == kNumLevels)
+        body_strip<SCHEME, kLevelsF32[L].dc, kLevelsF32[L].ds>(R, tile, smem, bars, err);
+    else if constexpr (L + 1 < kNumLevels)
+        dispatch_strip<SCHEME, L + 1>(R, tile, smem, bars, err);
+}
+
+__global__ void __launch_bounds__(kStripThreads, kMixedMinBlocks)
+    evolve_strip_kernel(const __grid_constant__ EvolveArgs args)
+{
+    __shared__ __align__(128) unsigned char smem[sizeof(StripSmem)];
+    __shared__ __align__(8) uint64_t bars[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int r = find_request(args);
+    const ReqDesc &R = args.r[r];
+    const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
+    if (!tile_ok(R, tile, R.err))
+        return;
+    if (R.scheme == 0)
+        dispatch_strip<0, 0>(R, tile, smem, bars, R.err);
+    else
+        dispatch_strip<1, 0>(R, tile, smem, bars, R.err);
+}
+
+}  // namespace
+
+cudaError_t launch_evolve_strip(const EvolveArgs &args, cudaStream_t stream)
+{
+    if (args.nreq <= 0 || args.total_tiles <= 0)
+        return cudaSuccess;
+    evolve_strip_kernel<<<args.total_tiles, kStripThreads, 0, stream>>>(args);
+    return cudaGetLastError();
+}
+
+}  // namespace dsp
