@@ -163,14 +163,13 @@ dsp_status check_usable(const dsp_grid *g)
     return g->latched;
 }
 
-// EXACT and STRANG_XY grids (both precisions) whose rows split into whole
-// 256-column strips evolve on row-strip tiles (ReqDesc::strips); every point's
-// arithmetic is the same on either tiling.
+// Grids whose rows split into whole 256-column strips evolve on row-strip tiles
+// (ReqDesc::strips): FP32_MIXED in every scheme, FP64 in EXACT and STRANG_XY.
+// Every point's arithmetic is the same on either tiling.
 bool use_strips(const dsp_grid *g)
 {
-    return g->allow_strips &&
-           (g->scheme == DSP_SCHEME_EXACT || g->scheme == DSP_SCHEME_STRANG_XY) &&
-           g->nx % dsp::kStripWidth == 0;
+    return g->allow_strips && g->nx % dsp::kStripWidth == 0 &&
+           (g->precision == DSP_FP32_MIXED || g->scheme != DSP_SCHEME_MAGNUS4);
 }
 
 int32_t strip_tiles(const dsp_grid *g)

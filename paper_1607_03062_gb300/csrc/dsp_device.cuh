@@ -1097,17 +1097,22 @@ __device__ __forceinline__ void coeffs_magnus_group(const Pt &p, const float4 &e
     qz = vfma(s1, nz, nz);
 }
 
-template <int G, int DC, int DS, typename Pt>
-__device__ __forceinline__ void step_group_magnus(Pt &p, const float4 *e)
-{
-    using V = decltype(p.ar);
-    V m, qr, qi, qz, Qr, Qi;
-    coeffs_magnus_group<DC, DS>(p, e[0], m, Qr, Qi, qz);
-    V Ar = vadd(m, vbc<V>(1.0f));
-    V ai = vneg(qz);
-#pragma unroll kMagnusGroupUnroll
-    for (int k = 1; k < G; ++k) {
-        coeffs_magnus_group<DC, DS>(p, e[k], m, qr, qi, qz);
+// The MAGNUS4 chain: first(...) for the group's first step, next(...) for the
+// others, finish(p) for the unitarity rebuild and the compensated update.
+// Every MAGNUS4 group (either tiling) goes through these operations.
+template <typename V>
+struct MagnusChain {
+    V Ar, ai, Qr, Qi;
+
+    __device__ __forceinline__ void first(V m, V qr, V qi, V qz)
+    {
+        Qr = qr;
+        Qi = qi;
+        Ar = vadd(m, vbc<V>(1.0f));
+        ai = vneg(qz);
+    }
+    __device__ __forceinline__ void next(V m, V qr, V qi, V qz)
+    {
         const V nAr = vfma(m, Ar, vfma(qz, ai, vfma(vneg(qr), Qr, vfma(vneg(qi), Qi, Ar))));
         const V nai = vfma(m, ai, vfma(vneg(qz), Ar, vfma(vneg(qi), Qr, vfma(qr, Qi, ai))));
         const V nQr = vfma(m, Qr, vfma(qz, Qi, vfma(qr, Ar, vfma(qi, ai, Qr))));
@@ -1117,10 +1122,30 @@ __device__ __forceinline__ void step_group_magnus(Pt &p, const float4 *e)
         Qr = nQr;
         Qi = nQi;
     }
-    V am = vadd(Ar, vbc<V>(-1.0f));  // exact: Re alpha is within [1/2, 2]
-    const V u = vfma(am, am, vfma(Qi, Qi, vfma(Qr, Qr, vfma(ai, ai, vadd(am, am)))));
-    am = vfma(vneg(u), vfma(vbc<V>(-0.5f), am, vbc<V>(0.5f)), am);  // am -= u / (2 (1 + am))
-    apply_group(p, am, ai, Qr, Qi);
+    template <typename Pt>
+    __device__ __forceinline__ void finish(Pt &p) const
+    {
+        V am = vadd(Ar, vbc<V>(-1.0f));  // exact: Re alpha is within [1/2, 2]
+        const V u = vfma(am, am, vfma(Qi, Qi, vfma(Qr, Qr, vfma(ai, ai, vadd(am, am)))));
+        am = vfma(vneg(u), vfma(vbc<V>(-0.5f), am, vbc<V>(0.5f)), am);  // am -= u / (2 (1 + am))
+        apply_group(p, am, ai, Qr, Qi);
+    }
+};
+
+template <int G, int DC, int DS, typename Pt>
+__device__ __forceinline__ void step_group_magnus(Pt &p, const float4 *e)
+{
+    using V = decltype(p.ar);
+    MagnusChain<V> c;
+    V m, qr, qi, qz;
+    coeffs_magnus_group<DC, DS>(p, e[0], m, qr, qi, qz);
+    c.first(m, qr, qi, qz);
+#pragma unroll kMagnusGroupUnroll
+    for (int k = 1; k < G; ++k) {
+        coeffs_magnus_group<DC, DS>(p, e[k], m, qr, qi, qz);
+        c.next(m, qr, qi, qz);
+    }
+    c.finish(p);
 }
 
 }  // namespace

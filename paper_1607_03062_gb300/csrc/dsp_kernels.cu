@@ -395,124 +395,150 @@ __global__ void __launch_bounds__(kStrip64Threads, 2)
 }
 
 // Projection of a state already on the device (a launch with no steps).  HBM
-// streaming: persistent CTAs (kProjCtasPerSm per SM) walk the launch's tiles in
-// halves of kProjTile = 512 points; the two state planes of a half tile (2 x 8
-// KB) arrive by 1-D bulk copies (cp.async.bulk) into a ring of kProjBufs buffers
-// in shared memory, each completing on its own mbarrier, so the copies of the
-// next kProjBufs - 1 half tiles are in flight while one is projected.  The value
-// of each point comes from project_node and store_point and the density partials
-// from granule_sums, as in the projection fused into the evolve kernels, so both
-// give the same bits.  Per point: 32 bytes of state read, 4 (FP32_MIXED) or 8
-// (FP64) bytes of map written; FP64-pipe work is one add per point for an FP64
-// map, none for FP32_MIXED.
-constexpr int kProjThreads = 256;
-constexpr int kProjTile = 512;                          // points per half tile
-constexpr int kProjPoints = kProjTile / kProjThreads;  // per thread
-constexpr int kProjBufs = 4;
-constexpr int kProjCtasPerSm = 3;
-constexpr int kProjPlane = kProjTile * 16;  // bytes of one state plane of a half tile
-static_assert(kTilePoints % kProjTile == 0 && kProjTile % kGranule == 0, "whole granules");
-
-struct ProjSmem {
-    unsigned char plane[kProjBufs][2][kProjPlane];  // [buffer][plane]
-    float2 red[kProjTile];
-    uint64_t bars[kProjBufs];
-};
+// streaming with no CTA-wide barrier: every warp works on its own granules
+// (256 points: the density's partial-sum unit) through its own ring of two
+// shared-memory buffers.  Lane 0 queues both state planes of a granule (2 x 4
+// KB) by 1-D bulk copy (cp.async.bulk) completing on the buffer's mbarrier, so
+// the next granule's copy is in flight while the warp projects the current one.
+// Lane l holds the granule's points l, l + 32, ..., l + 224: the pairwise tree
+// of granule_sums (slot j plus slot j + s for s = 128, ..., 1) then takes its
+// first three levels inside each lane and the last five across lanes by
+// shuffles, the same pairs in the same order, and each point's value comes
+// from project_node and store_point as in the evolve kernels, so both give the
+// same bits.  Per point: 32 bytes of state read, 4 (FP32_MIXED) or 8 (FP64)
+// bytes of map written; FP64-pipe work is one add per point for an FP64 map,
+// none for FP32_MIXED.
+constexpr int kProjWarps = 12;                        // warps per CTA, one CTA per SM
+constexpr int kProjThreads = 32 * kProjWarps;
+constexpr int kProjPer = kGranule / 32;               // points per lane and granule
+constexpr int kProjPlane = kGranule * 16;             // bytes of one state plane of a granule
+constexpr int kProjWarpBytes = 2 * 2 * kProjPlane;    // a warp's two buffers
+constexpr int kProjSmem = kProjWarps * (kProjWarpBytes + 2 * 8);
+static_assert(kTilePoints % kGranule == 0, "tiles hold whole granules");
 
 template <int PREC>
-__global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm)
+__global__ void __launch_bounds__(kProjThreads, 1)
     project_kernel(const __grid_constant__ EvolveArgs args)
 {
     extern __shared__ __align__(128) unsigned char proj_dyn[];
-    ProjSmem &sm = *reinterpret_cast<ProjSmem *>(proj_dyn);
-    constexpr int kHalves = kTilePoints / kProjTile;
-    const int tid = threadIdx.x;
-    const int total = args.total_tiles * kHalves;  // half tiles of the launch
-    if (tid == 0) {
-        for (int b = 0; b < kProjBufs; ++b)
-            mbar_init(&sm.bars[b], 1);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned char *buf = proj_dyn + w * kProjWarpBytes;  // [buffer][plane][kProjPlane]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(proj_dyn + kProjWarps * kProjWarpBytes) + 2 * w;
+    constexpr int kGranPerTile = kTilePoints / kGranule;
+    const int total = args.total_tiles * kGranPerTile;  // granules of the launch
+    const int wid = blockIdx.x * kProjWarps + w, nw = gridDim.x * kProjWarps;
+    if (lane == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
         fence_mbar_init();
     }
-    __syncthreads();
-    // one thread queues both planes of half tile H into buffer b (whole 16-byte
-    // points); a half tile past the end of its grid completes its phase empty
-    const auto issue = [&](int H, int b) {
-        const int T = H / kHalves;
+    __syncwarp();
+    // lane 0 queues both planes of granule Gi into buffer b (whole 16-byte points);
+    // a granule past the end of its grid completes its phase empty
+    const auto issue = [&](int Gi, int b) {
+        const int T = Gi / kGranPerTile;
         const ReqDesc &R = args.r[find_request(args, T)];
         const int64_t base = static_cast<int64_t>(T - R.tile_begin) * kTilePoints +
-                             static_cast<int64_t>(H % kHalves) * kProjTile;
+                             static_cast<int64_t>(Gi % kGranPerTile) * kGranule;
         const int64_t left = R.n_points - base;
         const uint32_t bytes =
-            left <= 0 ? 0u : 16u * static_cast<uint32_t>(left < kProjTile ? left : kProjTile);
-        mbar_arrive_expect_tx(&sm.bars[b], 2 * bytes);
+            left <= 0 ? 0u : 16u * static_cast<uint32_t>(left < kGranule ? left : kGranule);
+        mbar_arrive_expect_tx(&bars[b], 2 * bytes);
         if (bytes > 0) {
             const unsigned char *st = static_cast<const unsigned char *>(R.state);
-            bulk_load(sm.plane[b][0], st + 16 * base, bytes, &sm.bars[b]);
-            bulk_load(sm.plane[b][1], st + 16 * (R.n_points + base), bytes, &sm.bars[b]);
+            unsigned char *dst = buf + b * 2 * kProjPlane;
+            bulk_load(dst, st + 16 * base, bytes, &bars[b]);
+            bulk_load(dst + kProjPlane, st + 16 * (R.n_points + base), bytes, &bars[b]);
         }
     };
-    if (tid == 0)
-        for (int b = 0; b < kProjBufs; ++b)
-            if (static_cast<int>(blockIdx.x + b * gridDim.x) < total)
-                issue(blockIdx.x + b * gridDim.x, b);
+    if (lane == 0) {
+        if (wid < total)
+            issue(wid, 0);
+        if (wid + nw < total)
+            issue(wid + nw, 1);
+    }
     int k = 0;
-    for (int H = blockIdx.x; H < total; H += gridDim.x, ++k) {
-        const int b = k % kProjBufs;
-        const int T = H / kHalves;
+    for (int Gi = wid; Gi < total; Gi += nw, ++k) {
+        const int b = k & 1;
+        const int T = Gi / kGranPerTile;
         const ReqDesc &R = args.r[find_request(args, T)];
-        const bool ok = mbar_wait_bounded(&sm.bars[b], (k / kProjBufs) & 1);
-        if (!__syncthreads_and(ok)) {
-            if (tid == 0) {  // flag it; give the copies still queued a bounded chance to
-                             // land before the CTA exits
+        const bool arrived = mbar_wait_bounded(&bars[b], (k >> 1) & 1);
+        if (!__all_sync(0xffffffffu, arrived)) {
+            if (lane == 0) {  // flag it; give the other buffer's copy, if queued, a bounded
+                              // chance to land before the warp leaves
                 atomicOr(R.err, kErrTimeout);
-                for (int j = 1; j < kProjBufs; ++j)
-                    if (H + j * static_cast<int>(gridDim.x) < total)
-                        (void)mbar_wait_bounded(&sm.bars[(k + j) % kProjBufs],
-                                                ((k + j) / kProjBufs) & 1);
+                if (Gi + nw < total)
+                    (void)mbar_wait_bounded(&bars[b ^ 1], ((k + 1) >> 1) & 1);
             }
             return;
         }
         const int tile = T - R.tile_begin;
         if (tile_ok(R, tile, R.err)) {
-            const int64_t base = static_cast<int64_t>(tile) * kTilePoints +
-                                 static_cast<int64_t>(H % kHalves) * kProjTile;
-            // column and row of the thread's first point, then stepped (no division per point)
-            int64_t col = (base + tid) % R.nx, row = (base + tid) / R.nx;
+            const int64_t gbase = static_cast<int64_t>(tile) * kTilePoints +
+                                  static_cast<int64_t>(Gi % kGranPerTile) * kGranule;
+            // column and row of the granule's first point (one division per granule),
+            // then of this lane's points by stepping
+            int64_t col0 = 0, row0 = 0;
+            if (lane == 0) {
+                col0 = gbase % R.nx;
+                row0 = gbase / R.nx;
+            }
+            col0 = __shfl_sync(0xffffffffu, col0, 0);
+            row0 = __shfl_sync(0xffffffffu, row0, 0);
+            int64_t col = col0 + lane, row = row0;
+            while (col >= R.nx) {
+                col -= R.nx;
+                ++row;
+            }
+            const unsigned char *src = buf + b * 2 * kProjPlane;
+            float2 v[kProjPer];
 #pragma unroll
-            for (int s = 0; s < kProjPoints; ++s) {
-                const int l = s * kProjThreads + tid;
-                const int64_t idx = base + l;
-                float2 c = make_float2(0.0f, 0.0f);
+            for (int i = 0; i < kProjPer; ++i) {
+                const int l = lane + 32 * i;
+                const int64_t idx = gbase + l;
+                v[i] = make_float2(0.0f, 0.0f);
                 if (idx < R.n_points) {
                     SpinorDF d;
                     if constexpr (PREC == 1) {  // hi plane, lo plane
-                        const float4 u = reinterpret_cast<const float4 *>(sm.plane[b][0])[l];
-                        const float4 w = reinterpret_cast<const float4 *>(sm.plane[b][1])[l];
-                        d = SpinorDF{u.x, w.x, u.y, w.y, u.z, w.z, u.w, w.w};
+                        const float4 u = reinterpret_cast<const float4 *>(src)[l];
+                        const float4 q = reinterpret_cast<const float4 *>(src + kProjPlane)[l];
+                        d = SpinorDF{u.x, q.x, u.y, q.y, u.z, q.z, u.w, q.w};
                     } else {  // a plane, b plane
-                        const double2 u = reinterpret_cast<const double2 *>(sm.plane[b][0])[l];
-                        const double2 w = reinterpret_cast<const double2 *>(sm.plane[b][1])[l];
+                        const double2 u = reinterpret_cast<const double2 *>(src)[l];
+                        const double2 q = reinterpret_cast<const double2 *>(src + kProjPlane)[l];
                         split_f64(u.x, d.arh, d.arl);
                         split_f64(u.y, d.aih, d.ail);
-                        split_f64(w.x, d.brh, d.brl);
-                        split_f64(w.y, d.bih, d.bil);
+                        split_f64(q.x, d.brh, d.brl);
+                        split_f64(q.y, d.bih, d.bil);
                     }
-                    c = store_point<PREC>(R.map, idx, project_node<PREC>(R, col, row, d));
+                    v[i] = store_point<PREC>(R.map, idx, project_node<PREC>(R, col, row, d));
                 }
-                sm.red[l] = c;
-                col += kProjThreads;
+                col += 32;
                 while (col >= R.nx) {
                     col -= R.nx;
                     ++row;
                 }
             }
-            granule_sums(sm.red, kProjTile / kGranule, R.partials,
-                         (R.n_points + kGranule - 1) / kGranule,
-                         [&](int g) { return base / kGranule + g; });
+            // granule_sums' tree: s = 128, 64, 32 within the lane, s = 16 .. 1 across lanes
+#pragma unroll
+            for (int s = kProjPer / 2; s > 0; s >>= 1)
+#pragma unroll
+                for (int i = 0; i < s; ++i)
+                    df_add(v[i].x, v[i].y, v[i + s].x, v[i + s].y);
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                const float h = __shfl_down_sync(0xffffffffu, v[0].x, s);
+                const float l = __shfl_down_sync(0xffffffffu, v[0].y, s);
+                if (lane < s)
+                    df_add(v[0].x, v[0].y, h, l);
+            }
+            const int64_t gi = gbase / kGranule;
+            if (lane == 0 && gi < (R.n_points + kGranule - 1) / kGranule)
+                R.partials[gi] = df_to_f64(v[0].x, v[0].y);
         }
-        __syncthreads();  // buffer b and the density slots are free again
-        if (tid == 0 && H + kProjBufs * static_cast<int>(gridDim.x) < total)
-            issue(H + kProjBufs * gridDim.x, b);
+        __syncwarp();  // the warp is done with buffer b
+        if (lane == 0 && Gi + 2 * nw < total)
+            issue(Gi + 2 * nw, b);
     }
 }
 
@@ -625,21 +651,23 @@ cudaError_t launch_project(const EvolveArgs &args, int precision, cudaStream_t s
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // the ring of two tiles is above the 48 KB a kernel gets without asking
+    // the warps' rings are above the 48 KB a kernel gets without asking
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(project_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(sizeof(ProjSmem)));
+                                 kProjSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(project_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(sizeof(ProjSmem)));
+                                 kProjSmem);
     if (e != cudaSuccess)
         return e;
-    const int halves = args.total_tiles * (kTilePoints / kProjTile);
-    const int grid = halves < sms * kProjCtasPerSm ? halves : sms * kProjCtasPerSm;
+    // one CTA per SM, no more warps than granules
+    const int granules = args.total_tiles * (kTilePoints / kGranule);
+    const int need = (granules + kProjWarps - 1) / kProjWarps;
+    const int grid = need < sms ? need : sms;
     if (precision == 1)
-        project_kernel<1><<<grid, kProjThreads, sizeof(ProjSmem), stream>>>(args);
+        project_kernel<1><<<grid, kProjThreads, kProjSmem, stream>>>(args);
     else
-        project_kernel<0><<<grid, kProjThreads, sizeof(ProjSmem), stream>>>(args);
+        project_kernel<0><<<grid, kProjThreads, kProjSmem, stream>>>(args);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,8 @@
-// dsp_strip.cu -- the FP32_MIXED evolve kernel on row strips (schemes EXACT and
-// STRANG_XY, grids whose nx is a multiple of 256).  Shared device code is in
+// dsp_strip.cu -- the FP32_MIXED evolve kernel on row strips (every scheme,
+// grids whose nx is a multiple of 256).  Shared device code is in
 // dsp_device.cuh.
+
+#include <type_traits>
 
 #include "dsp_device.cuh"
 
@@ -8,8 +10,7 @@ namespace dsp {
 namespace {
 
 // ---------------------------------------------------------------------------
-// FP32_MIXED EXACT and STRANG_XY on row strips (grids whose nx is a multiple
-// of 256)
+// FP32_MIXED on row strips (grids whose nx is a multiple of 256)
 //
 // A CTA owns kStripRows = 4 rows x kStripThreads = 256 columns; thread t holds
 // column c0 + t of each of the 4 rows, as 2 packs (rows 0, 1 and rows 2, 3).  A
@@ -19,38 +20,52 @@ namespace {
 // the part that depends on dt P_x alone once per thread and step, as scalars:
 //   EXACT:     rows dt P_y and fl(dt P_y^2); column dt P_x;
 //   STRANG_XY: rows cos(dt P_y) - 1 and sin(dt P_y); column cos(dt P_x) - 1 and
-//              sin(dt P_x) (with dt P_x = 2a of the split).
+//              sin(dt P_x) (with dt P_x = 2a of the split);
+//   MAGNUS4:   rows dt Pbar_y and -fl(dt Pbar_y D_x); column dt Pbar_x (and the
+//              step's D_y, the same for every thread).
 // Every operation on a point is the contiguous path's (same operands, same
 // order, same rounding), so each point's result is bitwise the same on either
 // tiling; only the work per step shrinks (EXACT: 3.5 + dc + ds coefficient
 // lane-ops per spinor-step instead of 8 + dc + ds; STRANG_XY: 3 per spinor plus
-// (4 + dc + ds)/4 per thread instead of 12 + 2 (dc + ds)).
+// (4 + dc + ds)/4 per thread instead of 12 + 2 (dc + ds); MAGNUS4: 7.5 + dc + ds
+// instead of 12 + dc + ds).
 // ---------------------------------------------------------------------------
 
 constexpr int kStripThreads = 256;
 constexpr int kStripRows = 4;
 constexpr int kStripStage = 4096;             // bytes per staged table chunk
-constexpr int kStripChunk = kStripStage / 8;  // steps per chunk (float2 entries)
+constexpr int kStripChunk = kStripStage / 8;  // most steps per chunk (float2 entries)
+
+// Table entries: float2 (dt A_x, dt A_y) per step; MAGNUS4 float4 (dt Abar_x,
+// dt Abar_y, D_x, D_y).
+template <int SCHEME>
+using StripEntry = typename std::conditional<SCHEME == 2, float4, float2>::type;
 static_assert(kStripThreads * kStripRows == kTilePoints, "a strip tile holds kTilePoints points");
 static_assert(kStripThreads == kGranule, "a strip row is one density granule");
 static_assert(kStripThreads == kStripWidth && kStripRows == kStripHeight, "the host's tiling");
 
 struct StripSmem {
-    unsigned char stage[2][kStripStage];  // bulk-copied table entries (dt A_x, dt A_y)
-    float4 rows[kStripChunk][2];          // per step, per pack (rows 0, 1 and 2, 3): see StripRows
-    float ax[kStripChunk];                // per step: dt A_x
+    unsigned char stage[2][kStripStage];  // bulk-copied table entries (StripEntry)
+    float4 rows[kStripChunk][2];          // per step, per pack (rows 0, 1 and 2, 3): strip_row
+    float ax[kStripChunk];                // per step: dt A_x (MAGNUS4: dt Abar_x)
+    float dy[kStripChunk];                // per step, MAGNUS4: D_y
 };
 static_assert(sizeof(StripSmem) <= 48 * 1024, "static shared memory of one CTA");
 
-// The row part of a step for the two rows of a pack, from dt P_y of each:
+// The row part of a step for the two rows of a pack, from dt P_y of each (and,
+// for MAGNUS4, the step's D_x):
 //   EXACT     {P_y(r0), P_y(r1), fl(P_y(r0)^2), fl(P_y(r1)^2)}
-//   STRANG_XY {cy(r0), cy(r1), sb(r0), sb(r1)}, cy = cos b - 1, sb = sin b, b = dt P_y,
-// each as coeffs_group / coeffs_strang_group form it for one lane.
+//   STRANG_XY {cy(r0), cy(r1), sb(r0), sb(r1)}, cy = cos b - 1, sb = sin b, b = dt P_y
+//   MAGNUS4   {P_y(r0), P_y(r1), -fl(P_y(r0) D_x), -fl(P_y(r1) D_x)}
+// each as coeffs_group / coeffs_strang_group / coeffs_magnus_group form it for
+// one lane.
 template <int SCHEME, int DC, int DS>
-__device__ __forceinline__ float4 strip_row(float y0, float y1)
+__device__ __forceinline__ float4 strip_row(float y0, float y1, float dx)
 {
     if constexpr (SCHEME == 0) {
         return make_float4(y0, y1, __fmul_rn(y0, y0), __fmul_rn(y1, y1));
+    } else if constexpr (SCHEME == 2) {
+        return make_float4(y0, y1, -__fmul_rn(y0, dx), -__fmul_rn(y1, dx));
     } else {
         const float x0 = vmul(y0, y0), x1 = vmul(y1, y1);
         const float c0 = vmul(vhorner<float, DC, 1, 0>(x0), x0);
@@ -63,17 +78,20 @@ __device__ __forceinline__ float4 strip_row(float y0, float y1)
 
 // The column part of a step, from dt P_x = dt p_hi + (dt A_x + dt p_lo):
 //   EXACT     a = (P_x, P_x);
-//   STRANG_XY a = (cx, cx), b = (sa, sa): cx = cos 2a - 1, sa = sin 2a, 2a = dt P_x.
+//   STRANG_XY a = (cx, cx), b = (sa, sa): cx = cos 2a - 1, sa = sin 2a, 2a = dt P_x;
+//   MAGNUS4   a = (P_x, P_x), b = (D_y, D_y) (P_x from dt Abar_x).
 struct StripCol {
     float2 a, b;
 };
 
 template <int SCHEME, int DC, int DS>
-__device__ __forceinline__ StripCol strip_col(float pxh, float pxl, float ax)
+__device__ __forceinline__ StripCol strip_col(float pxh, float pxl, float ax, float dy)
 {
     const float px = __fadd_rn(pxh, __fadd_rn(ax, pxl));
     if constexpr (SCHEME == 0) {
         return StripCol{make_float2(px, px), make_float2(0.0f, 0.0f)};
+    } else if constexpr (SCHEME == 2) {
+        return StripCol{make_float2(px, px), make_float2(dy, dy)};
     } else {
         const float xx = vmul(px, px);
         const float cx = vmul(vhorner<float, DC, 1, 0>(xx), xx);
@@ -103,6 +121,21 @@ __device__ __forceinline__ void strip_coeffs_group(const StripCol &c, float4 r, 
     }
 }
 
+// (m, q, q_z) of a MAGNUS4 step for a pack in coeffs_magnus_group's form.
+template <int DC, int DS>
+__device__ __forceinline__ void strip_coeffs_magnus(const StripCol &c, float4 r, float2 &m,
+                                                    float2 &qr, float2 &qi, float2 &qz)
+{
+    const float2 Py = make_float2(r.x, r.y), nyx = make_float2(r.z, r.w);
+    const float2 nz = vfma(c.a, c.b, nyx);
+    const float2 x = vfma(c.a, c.a, vfma(Py, Py, vmul(nz, nz)));
+    m = vmul(vhorner<float2, DC, 1, 0>(x), x);
+    const float2 s1 = vmul(vhorner<float2, DS, 1, 1>(x), x);  // sin|n|/|n| - 1
+    qr = vfma(s1, Py, Py);
+    qi = vfma(s1, c.a, c.a);
+    qz = vfma(s1, nz, nz);
+}
+
 // (m, q) of an EXACT step alone, in coeffs_exact2's form.
 template <int DC, int DS>
 __device__ __forceinline__ void strip_coeffs_exact(const StripCol &c, float4 r, float2 &m,
@@ -123,7 +156,7 @@ struct StripThread {
 
     __device__ __forceinline__ StripCol col(int j) const
     {
-        return strip_col<SCHEME, DC, DS>(pxh, pxl, sm->ax[j]);
+        return strip_col<SCHEME, DC, DS>(pxh, pxl, sm->ax[j], SCHEME == 2 ? sm->dy[j] : 0.0f);
     }
     // one step alone: step_exact2 (EXACT) or step_single_scheme (STRANG_XY)
     __device__ __forceinline__ void single(MixedPack (&pk)[2], int j) const
@@ -135,6 +168,14 @@ struct StripThread {
             if constexpr (SCHEME == 0) {
                 strip_coeffs_exact<DC, DS>(c, sm->rows[j][q], m, qr, qi);
                 apply_exact2(pk[q], m, qr, qi);
+            } else if constexpr (SCHEME == 2) {  // step_magnus2's operations
+                const float4 r = sm->rows[j][q];
+                const float2 Py = make_float2(r.x, r.y), nyx = make_float2(r.z, r.w);
+                const float2 nz = fma2(c.a, c.b, nyx);
+                const float2 x = fma2(c.a, c.a, fma2(Py, Py, mul2(nz, nz)));
+                m = mul2(horner2<DC, 1, 0>(x), x);
+                const float2 sn = horner2<DS, 0, 1>(x);
+                apply2(pk[q], m, neg2(mul2(sn, nz)), mul2(sn, Py), mul2(sn, c.a));
             } else {
                 strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j][q], m, qr, qi);
                 apply_group(pk[q], m, bc2(0.0f), qr, qi);
@@ -153,36 +194,59 @@ struct StripThread {
             pair_apply2(pk[q], m1, q1r, q1i, m2, q2r, q2i);
         }
     }
-    // step_group's chain, both packs advanced step by step
+    // step_group's (step_group_magnus's) chain, both packs advanced step by step
     template <int G>
     __device__ __forceinline__ void group(MixedPack (&pk)[2], int j) const
     {
-        Chain<float2> ch[2];
-        float2 m, qr, qi;
-        StripCol c = col(j);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j][q], m, qr, qi);
-            ch[q].first(m, qr, qi);
-        }
-        c = col(j + 1);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j + 1][q], m, qr, qi);
-            ch[q].second(m, qr, qi);
-        }
-#pragma unroll kGroupUnroll
-        for (int k = 2; k < G; ++k) {
-            c = col(j + k);
+        if constexpr (SCHEME == 2) {
+            MagnusChain<float2> ch[2];
+            float2 m, qr, qi, qz;
+            StripCol c = col(j);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-                strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j + k][q], m, qr, qi);
-                ch[q].next(m, qr, qi);
+                strip_coeffs_magnus<DC, DS>(c, sm->rows[j][q], m, qr, qi, qz);
+                ch[q].first(m, qr, qi, qz);
             }
-        }
+#pragma unroll kGroupUnroll
+            for (int k = 1; k < G; ++k) {
+                c = col(j + k);
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
-            ch[q].finish(pk[q]);
+                for (int q = 0; q < 2; ++q) {
+                    strip_coeffs_magnus<DC, DS>(c, sm->rows[j + k][q], m, qr, qi, qz);
+                    ch[q].next(m, qr, qi, qz);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                ch[q].finish(pk[q]);
+        } else {
+            Chain<float2> ch[2];
+            float2 m, qr, qi;
+            StripCol c = col(j);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j][q], m, qr, qi);
+                ch[q].first(m, qr, qi);
+            }
+            c = col(j + 1);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j + 1][q], m, qr, qi);
+                ch[q].second(m, qr, qi);
+            }
+#pragma unroll kGroupUnroll
+            for (int k = 2; k < G; ++k) {
+                c = col(j + k);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j + k][q], m, qr, qi);
+                    ch[q].next(m, qr, qi);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                ch[q].finish(pk[q]);
+        }
     }
 };
 
@@ -190,21 +254,22 @@ struct StripThread {
 // bulk copy (double buffered, bounded waits), expanded into the row table,
 // then stepped in groups of G aligned to absolute step indices (ragged ends one
 // step at a time, as run_step_groups).  G = 1: every step alone.  EXACT pairs
-// (G = 2) take step_pair2's form; STRANG_XY pairs take the chain, as on the
-// contiguous tiles.
+// (G = 2) take step_pair2's form; STRANG_XY and MAGNUS4 pairs take the chain,
+// as on the contiguous tiles.
 template <int SCHEME, int G, int DC, int DS>
 __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint64_t *bars, int *err,
                                           const StripThread<SCHEME, DC, DS> &th,
                                           const float (&pyh)[kStripRows],
                                           const float (&pyl)[kStripRows], MixedPack (&pk)[2])
 {
-    using St = Stager<float2, kStripStage>;
+    using E = StripEntry<SCHEME>;
+    using St = Stager<E, kStripStage>;
     constexpr int GA = G > St::kAlign ? G : St::kAlign;  // staging starts on a group and 16 bytes
     static_assert(St::kCh % GA == 0, "chunks hold whole groups");
     const int64_t b_al = R.step_begin & ~static_cast<int64_t>(GA - 1);
     if (!table_range_ok(R, b_al, err))
         return false;
-    St st{&sm.stage[0][0], bars, static_cast<const float2 *>(R.table) + b_al, R.step_end - b_al, 0};
+    St st{&sm.stage[0][0], bars, static_cast<const E *>(R.table) + b_al, R.step_end - b_al, 0};
     st.withhold_first = R.withhold_first_copy;
     if (R.step_end <= R.step_begin)
         st.nsteps = 0;
@@ -220,17 +285,22 @@ __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint6
                 st.on_timeout(c, err);
             return false;
         }
-        const float2 *tb = st.stage(c);
+        const E *tb = st.stage(c);
         const int len = st.chunk_len(c);
         // the row table of this chunk, from dt P_y = dt p_hi + (dt A_y + dt p_lo)
         for (int j = threadIdx.x; j < len; j += blockDim.x) {
-            const float2 a = tb[j];
+            const E a = tb[j];
+            float dx = 0.0f;
             sm.ax[j] = a.x;
+            if constexpr (SCHEME == 2) {
+                sm.dy[j] = a.w;
+                dx = a.z;
+            }
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const float y0 = __fadd_rn(pyh[2 * q], __fadd_rn(a.y, pyl[2 * q]));
                 const float y1 = __fadd_rn(pyh[2 * q + 1], __fadd_rn(a.y, pyl[2 * q + 1]));
-                sm.rows[j][q] = strip_row<SCHEME, DC, DS>(y0, y1);
+                sm.rows[j][q] = strip_row<SCHEME, DC, DS>(y0, y1, dx);
             }
         }
         __syncthreads();  // the table is built and stage c & 1 is free again
@@ -385,8 +455,10 @@ __global__ void __launch_bounds__(kStripThreads, kMixedMinBlocks)
         return;
     if (R.scheme == 0)
         dispatch_strip<0, 0>(R, tile, smem, bars, R.err);
-    else
+    else if (R.scheme == 1)
         dispatch_strip<1, 0>(R, tile, smem, bars, R.err);
+    else
+        dispatch_strip<2, 0>(R, tile, smem, bars, R.err);
 }
 
 }  // namespace

@@ -176,36 +176,44 @@ def _strip_vs_contiguous(grid, tab, pieces=None, valley=1, rows=None, segmented=
     return out
 
 
-@pytest.mark.parametrize("scheme", ["exact", "strang_xy"])
+@pytest.mark.parametrize("scheme", ["exact", "strang_xy", "magnus4"])
 @pytest.mark.parametrize("G", sorted(GROUP_STEPS))
 def test_row_strips_bitwise_equal_contiguous_tiles(orc, G, scheme):
-    """FP32-mixed EXACT and STRANG_XY grids whose nx is a multiple of 256 evolve
-    on row strips (4 rows x 256 columns per CTA, the per-step momentum work
-    shared); every group size gives the contiguous tiling's map and density bit
+    """FP32-mixed grids whose nx is a multiple of 256 evolve on row strips (4
+    rows x 256 columns per CTA, the per-step momentum work shared); in every
+    scheme, every group size gives the contiguous tiling's map and density bit
     for bit, on a grid whose last strip hangs over the last row (10 rows), and
     the map meets the oracle."""
     grid = {"nx": 512, "ny": 10, "px": (-4, 4), "py": (-4, 4)}
     pulse = W.sin2_pulse(1.0, 1.55, 5.0, eps=0.4)
     n = GROUP_STEPS[G]
-    tab = B.sample_pulse(pulse, n)
+    sample = B.sample_pulse_gauss if scheme == "magnus4" else B.sample_pulse
+    tab = sample(pulse, n)
     (m1, n1), (m2, n2) = _strip_vs_contiguous(grid, tab, scheme=scheme)
     assert np.array_equal(m1, m2) and n1 == n2
     if G in (1, 16):
-        ref, nref = run_oracle(orc, grid, orc.pulse_table(pulse, n), scheme)
+        if scheme == "magnus4":
+            a, a_in, a_out, dt = orc.pulse_table_gauss(pulse, n)
+            ref, _, _, nref = orc.solve_grid(512, 10, grid["px"], grid["py"], a, dt, a_in,
+                                             a_out, scheme="magnus4")
+        else:
+            ref, nref = run_oracle(orc, grid, orc.pulse_table(pulse, n), scheme)
         assert_close("fp32_mixed", m1, n1, ref, nref)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
-@pytest.mark.parametrize("scheme", ["exact", "strang_xy"])
+@pytest.mark.parametrize("prec,scheme", [("fp64", "exact"), ("fp64", "strang_xy"),
+                                         ("fp32_mixed", "exact"), ("fp32_mixed", "strang_xy"),
+                                         ("fp32_mixed", "magnus4")])
 def test_row_strips_pieces_valley_band_segmented(orc, scheme, prec):
-    """Row strips against contiguous tiles, bit for bit, in both precisions:
-    ragged pieces (steps alone at both ends of each launch, chunk boundaries
-    crossed), valley K-, a band of a larger grid, and the time-parallel solve
-    (segments start from the identity column); the FP64 strips also against the
-    oracle."""
+    """Row strips against contiguous tiles, bit for bit (FP64 MAGNUS4 has no
+    strip path): ragged pieces (steps alone at both ends of each launch, chunk
+    boundaries crossed), valley K-, a band of a larger grid, and the
+    time-parallel solve (segments start from the identity column); the FP64
+    strips also against the oracle."""
     grid = {"nx": 256, "ny": 23, "px": (-3.0, 5.0), "py": (-2.5, 3.5)}
     pulse = W.sin2_pulse(2.0, 1.2, 4.0, eps=0.6)
-    tab = B.sample_pulse(pulse, 5000)
+    sample = B.sample_pulse_gauss if scheme == "magnus4" else B.sample_pulse
+    tab = sample(pulse, 5000)
     for kw in ({"pieces": [299, 5, 3, 4693]}, {"valley": -1, "pieces": [1024, 3976]},
                {"rows": (7, 19)}, {"segmented": True}):
         (m1, n1), (m2, n2) = _strip_vs_contiguous(grid, tab, scheme=scheme, prec=prec, **kw)
