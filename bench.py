@@ -404,7 +404,7 @@ def run_gpu(args):
     # ---- standalone projection of a state on the device (HBM-bound) ----
     projection = None
     if not args.no_projection and rank == 0:
-        projection = projection_leg(args, st_ptr, flush)
+        projection = projection_leg(args, st_ptr)
 
     if rank != 0:
         if world > 1:
@@ -573,14 +573,14 @@ def small_grid_leg(stream, reps=5, warm=3):
 # Standalone projection leg
 # ------------------------------------------------------------------------------------------
 
-def projection_leg(args, stream, flush, reps=10, warm=3):
+def projection_leg(args, stream, reps=10, warm=3):
     """dsp_project of a state already on the device (a launch with no steps), on
     the 4096^2 two-colour grid after 512 steps, in both precisions: the
     projection kernel reads the 32-byte state of every point and writes its map
     value (4 bytes FP32-mixed, 8 bytes FP64), plus one double per 256-point
-    granule of the density sum.  Algorithmic bytes / CUDA-event time of the launch, against the
-    measured HBM copy bandwidth; L2 flushed before every launch (the state alone
-    is 537 MB, four times the L2)."""
+    granule of the density sum.  Algorithmic bytes / CUDA-event time of the
+    launch, against the measured HBM copy bandwidth; the inputs are larger than
+    L2 (the state alone is 537 MB, four times the 129 MB L2), so no flush."""
     import torch
 
     from paper_1607_03062_gb300 import binding as B
@@ -599,7 +599,6 @@ def projection_leg(args, stream, flush, reps=10, warm=3):
         grid.evolve(steps)
         times = []
         for k in range(warm + reps):
-            flush.fill_(float(k))
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)

@@ -335,11 +335,11 @@ struct SpinorDF {
     float arh, arl, aih, ail, brh, brl, bih, bil;
 };
 
+// The same with the node table's entries of the column (cx) and row (cy) given.
 template <int PREC>
-__device__ __forceinline__ float2 project_node(const ReqDesc &R, int64_t col, int64_t row,
-                                               const SpinorDF &v)
+__device__ __forceinline__ float2 project_node_at(const ReqDesc &R, float2 cx, float2 cy,
+                                                  int64_t col, int64_t row, const SpinorDF &v)
 {
-    const float2 cx = R.nodes_out[col], cy = R.nodes_out[R.nx + row];
     if constexpr (PREC == 1) {
         float o;
         if (project_f32(cx.x, cy.x, v.arh, v.aih, v.brh, v.bih, o))
@@ -361,6 +361,13 @@ __device__ __forceinline__ float2 project_node(const ReqDesc &R, int64_t col, in
     float h, l;
     split_f64(c2, h, l);
     return make_float2(h, l);
+}
+
+template <int PREC>
+__device__ __forceinline__ float2 project_node(const ReqDesc &R, int64_t col, int64_t row,
+                                               const SpinorDF &v)
+{
+    return project_node_at<PREC>(R, R.nodes_out[col], R.nodes_out[R.nx + row], col, row, v);
 }
 
 // The map value of a point and its term in the density sum, from |c+|^2 = c.x +

@@ -396,10 +396,11 @@ __global__ void __launch_bounds__(kStrip64Threads, 2)
 
 // Projection of a state already on the device (a launch with no steps).  HBM
 // streaming with no CTA-wide barrier: every warp works on its own granules
-// (256 points: the density's partial-sum unit) through its own ring of two
-// shared-memory buffers.  Lane 0 queues both state planes of a granule (2 x 4
-// KB) by 1-D bulk copy (cp.async.bulk) completing on the buffer's mbarrier, so
-// the next granule's copy is in flight while the warp projects the current one.
+// (256 points: the density's partial-sum unit) through its own ring of
+// shared-memory buffers (ProjShape).  Lane 0 queues both state planes of a
+// granule (2 x 4 KB) by 1-D bulk copy (cp.async.bulk) completing on the
+// buffer's mbarrier; the copies of the other warps on the SM are in flight
+// while one projects (with two buffers a warp also overlaps its own).
 // Lane l holds the granule's points l, l + 32, ..., l + 224: the pairwise tree
 // of granule_sums (slot j plus slot j + s for s = 128, ..., 1) then takes its
 // first three levels inside each lane and the last five across lanes by
@@ -408,28 +409,52 @@ __global__ void __launch_bounds__(kStrip64Threads, 2)
 // same bits.  Per point: 32 bytes of state read, 4 (FP32_MIXED) or 8 (FP64)
 // bytes of map written; FP64-pipe work is one add per point for an FP64 map,
 // none for FP32_MIXED.
-constexpr int kProjWarps = 12;                        // warps per CTA, one CTA per SM
-constexpr int kProjThreads = 32 * kProjWarps;
-constexpr int kProjPer = kGranule / 32;               // points per lane and granule
-constexpr int kProjPlane = kGranule * 16;             // bytes of one state plane of a granule
-constexpr int kProjWarpBytes = 2 * 2 * kProjPlane;    // a warp's two buffers
-constexpr int kProjSmem = kProjWarps * (kProjWarpBytes + 2 * 8);
+// Shape per precision: warps per CTA (one CTA per SM) and buffers per warp's
+// ring.  Measured on a 4096^2 state (us per launch, FP32_MIXED / FP64): 12
+// warps x 2 buffers 109.5 / 258.7, 16 x 1 - / 242.1, 24 x 1 105.7 / 214.0: many
+// warps with one buffer each hide both the copies and the latency of the
+// double-float arithmetic best.
+#ifndef DSP_PROJ32_WARPS
+#define DSP_PROJ32_WARPS 24
+#endif
+#ifndef DSP_PROJ32_BUFS
+#define DSP_PROJ32_BUFS 1
+#endif
+#ifndef DSP_PROJ64_WARPS
+#define DSP_PROJ64_WARPS 24
+#endif
+#ifndef DSP_PROJ64_BUFS
+#define DSP_PROJ64_BUFS 1
+#endif
+template <int PREC>
+struct ProjShape {
+    static constexpr int warps = PREC == 1 ? DSP_PROJ32_WARPS : DSP_PROJ64_WARPS;
+    static constexpr int bufs = PREC == 1 ? DSP_PROJ32_BUFS : DSP_PROJ64_BUFS;
+    static constexpr int threads = 32 * warps;
+    static constexpr int plane = kGranule * 16;          // bytes of one state plane of a granule
+    static constexpr int warp_bytes = bufs * 2 * plane;  // a warp's ring
+    static constexpr int smem = warps * (warp_bytes + bufs * 8);
+};
+constexpr int kProjPer = kGranule / 32;  // points per lane and granule
 static_assert(kTilePoints % kGranule == 0, "tiles hold whole granules");
 
 template <int PREC>
-__global__ void __launch_bounds__(kProjThreads, 1)
+__global__ void __launch_bounds__(ProjShape<PREC>::threads, 1)
     project_kernel(const __grid_constant__ EvolveArgs args)
 {
+    using Sh = ProjShape<PREC>;
+    constexpr int kProjPlane = Sh::plane;
+    constexpr int NB = Sh::bufs;
     extern __shared__ __align__(128) unsigned char proj_dyn[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned char *buf = proj_dyn + w * kProjWarpBytes;  // [buffer][plane][kProjPlane]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(proj_dyn + kProjWarps * kProjWarpBytes) + 2 * w;
+    unsigned char *buf = proj_dyn + w * Sh::warp_bytes;  // [buffer][plane][kProjPlane]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(proj_dyn + Sh::warps * Sh::warp_bytes) + NB * w;
     constexpr int kGranPerTile = kTilePoints / kGranule;
     const int total = args.total_tiles * kGranPerTile;  // granules of the launch
-    const int wid = blockIdx.x * kProjWarps + w, nw = gridDim.x * kProjWarps;
+    const int wid = blockIdx.x * Sh::warps + w, nw = gridDim.x * Sh::warps;
     if (lane == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int b = 0; b < NB; ++b)
+            mbar_init(&bars[b], 1);
         fence_mbar_init();
     }
     __syncwarp();
@@ -451,24 +476,23 @@ __global__ void __launch_bounds__(kProjThreads, 1)
             bulk_load(dst + kProjPlane, st + 16 * (R.n_points + base), bytes, &bars[b]);
         }
     };
-    if (lane == 0) {
-        if (wid < total)
-            issue(wid, 0);
-        if (wid + nw < total)
-            issue(wid + nw, 1);
-    }
+    if (lane == 0)
+        for (int b = 0; b < NB; ++b)
+            if (wid + b * nw < total)
+                issue(wid + b * nw, b);
     int k = 0;
     for (int Gi = wid; Gi < total; Gi += nw, ++k) {
-        const int b = k & 1;
+        const int b = k % NB;
         const int T = Gi / kGranPerTile;
         const ReqDesc &R = args.r[find_request(args, T)];
-        const bool arrived = mbar_wait_bounded(&bars[b], (k >> 1) & 1);
+        const bool arrived = mbar_wait_bounded(&bars[b], (k / NB) & 1);
         if (!__all_sync(0xffffffffu, arrived)) {
-            if (lane == 0) {  // flag it; give the other buffer's copy, if queued, a bounded
-                              // chance to land before the warp leaves
+            if (lane == 0) {  // flag it; give the copies still queued a bounded chance to
+                              // land before the warp leaves
                 atomicOr(R.err, kErrTimeout);
-                if (Gi + nw < total)
-                    (void)mbar_wait_bounded(&bars[b ^ 1], ((k + 1) >> 1) & 1);
+                for (int j = 1; j < NB; ++j)
+                    if (Gi + j * nw < total)
+                        (void)mbar_wait_bounded(&bars[(k + j) % NB], ((k + j) / NB) & 1);
             }
             return;
         }
@@ -476,8 +500,7 @@ __global__ void __launch_bounds__(kProjThreads, 1)
         if (tile_ok(R, tile, R.err)) {
             const int64_t gbase = static_cast<int64_t>(tile) * kTilePoints +
                                   static_cast<int64_t>(Gi % kGranPerTile) * kGranule;
-            // column and row of the granule's first point (one division per granule),
-            // then of this lane's points by stepping
+            // column and row of the granule's first point (one division per granule)
             int64_t col0 = 0, row0 = 0;
             if (lane == 0) {
                 col0 = gbase % R.nx;
@@ -485,38 +508,59 @@ __global__ void __launch_bounds__(kProjThreads, 1)
             }
             col0 = __shfl_sync(0xffffffffu, col0, 0);
             row0 = __shfl_sync(0xffffffffu, row0, 0);
-            int64_t col = col0 + lane, row = row0;
-            while (col >= R.nx) {
-                col -= R.nx;
-                ++row;
-            }
             const unsigned char *src = buf + b * 2 * kProjPlane;
-            float2 v[kProjPer];
-#pragma unroll
-            for (int i = 0; i < kProjPer; ++i) {
-                const int l = lane + 32 * i;
-                const int64_t idx = gbase + l;
-                v[i] = make_float2(0.0f, 0.0f);
-                if (idx < R.n_points) {
-                    SpinorDF d;
-                    if constexpr (PREC == 1) {  // hi plane, lo plane
-                        const float4 u = reinterpret_cast<const float4 *>(src)[l];
-                        const float4 q = reinterpret_cast<const float4 *>(src + kProjPlane)[l];
-                        d = SpinorDF{u.x, q.x, u.y, q.y, u.z, q.z, u.w, q.w};
-                    } else {  // a plane, b plane
-                        const double2 u = reinterpret_cast<const double2 *>(src)[l];
-                        const double2 q = reinterpret_cast<const double2 *>(src + kProjPlane)[l];
-                        split_f64(u.x, d.arh, d.arl);
-                        split_f64(u.y, d.aih, d.ail);
-                        split_f64(q.x, d.brh, d.brl);
-                        split_f64(q.y, d.bih, d.bil);
-                    }
-                    v[i] = store_point<PREC>(R.map, idx, project_node<PREC>(R, col, row, d));
+            // the state of the lane's point l = lane + 32 i, as hi/lo pairs
+            const auto spinor = [&](int l) {
+                SpinorDF d;
+                if constexpr (PREC == 1) {  // hi plane, lo plane
+                    const float4 u = reinterpret_cast<const float4 *>(src)[l];
+                    const float4 q = reinterpret_cast<const float4 *>(src + kProjPlane)[l];
+                    d = SpinorDF{u.x, q.x, u.y, q.y, u.z, q.z, u.w, q.w};
+                } else {  // a plane, b plane
+                    const double2 u = reinterpret_cast<const double2 *>(src)[l];
+                    const double2 q = reinterpret_cast<const double2 *>(src + kProjPlane)[l];
+                    split_f64(u.x, d.arh, d.arl);
+                    split_f64(u.y, d.aih, d.ail);
+                    split_f64(q.x, d.brh, d.brl);
+                    split_f64(q.y, d.bih, d.bil);
                 }
-                col += 32;
+                return d;
+            };
+            float2 v[kProjPer];
+            if (gbase + kGranule <= R.n_points && col0 + kGranule <= R.nx) {
+                // a whole granule inside one row (every grid whose nx is a multiple of 256):
+                // one row node, the column nodes loaded up front, no bounds to check
+                const float2 cy = R.nodes_out[R.nx + row0];
+                float2 cx[kProjPer];
+#pragma unroll
+                for (int i = 0; i < kProjPer; ++i)
+                    cx[i] = R.nodes_out[col0 + lane + 32 * i];
+#pragma unroll
+                for (int i = 0; i < kProjPer; ++i) {
+                    const int l = lane + 32 * i;
+                    v[i] = store_point<PREC>(
+                        R.map, gbase + l,
+                        project_node_at<PREC>(R, cx[i], cy, col0 + l, row0, spinor(l)));
+                }
+            } else {
+                int64_t col = col0 + lane, row = row0;
                 while (col >= R.nx) {
                     col -= R.nx;
                     ++row;
+                }
+#pragma unroll
+                for (int i = 0; i < kProjPer; ++i) {
+                    const int l = lane + 32 * i;
+                    const int64_t idx = gbase + l;
+                    v[i] = make_float2(0.0f, 0.0f);
+                    if (idx < R.n_points)
+                        v[i] = store_point<PREC>(R.map, idx,
+                                                 project_node<PREC>(R, col, row, spinor(l)));
+                    col += 32;
+                    while (col >= R.nx) {
+                        col -= R.nx;
+                        ++row;
+                    }
                 }
             }
             // granule_sums' tree: s = 128, 64, 32 within the lane, s = 16 .. 1 across lanes
@@ -537,8 +581,8 @@ __global__ void __launch_bounds__(kProjThreads, 1)
                 R.partials[gi] = df_to_f64(v[0].x, v[0].y);
         }
         __syncwarp();  // the warp is done with buffer b
-        if (lane == 0 && Gi + 2 * nw < total)
-            issue(Gi + 2 * nw, b);
+        if (lane == 0 && Gi + NB * nw < total)
+            issue(Gi + NB * nw, b);
     }
 }
 
@@ -654,20 +698,21 @@ cudaError_t launch_project(const EvolveArgs &args, int precision, cudaStream_t s
     // the warps' rings are above the 48 KB a kernel gets without asking
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(project_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kProjSmem);
+                                 ProjShape<1>::smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(project_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kProjSmem);
+                                 ProjShape<0>::smem);
     if (e != cudaSuccess)
         return e;
     // one CTA per SM, no more warps than granules
     const int granules = args.total_tiles * (kTilePoints / kGranule);
-    const int need = (granules + kProjWarps - 1) / kProjWarps;
+    const int warps = precision == 1 ? ProjShape<1>::warps : ProjShape<0>::warps;
+    const int need = (granules + warps - 1) / warps;
     const int grid = need < sms ? need : sms;
     if (precision == 1)
-        project_kernel<1><<<grid, kProjThreads, kProjSmem, stream>>>(args);
+        project_kernel<1><<<grid, ProjShape<1>::threads, ProjShape<1>::smem, stream>>>(args);
     else
-        project_kernel<0><<<grid, kProjThreads, kProjSmem, stream>>>(args);
+        project_kernel<0><<<grid, ProjShape<0>::threads, ProjShape<0>::smem, stream>>>(args);
     return cudaGetLastError();
 }
 

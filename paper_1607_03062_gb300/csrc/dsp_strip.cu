@@ -31,6 +31,16 @@ namespace {
 // instead of 12 + dc + ds).
 // ---------------------------------------------------------------------------
 
+// Unroll factors of the strip path (measured on the 2048^2 x 1e5-step LZS
+// solves): the loop over a launch's groups, and the chain inside a group.
+#ifndef DSP_STRIP_GROUP_UNROLL
+#define DSP_STRIP_GROUP_UNROLL 2
+#endif
+#ifndef DSP_STRIP_CHAIN_UNROLL
+#define DSP_STRIP_CHAIN_UNROLL 16
+#endif
+constexpr int kStripGroupUnroll = DSP_STRIP_GROUP_UNROLL;
+constexpr int kStripChainUnroll = DSP_STRIP_CHAIN_UNROLL;
 constexpr int kStripThreads = 256;
 constexpr int kStripRows = 4;
 constexpr int kStripStage = 4096;             // bytes per staged table chunk
@@ -207,7 +217,7 @@ struct StripThread {
                 strip_coeffs_magnus<DC, DS>(c, sm->rows[j][q], m, qr, qi, qz);
                 ch[q].first(m, qr, qi, qz);
             }
-#pragma unroll kGroupUnroll
+#pragma unroll kStripChainUnroll
             for (int k = 1; k < G; ++k) {
                 c = col(j + k);
 #pragma unroll
@@ -234,7 +244,7 @@ struct StripThread {
                 strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j + 1][q], m, qr, qi);
                 ch[q].second(m, qr, qi);
             }
-#pragma unroll kGroupUnroll
+#pragma unroll kStripChainUnroll
             for (int k = 2; k < G; ++k) {
                 c = col(j + k);
 #pragma unroll
@@ -320,7 +330,7 @@ __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint6
                 for (; j + G <= len; j += G)
                     th.pair(pk, j);
             } else {
-#pragma unroll 1
+#pragma unroll kStripGroupUnroll
                 for (; j + G <= len; j += G)
                     th.template group<G>(pk, j);
             }
