@@ -274,13 +274,15 @@ dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info);
  * Use it on small grids: the waits of successive CTA waves add up. */
 dsp_status dsp_test_withhold_next_copy(dsp_grid *g);
 
-/* Test hook (not in the paper): strips = 0 makes the grid's evolve launches use
- * contiguous 1024-point tiles even where it would use row strips (FP32_MIXED
- * EXACT grids whose nx is a multiple of 256: a CTA then owns 4 rows x 256
- * columns and shares the per-step momentum work across them); strips = 1
- * restores the automatic choice.  Both tilings give bitwise the same map and
- * density; the hook exists so that a test can show it. */
-dsp_status dsp_test_tiling(dsp_grid *g, int32_t strips);
+/* Test hook (not in the paper) on the tiling of the grid's evolve launches.
+ * Grids whose nx is a multiple of 256 (FP32_MIXED every scheme, FP64 EXACT and
+ * STRANG_XY) evolve on row strips: a CTA owns 4 rows x 256 columns and shares
+ * the per-step momentum work across them; a launch of one such grid whose last
+ * wave of CTAs would be at most half full runs its last strips 2 rows high.
+ * tiling = 1: that automatic choice (the default); 0: contiguous 1024-point
+ * tiles; 2: row strips, all 4 rows high.  Every tiling gives bitwise the same
+ * map and density; the hook exists so that a test can show it. */
+dsp_status dsp_test_tiling(dsp_grid *g, int32_t tiling);
 
 /* Copies the raw spinor state (dsp_state_bytes bytes) to the host, or back
  * from the host, with the step cursor, for checkpoint / resume.  Synchronise. */

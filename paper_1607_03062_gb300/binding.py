@@ -307,10 +307,11 @@ def test_withhold_next_copy(h: int):
     _check(lib().dsp_test_withhold_next_copy(ctypes.c_void_p(h)), "test_withhold_next_copy")
 
 
-def test_tiling(h: int, strips: bool):
-    """Test hook: False forces contiguous tiles on a grid that would use row
-    strips (the results are bitwise the same either way)."""
-    _check(lib().dsp_test_tiling(ctypes.c_void_p(h), 1 if strips else 0), "test_tiling")
+def test_tiling(h: int, tiling):
+    """Test hook on a grid's tiling: 1 (or True) automatic, 0 (or False)
+    contiguous tiles, 2 row strips without the last-wave split (the results
+    are bitwise the same in every case)."""
+    _check(lib().dsp_test_tiling(ctypes.c_void_p(h), int(tiling)), "test_tiling")
 
 
 def status_string(code: int) -> str:

@@ -1,9 +1,9 @@
 """Builds the in-tree CUDA library ``_build/libdsp.so`` for sm_103a.
 
-Five translation units (the FP32-mixed evolve kernel on contiguous tiles and on
-row strips, the other kernels, the host API, the allocation-free density) are
-compiled in parallel with nvcc, then linked into one shared library with the
-CUDA runtime linked statically.  Host code is compiled without floating-point
+The translation units (the FP32-mixed evolve kernel on contiguous tiles; the
+row-strip kernel, compiled once per scheme and strip height; the other kernels;
+the host API; the allocation-free density) are compiled in parallel with nvcc,
+then linked into one shared library with the CUDA runtime linked statically.  Host code is compiled without floating-point
 contraction, so the host-side arithmetic (pulse tables, projection nodes) rounds
 the same way on every host architecture.
 """
@@ -37,6 +37,24 @@ def sources() -> list[str]:
                                             "dsp_api.cpp", "dsp_noalloc.cu")]
 
 
+# dsp_strip.cu is compiled once per scheme (EXACT, STRANG_XY, MAGNUS4) and strip height
+# (2 packs per thread: 4-row strips; 1: 2-row strips): (object suffix, defines).
+STRIP_VARIANTS = [(f"_s{s}_np{n}", [f"-DDSP_STRIP_SCHEME={s}", f"-DDSP_STRIP_NP={n}"])
+                  for s in (0, 1, 2) for n in (2, 1)]
+
+
+def units() -> list[tuple[str, str, list[str]]]:
+    """(source, object base name, extra defines) of every translation unit."""
+    out = []
+    for src in sources():
+        base = os.path.basename(src)
+        if base == "dsp_strip.cu":
+            out += [(src, base + suffix, defs) for suffix, defs in STRIP_VARIANTS]
+        else:
+            out.append((src, base, []))
+    return out
+
+
 def _stale(lib: str = LIB) -> bool:
     if not os.path.exists(lib):
         return True
@@ -63,9 +81,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
     os.makedirs(os.path.dirname(lib), exist_ok=True)
     nvcc = _nvcc()
     objs, procs = [], []
-    for src in sources():
-        obj = os.path.join(os.path.dirname(lib), os.path.basename(src) + ".o")
-        cmd = [nvcc, "-c", src, "-o", obj] + COMMON + (["-DDSP_BOUNDS_CHECK"] if bounds_check else [])
+    for src, name, defs in units():
+        obj = os.path.join(os.path.dirname(lib), name + ".o")
+        cmd = [nvcc, "-c", src, "-o", obj] + COMMON + defs + (["-DDSP_BOUNDS_CHECK"] if bounds_check else [])
         cmd += ["-Xcompiler", "-ffp-contract=off"]
         if src.endswith(".cu"):
             cmd += ARCH + ["-lineinfo"]

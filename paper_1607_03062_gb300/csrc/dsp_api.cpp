@@ -75,7 +75,7 @@ struct dsp_grid {
     bool fresh = true;      // state not yet written on the device
     bool projected = false;  // partial sums valid for the current pulse
     bool keep_final_state = true;  // dsp_set_keep_final_state
-    bool allow_strips = true;  // test hook dsp_test_tiling
+    int32_t tiling = 1;  // test hook dsp_test_tiling: 0 contiguous, 1 automatic, 2 no tail split
     bool state_stale = false;  // the last launch did not write the final state back
     dsp_status latched = DSP_OK;
 };
@@ -168,7 +168,7 @@ dsp_status check_usable(const dsp_grid *g)
 // Every point's arithmetic is the same on either tiling.
 bool use_strips(const dsp_grid *g)
 {
-    return g->allow_strips && g->nx % dsp::kStripWidth == 0 &&
+    return g->tiling != 0 && g->nx % dsp::kStripWidth == 0 &&
            (g->precision == DSP_FP32_MIXED || g->scheme != DSP_SCHEME_MAGNUS4);
 }
 
@@ -218,6 +218,9 @@ ReqDesc make_desc(const dsp_grid *g, int64_t begin, int64_t end, bool project, v
     r.n_tiles = g->n_tiles;
     // a projection of the state on the device runs on contiguous tiles
     r.strips = use_strips(g) && !(read_only && project) ? 1 : 0;
+    r.strip_h = dsp::kStripHeight;
+    r.strip_row0 = 0;
+    r.tail_split = g->tiling == 1 ? 1 : 0;
     if (r.strips)
         r.n_tiles = strip_tiles(g);
     r.group = g->group;
@@ -237,20 +240,84 @@ bool project_only(const ReqDesc &r)
     return r.step_begin == r.step_end && r.project && !r.fresh && r.nodes_out;
 }
 
+// Wave quantisation of a launch of one grid on row strips.  The strip kernel
+// holds S = SMs x (CTAs per SM) tiles at once; when the grid's T tiles leave a
+// last wave of r = T mod S tiles that is at most half full, the last ceil(r /
+// (nx / 256)) 4-row strips are launched instead as twice as many 2-row strips
+// (strip_h = 2, the same points at half the work per CTA), so that the last
+// wave takes about half as long.  Grids of less than one wave are all 2-row
+// strips.  Every point's arithmetic, and every granule, is unchanged: only
+// which CTA computes which rows.  Returns the descriptors to launch.
+std::vector<ReqDesc> split_last_wave(const ReqDesc &r, int precision)
+{
+    std::vector<ReqDesc> out(1, r);
+    if (!r.strips || !r.tail_split || r.strip_h != dsp::kStripHeight)
+        return out;
+    // per kernel: [0] FP64, [1 + scheme] FP32_MIXED
+    static int sms[4] = {0, 0, 0, 0}, per_sm[4] = {0, 0, 0, 0};
+    const int p = precision == DSP_FP64 ? 0 : 1 + r.scheme;
+    if (sms[p] == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms[p], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            dsp::strip_ctas_per_sm(precision == DSP_FP64 ? 0 : 1, r.scheme, &per_sm[p]) !=
+                cudaSuccess ||
+            per_sm[p] < 1) {
+            cudaGetLastError();
+            sms[p] = -1;
+        }
+    }
+    if (sms[p] <= 0)
+        return out;
+    const int64_t S = static_cast<int64_t>(sms[p]) * per_sm[p];
+    const int64_t ncb = r.nx / dsp::kStripWidth;
+    const int64_t nstrips = (r.ny + dsp::kStripHeight - 1) / dsp::kStripHeight;
+    const int64_t T = ncb * nstrips;
+    const int64_t rem = T % S;
+    if (rem == 0)
+        return out;
+    const int64_t k = std::min<int64_t>(nstrips, (rem + ncb - 1) / ncb);  // strips to halve
+    const int64_t row_tail = dsp::kStripHeight * (nstrips - k);
+    const int64_t tail_tiles = ncb * ((r.ny - row_tail + 1) / 2);
+    if (tail_tiles > S)
+        return out;
+    out.clear();
+    if (nstrips > k) {
+        ReqDesc full = r;
+        full.n_tiles = static_cast<int32_t>(ncb * (nstrips - k));
+        out.push_back(full);
+    }
+    ReqDesc tail = r;
+    tail.strip_h = 2;
+    tail.strip_row0 = static_cast<int32_t>(row_tail);
+    tail.n_tiles = static_cast<int32_t>(tail_tiles);
+    out.push_back(tail);
+    return out;
+}
+
 // Queues launches advancing several requests of one precision.  Requests go to
-// their kernel -- FP64, FP32_MIXED on contiguous tiles, FP32_MIXED on row strips,
-// or the projection kernel when every request only projects -- and are split
-// into launches of at most kMaxReqPerLaunch.  Each request reports device errors
-// in its own error word (ReqDesc::err).
+// their kernel -- FP64 or FP32_MIXED, on contiguous tiles or on row strips, or
+// the projection kernel when every request only projects -- and are split into
+// launches of at most kMaxReqPerLaunch.  Each request reports device errors in
+// its own error word (ReqDesc::err).  A launch of one grid on row strips has its
+// last wave split (split_last_wave).
 cudaError_t launch_requests(const std::vector<ReqDesc> &reqs, int precision, cudaStream_t stream)
 {
     bool proj = !reqs.empty();
     for (const ReqDesc &r : reqs)
         proj = proj && project_only(r);
-    for (int kind = 0; kind < 2; ++kind) {  // contiguous tiles, then row strips
+    std::vector<ReqDesc> split;
+    if (!proj && reqs.size() == 1)
+        split = split_last_wave(reqs[0], precision);
+    const std::vector<ReqDesc> &all = split.empty() ? reqs : split;
+    // kernel kinds: 0 contiguous tiles; 1 + 2 scheme + (strip_h == 2): row strips
+    const auto kind_of = [&](const ReqDesc &r) {
+        return proj || !r.strips ? 0 : 1 + 2 * r.scheme + (r.strip_h == 2 ? 1 : 0);
+    };
+    for (int kind = 0; kind < 7; ++kind) {
         std::vector<const ReqDesc *> sel;
-        for (const ReqDesc &r : reqs)
-            if (proj ? kind == 0 : r.strips == kind)
+        for (const ReqDesc &r : all)
+            if (kind_of(r) == kind)
                 sel.push_back(&r);
         size_t i = 0;
         while (i < sel.size()) {
@@ -276,7 +343,7 @@ cudaError_t launch_requests(const std::vector<ReqDesc> &reqs, int precision, cud
             else if (kind == 0)
                 e = dsp::launch_evolve_mixed(*a, stream);
             else
-                e = dsp::launch_evolve_strip(*a, stream);
+                e = dsp::launch_evolve_strip(*a, (kind - 1) / 2, (kind - 1) % 2 ? 2 : 4, stream);
             if (e != cudaSuccess)
                 return e;
         }
@@ -1021,14 +1088,14 @@ dsp_status dsp_test_withhold_next_copy(dsp_grid *g)
     return DSP_OK;
 }
 
-dsp_status dsp_test_tiling(dsp_grid *g, int32_t strips)
+dsp_status dsp_test_tiling(dsp_grid *g, int32_t tiling)
 {
     dsp_status s = check_usable(g);
     if (s != DSP_OK)
         return s;
-    if (strips != 0 && strips != 1)
+    if (tiling < 0 || tiling > 2)
         return DSP_E_INVALID;
-    g->allow_strips = strips != 0;
+    g->tiling = tiling;
     return DSP_OK;
 }
 

@@ -20,7 +20,7 @@ constexpr int kGranule = 256;
 // Spinors per thread (independent momenta advanced together for ILP).
 constexpr int kSpinorsPerThread = 2;
 constexpr int kThreads = kTilePoints / kSpinorsPerThread;
-// Requests one evolve launch can carry in its parameter block (96 x 216 bytes:
+// Requests one evolve launch can carry in its parameter block (96 x 224 bytes:
 // within the 32 KB kernel-parameter limit).
 constexpr int kMaxReqPerLaunch = 96;
 // Device-side error bits (the launch's error word).
@@ -77,10 +77,15 @@ struct ReqDesc {
                      // compensated update; G = 1 (every step alone), 2, 4, 8 or kGroupMax
     int32_t withhold_first_copy;  // test hook: announce chunk 0 but never copy it, so the
                                   // bounded wait for it runs out (no fault, no hang)
-    int32_t strips;  // EXACT or STRANG_XY with nx a multiple of kStripWidth: CTA tile b is
-                     // rows 4 (b / (nx / 256)) .. + 3, columns 256 (b % (nx / 256)) .. + 255
-                     // (the row-strip path); 0: CTA tile b is points 1024 b .. 1024 b + 1023
-    int32_t pad_;
+    int32_t strips;  // 1: row strips (nx a multiple of kStripWidth): CTA tile b is rows
+                     // strip_row0 + strip_h (b / (nx / 256)) .. + strip_h - 1, columns
+                     // 256 (b % (nx / 256)) .. + 255; 0: CTA tile b is points
+                     // 1024 b .. 1024 b + 1023
+    int32_t strip_h;     // rows per strip: 4, or 2 for the strips that split a launch's
+                         // last wave (the same points, half the work per CTA)
+    int32_t strip_row0;  // first row of this descriptor's strips
+    int32_t tail_split;  // 1: a launch of this request alone may split its last wave
+                         // (host only; see split_last_wave)
     int64_t table_steps;          // entries in the table (checked by bounds-check builds)
 };
 
@@ -136,7 +141,13 @@ struct CombineArgs {
 cudaError_t launch_evolve_f64(const EvolveArgs &args, cudaStream_t stream);
 cudaError_t launch_evolve_f64_strip(const EvolveArgs &args, cudaStream_t stream);
 cudaError_t launch_evolve_mixed(const EvolveArgs &args, cudaStream_t stream);
-cudaError_t launch_evolve_strip(const EvolveArgs &args, cudaStream_t stream);
+// FP32_MIXED row strips: one kernel per scheme and strip height (every request in
+// args has that scheme and strip_h).
+cudaError_t launch_evolve_strip(const EvolveArgs &args, int scheme, int strip_h,
+                                cudaStream_t stream);
+// CTAs of the 4-row strip kernel of a precision (and FP32_MIXED scheme) that one
+// SM holds at once.
+cudaError_t strip_ctas_per_sm(int precision, int scheme, int *ctas);
 // Projection only, of states already on the device: every request in args has
 // step_begin == step_end, project == 1, fresh == 0 and a node table.
 cudaError_t launch_project(const EvolveArgs &args, int precision, cudaStream_t stream);

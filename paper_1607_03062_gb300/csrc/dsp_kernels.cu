@@ -184,9 +184,9 @@ __device__ __forceinline__ double2 strip64_row(double Py)
     }
 }
 
-// One step of the thread's 4 spinors (step_f64's operations).
-template <int SCHEME, int DC, int DS>
-__device__ __forceinline__ void strip64_step(F64Point (&pt)[kStrip64Rows], double tx, double ax,
+// One step of the thread's H spinors (step_f64's operations).
+template <int SCHEME, int DC, int DS, int H>
+__device__ __forceinline__ void strip64_step(F64Point (&pt)[H], double tx, double ax,
                                              const double2 *rows)
 {
     const double Px = tx + ax;  // dt * P_x (times the valley sign)
@@ -197,7 +197,7 @@ __device__ __forceinline__ void strip64_step(F64Point (&pt)[kStrip64Rows], doubl
         sxx = Px * sinc_f64<DS>(xx);
     }
 #pragma unroll
-    for (int k = 0; k < kStrip64Rows; ++k) {
+    for (int k = 0; k < H; ++k) {
         const double2 r = rows[k];
         double c, qr, qi;
         if constexpr (SCHEME == 0) {
@@ -215,7 +215,9 @@ __device__ __forceinline__ void strip64_step(F64Point (&pt)[kStrip64Rows], doubl
     }
 }
 
-template <int SCHEME, int DC, int DS>
+// A strip tile of H rows (4 normally, 2 for the strips that split a launch's last
+// wave, see ReqDesc::strip_h).
+template <int SCHEME, int DC, int DS, int H>
 __device__ void body_strip_f64(const ReqDesc &R, int tile, unsigned char *smem, uint64_t *bars,
                                int *err)
 {
@@ -223,16 +225,17 @@ __device__ void body_strip_f64(const ReqDesc &R, int tile, unsigned char *smem, 
     const int tid = threadIdx.x;
     const int ncb = R.nx / kStrip64Threads;
     const int rb = tile / ncb, cb = tile - rb * ncb;
+    const int64_t row_first = R.strip_row0 + static_cast<int64_t>(rb) * H;
     const int64_t col = static_cast<int64_t>(cb) * kStrip64Threads + tid;
     const double vs = R.valley > 0 ? 1.0 : -1.0;
     double2 *a_plane = static_cast<double2 *>(R.state);
     double2 *b_plane = a_plane + R.n_points;
     const double px = grid_node(R.px_min, R.hx, col);
     const double tx = vs * (R.dt * px);  // valley K- is stepped as K+ on -P
-    F64Point pt[kStrip64Rows];
+    F64Point pt[H];
 #pragma unroll
-    for (int k = 0; k < kStrip64Rows; ++k) {
-        const int64_t row = static_cast<int64_t>(rb) * kStrip64Rows + k;
+    for (int k = 0; k < H; ++k) {
+        const int64_t row = row_first + k;
         const bool valid = row < R.ny;  // the last strip of a grid may hang over its end
         const int64_t idx = row * R.nx + col;
         const double py = grid_node(R.py_min, R.hy, R.row0 + row);
@@ -280,7 +283,7 @@ __device__ void body_strip_f64(const ReqDesc &R, int tile, unsigned char *smem, 
                 const double2 a = tb[j];
                 sm.ax[j] = a.x;
 #pragma unroll
-                for (int k = 0; k < kStrip64Rows; ++k)
+                for (int k = 0; k < H; ++k)
                     sm.rows[j][k] = strip64_row<SCHEME, DC, DS>(pt[k].ty + a.y);
             }
             __syncthreads();  // the table is built and stage c & 1 is free again
@@ -288,7 +291,7 @@ __device__ void body_strip_f64(const ReqDesc &R, int tile, unsigned char *smem, 
                 st.issue(c + 2);
 #pragma unroll 2
             for (int j = 0; j < len; ++j)
-                strip64_step<SCHEME, DC, DS>(pt, tx, sm.ax[j], sm.rows[j]);
+                strip64_step<SCHEME, DC, DS, H>(pt, tx, sm.ax[j], sm.rows[j]);
             __syncthreads();  // everyone is done with the row table
         }
     }
@@ -297,8 +300,8 @@ __device__ void body_strip_f64(const ReqDesc &R, int tile, unsigned char *smem, 
 
     float2 *red = reinterpret_cast<float2 *>(smem);  // the staging memory is free now
 #pragma unroll
-    for (int k = 0; k < kStrip64Rows; ++k) {
-        const int64_t row = static_cast<int64_t>(rb) * kStrip64Rows + k;
+    for (int k = 0; k < H; ++k) {
+        const int64_t row = row_first + k;
         const int64_t idx = row * R.nx + col;
         float2 c = make_float2(0.0f, 0.0f);
         if (row < R.ny) {
@@ -318,19 +321,24 @@ __device__ void body_strip_f64(const ReqDesc &R, int tile, unsigned char *smem, 
         if (R.project)
             red[k * kGranule + tid] = c;
     }
-    if (R.project)  // granule of strip row k: row (rb * 4 + k), columns from cb * 256
-        granule_sums(red, kStrip64Rows, R.partials, (R.n_points + kGranule - 1) / kGranule,
-                     [&](int g) { return (static_cast<int64_t>(rb) * kStrip64Rows + g) * ncb + cb; });
+    if (R.project)  // granule of strip row k: row (row_first + k), columns from cb * 256
+        granule_sums(red, H, R.partials, (R.n_points + kGranule - 1) / kGranule,
+                     [&](int g) { return (row_first + g) * ncb + cb; });
 }
 
 template <int SCHEME, int L>
 __device__ __forceinline__ void dispatch_strip_f64(const ReqDesc &R, int tile, unsigned char *smem,
                                                    uint64_t *bars, int *err)
 {
-    if (R.level == L || L + 1 == kNumLevels)
-        body_strip_f64<SCHEME, kLevelsF64[L].dc, kLevelsF64[L].ds>(R, tile, smem, bars, err);
-    else if constexpr (L + 1 < kNumLevels)
+    if (R.level == L || L + 1 == kNumLevels) {
+        constexpr int DC = kLevelsF64[L].dc, DS = kLevelsF64[L].ds;
+        if (R.strip_h == 2)
+            body_strip_f64<SCHEME, DC, DS, 2>(R, tile, smem, bars, err);
+        else
+            body_strip_f64<SCHEME, DC, DS, kStrip64Rows>(R, tile, smem, bars, err);
+    } else if constexpr (L + 1 < kNumLevels) {
         dispatch_strip_f64<SCHEME, L + 1>(R, tile, smem, bars, err);
+    }
 }
 
 // Block-uniform dispatch on the request's series level (compile-time degrees).
@@ -677,6 +685,40 @@ cudaError_t launch_evolve_f64(const EvolveArgs &args, cudaStream_t stream)
         return cudaSuccess;
     evolve_f64_kernel<<<args.total_tiles, kF64Threads, 0, stream>>>(args);
     return cudaGetLastError();
+}
+
+// The FP32_MIXED strip kernels, one object of dsp_strip.cu each.
+cudaError_t strip_ctas_per_sm_s0_np2(int *ctas);
+cudaError_t strip_ctas_per_sm_s1_np2(int *ctas);
+cudaError_t strip_ctas_per_sm_s2_np2(int *ctas);
+cudaError_t launch_evolve_strip_s0_np2(const EvolveArgs &args, cudaStream_t stream);
+cudaError_t launch_evolve_strip_s0_np1(const EvolveArgs &args, cudaStream_t stream);
+cudaError_t launch_evolve_strip_s1_np2(const EvolveArgs &args, cudaStream_t stream);
+cudaError_t launch_evolve_strip_s1_np1(const EvolveArgs &args, cudaStream_t stream);
+cudaError_t launch_evolve_strip_s2_np2(const EvolveArgs &args, cudaStream_t stream);
+cudaError_t launch_evolve_strip_s2_np1(const EvolveArgs &args, cudaStream_t stream);
+
+cudaError_t strip_ctas_per_sm(int precision, int scheme, int *ctas)
+{
+    if (precision == 1)
+        return scheme == 0   ? strip_ctas_per_sm_s0_np2(ctas)
+               : scheme == 1 ? strip_ctas_per_sm_s1_np2(ctas)
+                             : strip_ctas_per_sm_s2_np2(ctas);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, evolve_f64_strip_kernel,
+                                                         kStrip64Threads, 0);
+}
+
+cudaError_t launch_evolve_strip(const EvolveArgs &args, int scheme, int strip_h,
+                                cudaStream_t stream)
+{
+    const bool half = strip_h == 2;
+    if (scheme == 0)
+        return half ? launch_evolve_strip_s0_np1(args, stream)
+                    : launch_evolve_strip_s0_np2(args, stream);
+    if (scheme == 1)
+        return half ? launch_evolve_strip_s1_np1(args, stream)
+                    : launch_evolve_strip_s1_np2(args, stream);
+    return half ? launch_evolve_strip_s2_np1(args, stream) : launch_evolve_strip_s2_np2(args, stream);
 }
 
 cudaError_t launch_evolve_f64_strip(const EvolveArgs &args, cudaStream_t stream)

@@ -1,6 +1,11 @@
 // dsp_strip.cu -- the FP32_MIXED evolve kernel on row strips (every scheme,
 // grids whose nx is a multiple of 256).  Shared device code is in
 // dsp_device.cuh.
+//
+// Compiled once per scheme and strip height, with -DDSP_STRIP_SCHEME=<0|1|2>
+// (EXACT, STRANG_XY, MAGNUS4) and -DDSP_STRIP_NP=<2|1> (packs per thread: 4-row
+// or 2-row strips), so that the objects build in parallel; each defines its own
+// kernel, launch_evolve_strip_s<SCHEME>_np<NP> and strip_ctas_per_sm_s<SCHEME>_np<NP>.
 
 #include <type_traits>
 
@@ -13,7 +18,9 @@ namespace {
 // FP32_MIXED on row strips (grids whose nx is a multiple of 256)
 //
 // A CTA owns kStripRows = 4 rows x kStripThreads = 256 columns; thread t holds
-// column c0 + t of each of the 4 rows, as 2 packs (rows 0, 1 and rows 2, 3).  A
+// column c0 + t of each of the 4 rows, as 2 packs (rows 0, 1 and rows 2, 3).
+// (A launch's last strips may be 2 rows high, one pack per thread: see
+// ReqDesc::strip_h.)  A
 // thread's spinors share p_x and the CTA's threads share the 4 p_y, so the part
 // of a step's coefficients that depends on dt P_y alone is computed once per row
 // and step into a table in shared memory (built for each chunk of steps), and
@@ -31,13 +38,20 @@ namespace {
 // instead of 12 + dc + ds).
 // ---------------------------------------------------------------------------
 
-// Unroll factors of the strip path (measured on the 2048^2 x 1e5-step LZS
-// solves): the loop over a launch's groups, and the chain inside a group.
+#if !defined(DSP_STRIP_SCHEME) || !defined(DSP_STRIP_NP)
+#error "compile with -DDSP_STRIP_SCHEME=<0|1|2> -DDSP_STRIP_NP=<1|2>"
+#endif
+
+// Unroll factors of the strip path: the loop over a launch's groups, and the
+// chain inside a group.  4-row strips (measured on the 2048^2 x 1e5-step LZS
+// solves, mean ms per solve: x1/x8 272.3, x2/x8 266.8, x1/x16 267.6, x2/x16
+// 264.5, x1/x4 280.3); 2-row strips run only in a launch's last wave and keep
+// a smaller body.
 #ifndef DSP_STRIP_GROUP_UNROLL
-#define DSP_STRIP_GROUP_UNROLL 2
+#define DSP_STRIP_GROUP_UNROLL (DSP_STRIP_NP == 2 ? 2 : 1)
 #endif
 #ifndef DSP_STRIP_CHAIN_UNROLL
-#define DSP_STRIP_CHAIN_UNROLL 16
+#define DSP_STRIP_CHAIN_UNROLL (DSP_STRIP_NP == 2 ? 16 : 8)
 #endif
 constexpr int kStripGroupUnroll = DSP_STRIP_GROUP_UNROLL;
 constexpr int kStripChainUnroll = DSP_STRIP_CHAIN_UNROLL;
@@ -159,7 +173,7 @@ __device__ __forceinline__ void strip_coeffs_exact(const StripCol &c, float4 r, 
     qi = mul2(sn, c.a);
 }
 
-template <int SCHEME, int DC, int DS>
+template <int SCHEME, int DC, int DS, int NP>
 struct StripThread {
     float pxh, pxl;  // dt p_x of the column, hi + lo
     const StripSmem *sm;
@@ -169,11 +183,11 @@ struct StripThread {
         return strip_col<SCHEME, DC, DS>(pxh, pxl, sm->ax[j], SCHEME == 2 ? sm->dy[j] : 0.0f);
     }
     // one step alone: step_exact2 (EXACT) or step_single_scheme (STRANG_XY)
-    __device__ __forceinline__ void single(MixedPack (&pk)[2], int j) const
+    __device__ __forceinline__ void single(MixedPack (&pk)[NP], int j) const
     {
         const StripCol c = col(j);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < NP; ++q) {
             float2 m, qr, qi;
             if constexpr (SCHEME == 0) {
                 strip_coeffs_exact<DC, DS>(c, sm->rows[j][q], m, qr, qi);
@@ -193,11 +207,11 @@ struct StripThread {
         }
     }
     // two EXACT steps multiplied (step_pair2)
-    __device__ __forceinline__ void pair(MixedPack (&pk)[2], int j) const
+    __device__ __forceinline__ void pair(MixedPack (&pk)[NP], int j) const
     {
         const StripCol c0 = col(j), c1 = col(j + 1);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < NP; ++q) {
             float2 m1, q1r, q1i, m2, q2r, q2i;
             strip_coeffs_exact<DC, DS>(c0, sm->rows[j][q], m1, q1r, q1i);
             strip_coeffs_exact<DC, DS>(c1, sm->rows[j + 1][q], m2, q2r, q2i);
@@ -206,14 +220,14 @@ struct StripThread {
     }
     // step_group's (step_group_magnus's) chain, both packs advanced step by step
     template <int G>
-    __device__ __forceinline__ void group(MixedPack (&pk)[2], int j) const
+    __device__ __forceinline__ void group(MixedPack (&pk)[NP], int j) const
     {
         if constexpr (SCHEME == 2) {
-            MagnusChain<float2> ch[2];
+            MagnusChain<float2> ch[NP];
             float2 m, qr, qi, qz;
             StripCol c = col(j);
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < NP; ++q) {
                 strip_coeffs_magnus<DC, DS>(c, sm->rows[j][q], m, qr, qi, qz);
                 ch[q].first(m, qr, qi, qz);
             }
@@ -221,26 +235,26 @@ struct StripThread {
             for (int k = 1; k < G; ++k) {
                 c = col(j + k);
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
+                for (int q = 0; q < NP; ++q) {
                     strip_coeffs_magnus<DC, DS>(c, sm->rows[j + k][q], m, qr, qi, qz);
                     ch[q].next(m, qr, qi, qz);
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
+            for (int q = 0; q < NP; ++q)
                 ch[q].finish(pk[q]);
         } else {
-            Chain<float2> ch[2];
+            Chain<float2> ch[NP];
             float2 m, qr, qi;
             StripCol c = col(j);
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < NP; ++q) {
                 strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j][q], m, qr, qi);
                 ch[q].first(m, qr, qi);
             }
             c = col(j + 1);
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < NP; ++q) {
                 strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j + 1][q], m, qr, qi);
                 ch[q].second(m, qr, qi);
             }
@@ -248,13 +262,13 @@ struct StripThread {
             for (int k = 2; k < G; ++k) {
                 c = col(j + k);
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
+                for (int q = 0; q < NP; ++q) {
                     strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j + k][q], m, qr, qi);
                     ch[q].next(m, qr, qi);
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
+            for (int q = 0; q < NP; ++q)
                 ch[q].finish(pk[q]);
         }
     }
@@ -266,11 +280,11 @@ struct StripThread {
 // step at a time, as run_step_groups).  G = 1: every step alone.  EXACT pairs
 // (G = 2) take step_pair2's form; STRANG_XY and MAGNUS4 pairs take the chain,
 // as on the contiguous tiles.
-template <int SCHEME, int G, int DC, int DS>
+template <int SCHEME, int G, int DC, int DS, int NP>
 __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint64_t *bars, int *err,
-                                          const StripThread<SCHEME, DC, DS> &th,
-                                          const float (&pyh)[kStripRows],
-                                          const float (&pyl)[kStripRows], MixedPack (&pk)[2])
+                                          const StripThread<SCHEME, DC, DS, NP> &th,
+                                          const float (&pyh)[2 * NP],
+                                          const float (&pyl)[2 * NP], MixedPack (&pk)[NP])
 {
     using E = StripEntry<SCHEME>;
     using St = Stager<E, kStripStage>;
@@ -307,7 +321,7 @@ __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint6
                 dx = a.z;
             }
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < NP; ++q) {
                 const float y0 = __fadd_rn(pyh[2 * q], __fadd_rn(a.y, pyl[2 * q]));
                 const float y1 = __fadd_rn(pyh[2 * q + 1], __fadd_rn(a.y, pyl[2 * q + 1]));
                 sm.rows[j][q] = strip_row<SCHEME, DC, DS>(y0, y1, dx);
@@ -342,14 +356,18 @@ __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint6
     return true;
 }
 
-template <int SCHEME, int DC, int DS>
+// A strip tile of NP packs per thread (2 NP rows: 4 normally, 2 for the strips
+// that split a launch's last wave, see ReqDesc::strip_h).
+template <int SCHEME, int DC, int DS, int NP>
 __device__ void body_strip(const ReqDesc &R, int tile, unsigned char *smem, uint64_t *bars,
                            int *err)
 {
+    constexpr int H = 2 * NP;  // rows of the strip
     StripSmem &sm = *reinterpret_cast<StripSmem *>(smem);
     const int tid = threadIdx.x;
     const int ncb = R.nx / kStripThreads;
     const int rb = tile / ncb, cb = tile - rb * ncb;
+    const int64_t row_first = R.strip_row0 + static_cast<int64_t>(rb) * H;
     const int64_t col = static_cast<int64_t>(cb) * kStripThreads + tid;
     const double vs = R.valley > 0 ? 1.0 : -1.0;
     float4 *hi_plane = static_cast<float4 *>(R.state);
@@ -357,15 +375,15 @@ __device__ void body_strip(const ReqDesc &R, int tile, unsigned char *smem, uint
     // valley K- is stepped as K+ on -P: the table holds -dt*A, here -dt*p
     const double px = grid_node(R.px_min, R.hx, col);
     const double tx = vs * (R.dt * px);
-    StripThread<SCHEME, DC, DS> th;
+    StripThread<SCHEME, DC, DS, NP> th;
     th.pxh = static_cast<float>(tx);
     th.pxl = static_cast<float>(tx - static_cast<double>(th.pxh));
     th.sm = &sm;
-    float pyh[kStripRows], pyl[kStripRows];
-    MixedPoint pt[kStripRows];
+    float pyh[H], pyl[H];
+    MixedPoint pt[H];
 #pragma unroll
-    for (int k = 0; k < kStripRows; ++k) {
-        const int64_t row = static_cast<int64_t>(rb) * kStripRows + k;
+    for (int k = 0; k < H; ++k) {
+        const int64_t row = row_first + k;
         const bool valid = row < R.ny;  // the last strip of a grid may hang over its end
         const int64_t idx = row * R.nx + col;
         const double py = grid_node(R.py_min, R.hy, R.row0 + row);
@@ -391,7 +409,10 @@ __device__ void body_strip(const ReqDesc &R, int tile, unsigned char *smem, uint
             pt[k].lar = l.x; pt[k].lai = l.y; pt[k].lbr = l.z; pt[k].lbi = l.w;
         }
     }
-    MixedPack pk[2] = {pack_points(pt[0], pt[1]), pack_points(pt[2], pt[3])};
+    MixedPack pk[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+        pk[q] = pack_points(pt[2 * q], pt[2 * q + 1]);
     bool ok;
     if constexpr (kGroupedLevel<DC, DS>) {
         if (R.group == kGroupMax)
@@ -407,15 +428,16 @@ __device__ void body_strip(const ReqDesc &R, int tile, unsigned char *smem, uint
     } else {  // no group paths at this level (the host keeps G = 1)
         ok = run_strip<SCHEME, 1>(R, sm, bars, err, th, pyh, pyl, pk);
     }
-    unpack_points(pk[0], pt[0], pt[1]);
-    unpack_points(pk[1], pt[2], pt[3]);
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+        unpack_points(pk[q], pt[2 * q], pt[2 * q + 1]);
     if (!ok)
         return;
 
     float2 *red = reinterpret_cast<float2 *>(smem);  // the staging memory is free now
 #pragma unroll
-    for (int k = 0; k < kStripRows; ++k) {
-        const int64_t row = static_cast<int64_t>(rb) * kStripRows + k;
+    for (int k = 0; k < H; ++k) {
+        const int64_t row = row_first + k;
         const int64_t idx = row * R.nx + col;
         float2 c = make_float2(0.0f, 0.0f);
         if (row < R.ny) {
@@ -432,21 +454,24 @@ __device__ void body_strip(const ReqDesc &R, int tile, unsigned char *smem, uint
         if (R.project)
             red[k * kGranule + tid] = c;
     }
-    if (R.project)  // granule of strip row k: row (rb * 4 + k), columns from cb * 256
-        granule_sums(red, kStripRows, R.partials, (R.n_points + kGranule - 1) / kGranule,
-                     [&](int g) { return (static_cast<int64_t>(rb) * kStripRows + g) * ncb + cb; });
+    if (R.project)  // granule of strip row k: row (row_first + k), columns from cb * 256
+        granule_sums(red, H, R.partials, (R.n_points + kGranule - 1) / kGranule,
+                     [&](int g) { return (row_first + g) * ncb + cb; });
 }
 
 template <int SCHEME, int L>
 __device__ __forceinline__ void dispatch_strip(const ReqDesc &R, int tile, unsigned char *smem,
                                                uint64_t *bars, int *err)
 {
-    if (R.level == L || L + 1 == kNumLevels)
-        body_strip<SCHEME, kLevelsF32[L].dc, kLevelsF32[L].ds>(R, tile, smem, bars, err);
-    else if constexpr (L + 1 < kNumLevels)
+    if (R.level == L || L + 1 == kNumLevels) {
+        body_strip<SCHEME, kLevelsF32[L].dc, kLevelsF32[L].ds, DSP_STRIP_NP>(R, tile, smem, bars,
+                                                                            err);
+    } else if constexpr (L + 1 < kNumLevels) {
         dispatch_strip<SCHEME, L + 1>(R, tile, smem, bars, err);
+    }
 }
 
+template <int SCHEME, int NP>
 __global__ void __launch_bounds__(kStripThreads, kMixedMinBlocks)
     evolve_strip_kernel(const __grid_constant__ EvolveArgs args)
 {
@@ -463,21 +488,27 @@ __global__ void __launch_bounds__(kStripThreads, kMixedMinBlocks)
     const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
     if (!tile_ok(R, tile, R.err))
         return;
-    if (R.scheme == 0)
-        dispatch_strip<0, 0>(R, tile, smem, bars, R.err);
-    else if (R.scheme == 1)
-        dispatch_strip<1, 0>(R, tile, smem, bars, R.err);
-    else
-        dispatch_strip<2, 0>(R, tile, smem, bars, R.err);
+    dispatch_strip<SCHEME, 0>(R, tile, smem, bars, R.err);
 }
 
 }  // namespace
 
-cudaError_t launch_evolve_strip(const EvolveArgs &args, cudaStream_t stream)
+#define DSP_CAT4_(a, b, c, d) a##b##c##d
+#define DSP_CAT4(a, b, c, d) DSP_CAT4_(a, b, c, d)
+#define DSP_STRIP_FN(base) DSP_CAT4(base, _s, DSP_STRIP_SCHEME, DSP_CAT4(_np, DSP_STRIP_NP, , ))
+
+cudaError_t DSP_STRIP_FN(strip_ctas_per_sm)(int *ctas)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        ctas, evolve_strip_kernel<DSP_STRIP_SCHEME, DSP_STRIP_NP>, kStripThreads, 0);
+}
+
+cudaError_t DSP_STRIP_FN(launch_evolve_strip)(const EvolveArgs &args, cudaStream_t stream)
 {
     if (args.nreq <= 0 || args.total_tiles <= 0)
         return cudaSuccess;
-    evolve_strip_kernel<<<args.total_tiles, kStripThreads, 0, stream>>>(args);
+    evolve_strip_kernel<DSP_STRIP_SCHEME, DSP_STRIP_NP>
+        <<<args.total_tiles, kStripThreads, 0, stream>>>(args);
     return cudaGetLastError();
 }
 

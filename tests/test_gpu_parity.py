@@ -149,14 +149,16 @@ def test_step_groups_vs_oracle_and_pieces(orc, G, scheme):
 
 def _strip_vs_contiguous(grid, tab, pieces=None, valley=1, rows=None, segmented=False,
                          scheme="exact", prec="fp32_mixed"):
-    """The same grid solved on row-strip tiles and, through the test hook, on
-    contiguous tiles: (map, density) of each."""
+    """The same grid solved on each tiling the test hook selects -- automatic (row
+    strips, the last wave of a launch in 2-row strips), 4-row strips only, and
+    contiguous tiles: (map, density) of each, in that order."""
     out = []
-    for strips in (True, False):
+    for tiling in (1, 2, 0):
         g = B.Grid(grid["nx"], grid["ny"], grid["px"], grid["py"], prec, scheme, valley,
                    rows=rows)
-        B.test_tiling(g.h, strips)
+        B.test_tiling(g.h, tiling)
         info = B.get_info(g.h)
+        strips = tiling != 0
         assert info["n_tiles"] == ((g.nx // 256) * -(-g.ny // 4) if strips
                                    else -(-(g.nx * g.ny) // 1024))
         assert info["row_strips"] == (1 if strips else 0)
@@ -173,7 +175,21 @@ def _strip_vs_contiguous(grid, tab, pieces=None, valley=1, rows=None, segmented=
         torch.cuda.synchronize()
         out.append((m.double().cpu().numpy().copy(), n))
         g.close()
-    return out
+    (m1, n1), (m2, n2), (m3, n3) = out
+    assert np.array_equal(m1, m2) and n1 == n2, "last-wave split vs 4-row strips"
+    return out[0], out[2]
+
+
+def test_last_wave_split_mixes_strip_heights():
+    """A 512 x 700 grid: 350 strip tiles leave a last wave of 46 on this GPU's 304
+    slots, so a launch runs rows 0-607 in 4-row strips and rows 608-699 in 2-row
+    strips; EXACT FP32-mixed in groups of 16, both precisions of EXACT, and
+    STRANG_XY: bitwise the 4-row-only and contiguous results."""
+    grid = {"nx": 512, "ny": 700, "px": (-4, 4), "py": (-4, 4)}
+    tab = B.sample_pulse(W.sin2_pulse(1.0, 1.55, 5.0, eps=0.4), 12000)
+    for prec, scheme in (("fp32_mixed", "exact"), ("fp64", "exact"), ("fp32_mixed", "strang_xy")):
+        (m1, n1), (m2, n2) = _strip_vs_contiguous(grid, tab, scheme=scheme, prec=prec)
+        assert np.array_equal(m1, m2) and n1 == n2, (prec, scheme)
 
 
 @pytest.mark.parametrize("scheme", ["exact", "strang_xy", "magnus4"])
