@@ -53,7 +53,10 @@ typedef int32_t dsp_status;
                               built with -DDSP_BOUNDS_CHECK (accesses are skipped) */
 
 /* Arithmetic of the evolution. */
-#define DSP_FP64 0       /* everything in FP64                                      */
+#define DSP_FP64 0       /* the spinor and its update in FP64; in the EXACT scheme the
+                            small parts cos(theta) - 1 and sin(theta)/theta - 1 are
+                            evaluated in double-float FP32 arithmetic (~1e-19
+                            absolute, below an FP64 ulp of the state)               */
 #define DSP_FP32_MIXED 1 /* spinor in compensated FP32 (hi + lo); dt P_n formed as
                             dt p_hi + (dt A_n + dt p_lo) with dt p an FP32 hi/lo
                             pair and dt A_n one FP32 per step, rounded on the host

@@ -82,6 +82,26 @@ __device__ __forceinline__ void df_add(float &h, float &l, float h2, float l2)
     l = __fadd_rn(e, -__fadd_rn(h, -s));
 }
 
+// (ph, pl) = (ah + al)(bh + bl) to ~2^-46 relative: the high product split
+// exactly by FMA, the cross terms added, then renormalised (Fast2Sum: |p| >= |e|).
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &ph, float &pl)
+{
+    const float p = __fmul_rn(ah, bh);
+    const float e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, __fmaf_rn(ah, bh, -p)));
+    ph = __fadd_rn(p, e);
+    pl = __fadd_rn(e, -__fadd_rn(ph, -p));
+}
+
+// The double c as a hi + lo pair of floats (rounded to nearest; compile time).
+struct DFConst {
+    float h, l;
+};
+__host__ __device__ constexpr DFConst df_const(double c)
+{
+    return DFConst{static_cast<float>(c),
+                   static_cast<float>(c - static_cast<double>(static_cast<float>(c)))};
+}
+
 // Density partial sums, one per granule of kGranule consecutive points (point
 // index / kGranule): red holds n_gran granules of kGranule double-float slots
 // (slot k of a granule = its point k; zero for points past the grid's end).

@@ -17,7 +17,71 @@ struct F64Point {
     double tx, ty;  // dt * p (times the valley sign)
 };
 
-// psi <- U psi for U = [[c, -q], [conj(q), c]] (EXACT and STRANG_XY), in FP64.
+// ---------------------------------------------------------------------------
+// The FP64 EXACT step with its small parts in double-float.
+//
+// GB300's FP64 pipe runs at 1/64 of the FP32 rate (a warp's DFMA holds a
+// scheduler's FP64 unit for ~64 cycles), so only what must accumulate in FP64 is
+// done there: the update psi <- psi + m psi - (q conj ...) and q = dt P + s1 dt P.
+// The small parts m = cos(theta) - 1 and s1 = sin(theta)/theta - 1 of theta^2 =
+// |dt P|^2 are evaluated in double-float FP32 arithmetic (pairs of floats, ~2^-46
+// relative): being small (~theta^2/2, ~theta^2/6), they come out to ~1e-19
+// absolute, far below an FP64 ulp of the state, so the step is FP64-accurate.
+// FP64 operations per spinor-step: 2 (dt P) + 2 (m, s1 to double) + 2 (q) + 12
+// (update) = 18 instead of 18 + dc + ds; the ~100 FP32 operations of the series
+// issue beside them.
+// ---------------------------------------------------------------------------
+
+// dt P squared as a float pair, from the double (split exactly into hi + lo).
+__device__ __forceinline__ float2 square_df(double P)
+{
+    float h, l;
+    split_f64(P, h, l);
+    const float p = __fmul_rn(h, h);
+    const float e = __fmaf_rn(__fadd_rn(h, h), l, __fmaf_rn(h, h, -p));
+    const float sh = __fadd_rn(p, e);
+    return make_float2(sh, __fadd_rn(e, -__fadd_rn(sh, -p)));
+}
+
+// sum_{k=K..D} c_k x^(k-K) in double-float, c_k = (-1)^k / (2k + ODD)!.
+template <int D, int K, int ODD>
+__device__ __forceinline__ void horner_df(float xh, float xl, float &th, float &tl)
+{
+    constexpr DFConst c = df_const(((K & 1) ? -1.0 : 1.0) * inv_factorial<2 * K + ODD>());
+    if constexpr (K == D) {
+        th = c.h;
+        tl = c.l;
+    } else {
+        float uh, ul;
+        horner_df<D, K + 1, ODD>(xh, xl, uh, ul);
+        df_mul(xh, xl, uh, ul, th, tl);
+        df_add(th, tl, c.h, c.l);
+    }
+}
+
+// The FP64 EXACT step: dt P = (Px, Py), their squares as float pairs.
+template <int DC, int DS>
+__device__ __forceinline__ void step_f64_exact(F64Point &s, double Px, double Py, float2 px2,
+                                               float2 py2)
+{
+    float xh = px2.x, xl = px2.y;
+    df_add(xh, xl, py2.x, py2.y);  // theta^2
+    float th, tl, mh, ml, sh, sl;
+    horner_df<DC, 1, 0>(xh, xl, th, tl);  // (cos(theta) - 1) / theta^2
+    df_mul(xh, xl, th, tl, mh, ml);
+    horner_df<DS, 1, 1>(xh, xl, th, tl);  // (sin(theta)/theta - 1) / theta^2
+    df_mul(xh, xl, th, tl, sh, sl);
+    const double m = df_to_f64(mh, ml), s1 = df_to_f64(sh, sl);
+    const double qr = fma(s1, Py, Py), qi = fma(s1, Px, Px);
+    // a' = a + m a - q b ; b' = b + m b + conj(q) a, q = qr + i qi
+    const double nar = fma(m, s.ar, fma(-qr, s.br, fma(qi, s.bi, s.ar)));
+    const double nai = fma(m, s.ai, fma(-qr, s.bi, fma(-qi, s.br, s.ai)));
+    const double nbr = fma(m, s.br, fma(qr, s.ar, fma(qi, s.ai, s.br)));
+    const double nbi = fma(m, s.bi, fma(qr, s.ai, fma(-qi, s.ar, s.bi)));
+    s.ar = nar; s.ai = nai; s.br = nbr; s.bi = nbi;
+}
+
+// psi <- U psi for U = [[c, -q], [conj(q), c]] (STRANG_XY), in FP64.
 __device__ __forceinline__ void apply_f64(F64Point &s, double c, double qr, double qi)
 {
     const double nar = fma(c, s.ar, fma(-qr, s.br, qi * s.bi));
@@ -31,14 +95,12 @@ template <int SCHEME, int DC, int DS>
 __device__ __forceinline__ void step_f64(F64Point &s, double2 a, double2 d)
 {
     const double Px = s.tx + a.x, Py = s.ty + a.y;  // dt * P (times the valley sign)
-    double c, qr, qi, qz = 0.0;
     if constexpr (SCHEME == 0) {
-        const double x = fma(Px, Px, Py * Py);
-        c = cos_f64<DC>(x);
-        const double sn = sinc_f64<DS>(x);
-        qr = sn * Py;
-        qi = sn * Px;
-    } else if constexpr (SCHEME == 1) {
+        step_f64_exact<DC, DS>(s, Px, Py, square_df(Px), square_df(Py));
+        return;
+    }
+    double c, qr, qi, qz = 0.0;
+    if constexpr (SCHEME == 1) {
         const double xx = Px * Px, xy = Py * Py;
         const double cy = cos_f64<DC>(xy);
         c = cy * cos_f64<DC>(xx);
@@ -150,10 +212,10 @@ __device__ void body_f64(const ReqDesc &R, int tile, unsigned char *smem, uint64
 // The tiling of the FP32_MIXED strips (a CTA owns 4 rows x 256 columns, thread
 // t column c0 + t of each row): dt P_x is formed once per thread and step for
 // its 4 spinors, and the dt P_y parts of a step once per row into a table in
-// shared memory (EXACT: dt P_y and dt P_y^2; STRANG_XY: cos(dt P_y) and
-// dt P_y sinc(dt P_y)).  Every operation on a point is step_f64's, so each
-// point's result is bitwise the same on either tiling; FP64 work per spinor-step
-// drops from 18 + dc + ds to 15.25 + dc + ds (EXACT).
+// shared memory (EXACT: dt P_y and dt P_y^2 as a float pair; STRANG_XY:
+// cos(dt P_y) and dt P_y sinc(dt P_y)).  Every operation on a point is
+// step_f64's, so each point's result is bitwise the same on either tiling; FP64
+// work per spinor-step drops from 18 to 16.25 (EXACT).
 // ---------------------------------------------------------------------------
 
 constexpr int kStrip64Threads = kStripWidth;
@@ -172,46 +234,49 @@ static_assert(sizeof(Strip64Smem) <= 48 * 1024, "static shared memory of one CTA
 static_assert(sizeof(Strip64Smem) >= kTilePoints * sizeof(float2), "holds the density slots");
 
 // The row part of a step from dt P_y, as step_f64 forms it:
-//   EXACT {P_y, P_y * P_y};  STRANG_XY {cos(P_y), P_y * sinc(P_y)} (b = dt P_y).
+//   EXACT {P_y, (P_y^2 as a float pair, in the second double's bits)};
+//   STRANG_XY {cos(P_y), P_y * sinc(P_y)} (b = dt P_y).
 template <int SCHEME, int DC, int DS>
 __device__ __forceinline__ double2 strip64_row(double Py)
 {
     if constexpr (SCHEME == 0) {
-        return make_double2(Py, Py * Py);
+        const float2 p2 = square_df(Py);
+        const unsigned long long bits =
+            (static_cast<unsigned long long>(__float_as_uint(p2.y)) << 32) | __float_as_uint(p2.x);
+        return make_double2(Py, __longlong_as_double(static_cast<long long>(bits)));
     } else {
         const double xy = Py * Py;
         return make_double2(cos_f64<DC>(xy), Py * sinc_f64<DS>(xy));
     }
 }
 
-// One step of the thread's H spinors (step_f64's operations).
+// One step of the thread's H spinors (step_f64's operations; SCHEME 0 EXACT, 1
+// STRANG_XY).
 template <int SCHEME, int DC, int DS, int H>
 __device__ __forceinline__ void strip64_step(F64Point (&pt)[H], double tx, double ax,
                                              const double2 *rows)
 {
     const double Px = tx + ax;  // dt * P_x (times the valley sign)
-    [[maybe_unused]] double cxx = 0.0, sxx = 0.0;
-    if constexpr (SCHEME == 1) {
-        const double xx = Px * Px;
-        cxx = cos_f64<DC>(xx);
-        sxx = Px * sinc_f64<DS>(xx);
+    if constexpr (SCHEME == 0) {
+        const float2 px2 = square_df(Px);
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const double2 r = rows[k];
+            const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(r.y));
+            const float2 py2 = make_float2(__uint_as_float(static_cast<unsigned int>(bits)),
+                                           __uint_as_float(static_cast<unsigned int>(bits >> 32)));
+            step_f64_exact<DC, DS>(pt[k], Px, r.x, px2, py2);
+        }
+        return;
     }
+    // STRANG_XY: the column's cos(dt P_x) and dt P_x sinc(dt P_x), then per row
+    const double xx = Px * Px;
+    const double cxx = cos_f64<DC>(xx);
+    const double sxx = Px * sinc_f64<DS>(xx);
 #pragma unroll
     for (int k = 0; k < H; ++k) {
         const double2 r = rows[k];
-        double c, qr, qi;
-        if constexpr (SCHEME == 0) {
-            const double x = fma(Px, Px, r.y);
-            c = cos_f64<DC>(x);
-            const double sn = sinc_f64<DS>(x);
-            qr = sn * r.x;
-            qi = sn * Px;
-        } else {
-            c = r.x * cxx;
-            qr = r.y;
-            qi = r.x * sxx;
-        }
-        apply_f64(pt[k], c, qr, qi);
+        apply_f64(pt[k], r.x * cxx, r.y, r.x * sxx);
     }
 }
 
