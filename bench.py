@@ -192,22 +192,35 @@ def load_peaks():
 # i.e. 20 + dc + ds + 22/G per spinor-step.  Single steps (G = 1): 32 + dc + ds.
 # ------------------------------------------------------------------------------------------
 
-def ops_mixed(dc, ds, group=2, strips=False):
-    """FP32 lane instructions per spinor-step of the FP32-mixed EXACT path.  On row
-    strips (strips=True) the momentum work of a step is shared: each thread forms
-    dt P_x once for its 4 spinors (2 scalar adds: 0.5 per spinor) and reads dt P_y
-    and fl(dt P_y^2) from the strip's row table, so the per-step coefficients cost
-    theta^2 (1) + dc + ds + q (2) + 0.5 = 3.5 + dc + ds instead of 8 + dc + ds (the
-    table itself, 3 operations per row and step for 1024 spinors, is left out)."""
+def tan_norm_degree(group):
+    """Degree of the (1 + y)^(-1/2) series that normalises a tan-normalised group."""
+    return 4 if group >= 16 else 5 if group >= 8 else 6 if group >= 4 else 7
+
+
+def tan_chain_ops(group):
+    """FP32 lane instructions per spinor-step of a tan-normalised group of G steps,
+    past the step's coefficients: the chain (0 for the first step, 6 for the second,
+    9 for each further one) and, once per group, y = det W - 1 (5), its series (DF),
+    the scaled entries (5) and the compensated update (28): 9 + (26 + DF) / G."""
+    return 9 + (26.0 + tan_norm_degree(group)) / group
+
+
+def ops_mixed(dc, ds, group=2, strips=False, tdeg=0):
+    """FP32 lane instructions per spinor-step of the FP32-mixed EXACT path.  Steps one
+    at a time (G = 1): dt P (4) + theta^2 (2) + dc + ds + q (2) + the update (12) and
+    Fast2Sum (12) = 32 + dc + ds.  Tan-normalised groups: dt P (4) + theta^2 (2) +
+    tan(theta)/theta - 1 (tdeg) + tau (2) + tan_chain_ops.  On row strips the
+    momentum work of a step is shared: each thread forms dt P_x once for its 4 spinors
+    (2 scalar adds: 0.5 per spinor) and reads dt P_y and fl(dt P_y^2) from the strip's
+    row table: 4.5 fewer per spinor-step (the table itself, a few operations per row
+    and step for 1024 spinors, is left out)."""
     save = 4.5 if strips else 0.0
     if group == 1:
         return 32 + dc + ds - save
-    if group == 2:
-        return 28.5 + dc + ds - save
-    return 20 + dc + ds + 22.0 / group - save
+    return 8 + tdeg + tan_chain_ops(group) - save
 
 
-def ops_magnus4(dc, ds, group=1, strips=False):
+def ops_magnus4(dc, ds, group=1, strips=False, tdeg=0):
     """FP32 lane instructions per spinor-step of the MAGNUS4 path.  Per step: 4 (Pbar) +
     2 (n_z) + 3 (|n|^2) + dc + ds + 3 (q, q_z).  Single steps: + 16 ((U - I) psi + lo)
     + 12 (Fast2Sum).  Groups of G: + 16 per further step of the chain, 1 to start it,
@@ -220,17 +233,20 @@ def ops_magnus4(dc, ds, group=1, strips=False):
     return 28 + dc + ds + 21.0 / group - save
 
 
-def ops_strang(dc, ds, group=1, strips=False):
-    """FP32 lane instructions per spinor-step of the STRANG_XY path.  Per step: 4 (P) +
-    2 (P_x^2, P_y^2) + 2 dc + 2 ds (cos - 1 and sin/theta - 1 of both) + 5 (sin 2a, sin b,
-    cos b sin 2a, m).  Single steps: + 28 (update, Fast2Sum).  Groups of G: the EXACT
-    chain, + 12 per further step, 10 to start it, 8 + 28 per group.  On row strips the
+def ops_strang(dc, ds, group=1, strips=False, tdeg=0):
+    """FP32 lane instructions per spinor-step of the STRANG_XY path.  Steps one at a
+    time: dt P (4) + P_x^2, P_y^2 (2) + 2 dc + 2 ds (cos - 1 and sin/theta - 1 of both)
+    + 5 (sin 2a, sin b, cos b sin 2a, m) + 28 (update, Fast2Sum); on row strips the
     P_y parts come from the strip's row table and the P_x parts are formed once per
-    thread for its 4 spinors: 3 per spinor (cos b sin 2a, m) + (4 + dc + ds) / 4."""
-    coef = 3 + (4 + dc + ds) / 4.0 if strips else 11 + 2 * (dc + ds)
+    thread for its 4 spinors: 3 per spinor + (4 + dc + ds) / 4.  Tan-normalised
+    groups: dt P (4) + squares (2) + tan b, tan 2a (tdeg + 1 each) + sec 2a - 1 (tdeg)
+    + tau_r (1) = 9 + 3 tdeg, on row strips 1 per spinor + (4 + 2 tdeg) / 4 per thread;
+    then tan_chain_ops."""
     if group == 1:
+        coef = 3 + (4 + dc + ds) / 4.0 if strips else 11 + 2 * (dc + ds)
         return coef + 28
-    return coef + 12 + 22.0 / group
+    coef = 1 + (4 + 2 * tdeg) / 4.0 if strips else 9 + 3 * tdeg
+    return coef + tan_chain_ops(group)
 
 
 def ops_fp64(dc, ds, strips=False):
@@ -322,7 +338,8 @@ def run_gpu(args):
                                         bool(info["row_strips"])))
                 else:
                     ops.append(ops_mixed(info["cos_degree"], info["sinc_degree"],
-                                         info["group_steps"], bool(info["row_strips"])))
+                                         info["group_steps"], bool(info["row_strips"]),
+                                         info["tan_degree"]))
         B.destroy_grid(h)
         del state, mp
         return times, dens, ops
@@ -522,7 +539,7 @@ def scheme_leg(args, cfgs, stream, world, rank, scheme, warm=1, reps=2):
             times.append(e0.elapsed_time(e1) / 1e3)
             info = B.get_info(h)
             ops.append(ops_fn(info["cos_degree"], info["sinc_degree"], info["group_steps"],
-                              bool(info["row_strips"])))
+                              bool(info["row_strips"]), info["tan_degree"]))
     B.destroy_grid(h)
     work = float(n) * n * args.time_steps
     achieved = statistics.mean(o * work / t for o, t in zip(ops, times)) / 1e12

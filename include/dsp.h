@@ -248,9 +248,14 @@ dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps);
  * FP64), theta_max = dt * max|p + A_n| over the box, the tile count, and
  * group_steps G: the number of step operators multiplied into one before each
  * compensated update (FP32_MIXED, every scheme: the largest of 16, 8, 4, 2 with
- * G * theta_max <= 0.2, else 1; 1 in FP64).  Not in the paper: with G > 1 the
- * update is paid once per group, and the group's Re(alpha) - 1 is rebuilt from
- * unitarity, so the applied operator stays unitary to FP32 rounding. */
+ * G * theta_max <= 0.2, else 1; 1 in FP64), and for EXACT and STRANG_XY groups
+ * tan_degree, the degree in theta^2 of the tan(theta)/theta (and sec) series
+ * (0 when G = 1).  Not in the paper: with G > 1 the update is paid once per
+ * group.  EXACT and STRANG_XY groups multiply the steps divided by their real
+ * diagonal cos(theta) (a step then costs 8 multiply-adds instead of 12) and
+ * divide the product by the square root of its determinant; MAGNUS4 groups
+ * multiply the steps themselves and rebuild Re(alpha) - 1 from unitarity.
+ * Either way the applied operator is unitary to FP32 rounding. */
 typedef struct {
     int32_t nx, ny, precision, scheme, valley;
     int32_t cos_degree, sinc_degree;
@@ -261,10 +266,12 @@ typedef struct {
     int32_t row_begin;  /* first global row (0 unless the grid is a band)      */
     int32_t ny_total;   /* rows of the full grid (ny unless the grid is a band) */
     int32_t row_strips; /* 1: evolve launches tile the grid in row strips of 4 rows
-                           x 256 columns (FP32_MIXED EXACT, nx a multiple of 256),
-                           sharing each step's momentum work across a strip;
-                           0: contiguous tiles of 1024 points.  n_tiles counts the
-                           tiles of the tiling in use. */
+                           x 256 columns (nx a multiple of 256; FP32_MIXED every
+                           scheme, FP64 EXACT and STRANG_XY), sharing each step's
+                           momentum work across a strip; 0: contiguous tiles of
+                           1024 points.  n_tiles counts the tiles of the tiling
+                           in use. */
+    int32_t tan_degree; /* see above */
 } dsp_grid_info;
 dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info);
 

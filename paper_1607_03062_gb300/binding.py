@@ -63,7 +63,8 @@ class GridInfo(ctypes.Structure):
         ("n_steps", ctypes.c_int64), ("cursor", ctypes.c_int64), ("dt", ctypes.c_double),
         ("theta_max", ctypes.c_double),
         ("group_steps", ctypes.c_int32), ("row_begin", ctypes.c_int32),
-        ("ny_total", ctypes.c_int32), ("row_strips", ctypes.c_int32)]
+        ("ny_total", ctypes.c_int32), ("row_strips", ctypes.c_int32),
+        ("tan_degree", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):

@@ -70,7 +70,8 @@ struct dsp_grid {
     double dt = 0, a_in[2] = {0, 0}, a_out[2] = {0, 0};
     int32_t level = 0;
     double theta_max = 0.0;
-    int32_t group = 1;  // FP32_MIXED EXACT: steps multiplied per update (choose_group)
+    int32_t group = 1;  // FP32_MIXED: steps multiplied per update (choose_group)
+    int32_t tdeg = 0;   // FP32_MIXED EXACT / STRANG_XY: tan series degree (choose_tan_degree)
     bool withhold_next = false;  // test hook, see dsp_test_withhold_next_copy
     bool fresh = true;      // state not yet written on the device
     bool projected = false;  // partial sums valid for the current pulse
@@ -126,17 +127,42 @@ int32_t choose_level(int32_t precision, double theta, int64_t n_steps)
     return dsp::kNumLevels - 1;
 }
 
+// Degree DT of the tan (STRANG_XY: and sec) series of the tan-normalised groups
+// (FP32_MIXED EXACT and STRANG_XY): the lowest of kTanDegrees whose truncation
+// stays inside the FP32_MIXED budget over the run.  Dropping x^(DT+1) and beyond
+// perturbs the step's rotation angle by ~theta c_(DT+1) x^(DT+1), with a fixed
+// sign, so it adds up over the steps.  0: no degree is enough (groups are not used).
+int32_t choose_tan_degree(int32_t scheme, double theta, int64_t n_steps)
+{
+    const double x = theta * theta;
+    const double budget = 1e-6 / static_cast<double>(std::max<int64_t>(n_steps, 1));
+    for (int i = 0; i < dsp::kNumTanDegrees; ++i) {
+        const int d = dsp::kTanDegrees[i];
+        const double c = scheme == DSP_SCHEME_STRANG_XY
+                             ? std::max(dsp::kTanSeries[d + 1], dsp::kSecSeries[d + 1])
+                             : dsp::kTanSeries[d + 1];
+        if (theta * c * std::pow(x, d + 1) <= budget)
+            return d;
+    }
+    return 0;
+}
+
 // Steps multiplied into one operator before each compensated update (FP32_MIXED,
 // every scheme): the largest G in {16, 8, 4, 2} whose group rotation G *
-// theta_max stays within kGroupAngleMax, else 1.
-int32_t choose_group(int32_t precision, int32_t scheme, int32_t level, double theta_max)
+// theta_max stays within kGroupAngleMax, else 1.  EXACT and STRANG_XY groups need
+// a tan degree (tdeg > 0), MAGNUS4 groups a series level with group code.
+int32_t choose_group(int32_t precision, int32_t scheme, int32_t level, int32_t tdeg,
+                     double theta_max)
 {
-    (void)scheme;
     if (precision != DSP_FP32_MIXED)
         return 1;
-    const dsp::SeriesLevel lv = dsp::kLevelsF32[level];
-    if (lv.dc > dsp::kGroupMaxDegree || lv.ds > dsp::kGroupMaxDegree)
-        return 1;  // the kernels have no group path at this level
+    if (scheme == DSP_SCHEME_MAGNUS4) {
+        const dsp::SeriesLevel lv = dsp::kLevelsF32[level];
+        if (lv.dc > dsp::kGroupMaxDegree || lv.ds > dsp::kGroupMaxDegree)
+            return 1;  // the kernels have no group path at this level
+    } else if (tdeg <= 0) {
+        return 1;
+    }
     for (int32_t G = dsp::kGroupMax; G >= 2; G /= 2)
         if (G * theta_max <= dsp::kGroupAngleMax)
             return G;
@@ -224,6 +250,7 @@ ReqDesc make_desc(const dsp_grid *g, int64_t begin, int64_t end, bool project, v
     if (r.strips)
         r.n_tiles = strip_tiles(g);
     r.group = g->group;
+    r.tdeg = g->tdeg;
     r.withhold_first_copy = g->withhold_next ? 1 : 0;
     r.table_steps = g->table_cap;
     return r;
@@ -669,7 +696,10 @@ dsp_status prepare_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, doub
     g->a_out[1] = a_out[1];
     g->theta_max = tmax;
     g->level = choose_level(g->precision, tmax, n_steps);
-    g->group = choose_group(g->precision, g->scheme, g->level, tmax);
+    g->tdeg = g->precision == DSP_FP32_MIXED && g->scheme != DSP_SCHEME_MAGNUS4
+                  ? choose_tan_degree(g->scheme, tmax, n_steps)
+                  : 0;
+    g->group = choose_group(g->precision, g->scheme, g->level, g->tdeg, tmax);
     g->fresh = true;
     g->projected = false;
     g->state_stale = false;
@@ -1122,6 +1152,7 @@ dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info)
     info->row_begin = g->row0;
     info->ny_total = g->ny_total;
     info->row_strips = use_strips(g) ? 1 : 0;
+    info->tan_degree = g->group > 1 ? g->tdeg : 0;
     return DSP_OK;
 }
 

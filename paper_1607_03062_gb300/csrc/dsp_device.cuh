@@ -152,16 +152,6 @@ __device__ __forceinline__ T horner(T x)
 }
 
 template <int D>
-__device__ __forceinline__ float cosm1_f32(float x)
-{
-    return horner<float, D, 1, 0>(x) * x;
-}
-template <int D>
-__device__ __forceinline__ float sinc_f32(float x)
-{
-    return horner<float, D, 0, 1>(x);
-}
-template <int D>
 __device__ __forceinline__ double cos_f64(double x)
 {
     return horner<double, D, 0, 0>(x);
@@ -413,10 +403,9 @@ __device__ __forceinline__ int find_request(const EvolveArgs &a,
 
 constexpr int kStageBytes = 16384;  // per stage; two stages per CTA
 
-// Tuning constants: unroll factors of the step-pair loop and of the chain inside
-// a step group (measured fastest fully unrolled, although ptxas then keeps a few
-// values in local memory), and spinors per thread of the FP32-mixed kernel (a CTA
-// always owns one 1024-point tile).
+// Tuning constants: unroll factors of the loop over groups of two steps and of
+// the chain inside a step group, and spinors per thread of the FP32-mixed kernel
+// (even: the steps run on FP32x2 pairs; a CTA always owns one 1024-point tile).
 #ifndef DSP_PAIR_UNROLL
 #define DSP_PAIR_UNROLL 2
 #endif
@@ -425,9 +414,6 @@ constexpr int kStageBytes = 16384;  // per stage; two stages per CTA
 #endif
 #ifndef DSP_MIXED_MINB
 #define DSP_MIXED_MINB 2
-#endif
-#ifndef DSP_PACKED_PAIRS
-#define DSP_PACKED_PAIRS 1
 #endif
 #ifndef DSP_GROUP_UNROLL
 #define DSP_GROUP_UNROLL 8
@@ -438,18 +424,19 @@ constexpr int kGroupUnroll = DSP_GROUP_UNROLL;  // chain loop inside one group (
 #define DSP_MAGNUS_GROUP_UNROLL 1
 #endif
 constexpr int kMagnusGroupUnroll = DSP_MAGNUS_GROUP_UNROLL;  // the MAGNUS4 chain's
-// Series levels that can run in step groups.  G >= 2 needs theta_max <= 0.1, where a
-// level above degree kGroupMaxDegree is chosen only for runs of more than ~3e8 steps;
-// the host keeps G = 1 at those levels (choose_group), and no group code is compiled
-// for them.
+// MAGNUS4 series levels that can run in step groups.  G >= 2 needs theta_max <= 0.1,
+// where a level above degree kGroupMaxDegree is chosen only for runs of more than
+// ~3e8 steps; the host keeps G = 1 at those levels (choose_group), and no group code
+// is compiled for them.  (EXACT and STRANG_XY groups use the tan series instead,
+// of degree DT in kTanDegrees.)
 template <int DC, int DS>
 constexpr bool kGroupedLevel = DC <= kGroupMaxDegree && DS <= kGroupMaxDegree;
 constexpr int kMixedSpt = DSP_MIXED_SPT;
 constexpr int kMixedThreads = kTilePoints / kMixedSpt;
 constexpr int kMixedMinBlocks = DSP_MIXED_MINB;  // resident CTAs per SM the registers allow
-constexpr bool kPackedPairs = DSP_PACKED_PAIRS != 0;  // FP32x2 form of the paired path
 constexpr int kF64Threads = kThreads;
 static_assert(kTilePoints % kMixedSpt == 0, "a CTA owns one whole tile");
+static_assert(kMixedSpt % 2 == 0, "FP32x2 pairs of spinors");
 
 // MAGNUS4 table entries: the Gauss-point mean (dt*Abar, valley-signed) and the
 // commutator factor D = -(sqrt(3)/6) dt (A2 - A1) (valley-signed).  FP32_MIXED:
@@ -638,7 +625,7 @@ __device__ __forceinline__ bool run_step_groups(const ReqDesc &R, unsigned char 
 }
 
 // ---------------------------------------------------------------------------
-// FP32_MIXED step
+// FP32_MIXED state of one momentum (loads and stores; the steps run packed)
 // ---------------------------------------------------------------------------
 
 struct MixedPoint {
@@ -647,116 +634,11 @@ struct MixedPoint {
     float pxh, pxl, pyh, pyl;  // dt * p as hi + lo
 };
 
-// Coefficients of U - I = [[cm1 - i qz, -q], [conj(q), cm1 + i qz]], q = qr + i qi,
-// for the step with kinematic momentum dt*P = (Px, Py).  EXACT and STRANG_XY have
-// qz = 0.
-template <int SCHEME, int DC, int DS>
-__device__ __forceinline__ void step_coeffs_f32(float Px, float Py, float2 d, float &cm1,
-                                                float &qr, float &qi, float &qz)
-{
-    if constexpr (SCHEME == 0) {
-        const float x = fmaf(Px, Px, Py * Py);  // theta^2
-        cm1 = cosm1_f32<DC>(x);
-        const float sn = sinc_f32<DS>(x);
-        qr = sn * Py;
-        qi = sn * Px;
-        qz = 0.0f;
-    } else if constexpr (SCHEME == 1) {
-        // e^{-i a sx} e^{-i b sy} e^{-i a sx}, a = dt Px / 2, b = dt Py:
-        //   = [[cos b cos 2a, -(sin b + i cos b sin 2a)], [sin b - i cos b sin 2a, cos b cos 2a]]
-        const float xx = Px * Px, xy = Py * Py;
-        const float cmx = cosm1_f32<DC>(xx), cmy = cosm1_f32<DC>(xy);
-        const float sx = Px * sinc_f32<DS>(xx);
-        cm1 = fmaf(cmx, cmy, cmx) + cmy;
-        qr = Py * sinc_f32<DS>(xy);
-        qi = fmaf(cmy, sx, sx);
-        qz = 0.0f;
-    } else {
-        // MAGNUS4: exp(-i n.sigma), n = (dt Pbar, n_z), n_z = -(sqrt 3/6) (dt P1 x dt P2)_z
-        // = (dt Pbar x D')_z with D' = -(sqrt 3/6) dt (A2 - A1) from the table (the
-        // cross product of the two nearly parallel momenta is never formed).
-        const float nz = fmaf(Px, d.y, -(Py * d.x));
-        const float x = fmaf(Px, Px, fmaf(Py, Py, nz * nz));
-        cm1 = cosm1_f32<DC>(x);
-        const float sn = sinc_f32<DS>(x);
-        qr = sn * Py;
-        qi = sn * Px;
-        qz = sn * nz;
-    }
-}
-
-// psi <- U psi as psi_hi + (U - I) psi_hi + psi_lo, the rounding error of the
-// hi update carried into lo (Fast2Sum).
-template <int SCHEME>
-__device__ __forceinline__ void apply_f32(MixedPoint &s, float cm1, float qr, float qi, float qz)
-{
-    float dar, dai, dbr, dbi;
-    if constexpr (SCHEME == 2) {
-        dar = fmaf(cm1, s.ar, fmaf(qz, s.ai, fmaf(-qr, s.br, fmaf(qi, s.bi, s.lar))));
-        dai = fmaf(cm1, s.ai, fmaf(-qz, s.ar, fmaf(-qr, s.bi, fmaf(-qi, s.br, s.lai))));
-        dbr = fmaf(cm1, s.br, fmaf(-qz, s.bi, fmaf(qr, s.ar, fmaf(qi, s.ai, s.lbr))));
-        dbi = fmaf(cm1, s.bi, fmaf(qz, s.br, fmaf(qr, s.ai, fmaf(-qi, s.ar, s.lbi))));
-    } else {
-        dar = fmaf(cm1, s.ar, fmaf(-qr, s.br, fmaf(qi, s.bi, s.lar)));
-        dai = fmaf(cm1, s.ai, fmaf(-qr, s.bi, fmaf(-qi, s.br, s.lai)));
-        dbr = fmaf(cm1, s.br, fmaf(qr, s.ar, fmaf(qi, s.ai, s.lbr)));
-        dbi = fmaf(cm1, s.bi, fmaf(qr, s.ai, fmaf(-qi, s.ar, s.lbi)));
-    }
-    float t;
-    t = s.ar + dar; s.lar = dar - (t - s.ar); s.ar = t;
-    t = s.ai + dai; s.lai = dai - (t - s.ai); s.ai = t;
-    t = s.br + dbr; s.lbr = dbr - (t - s.br); s.br = t;
-    t = s.bi + dbi; s.lbi = dbi - (t - s.bi); s.bi = t;
-}
-
-// dt*P = dt p_hi + (dt A + dt p_lo), rounded in that order.
-[[maybe_unused]] __device__ __forceinline__ float momentum_f32(float ph, float a, float pl)
-{
-    return __fadd_rn(ph, __fadd_rn(a, pl));
-}
-
-template <int SCHEME, int DC, int DS>
-__device__ __forceinline__ void step_mixed(MixedPoint &p, const float2 &a, float2 d)
-{
-    float cm1, qr, qi, qz;
-    step_coeffs_f32<SCHEME, DC, DS>(momentum_f32(p.pxh, a.x, p.pxl),
-                                    momentum_f32(p.pyh, a.y, p.pyl), d, cm1, qr, qi, qz);
-    apply_f32<SCHEME>(p, cm1, qr, qi, qz);
-}
-
-// Two EXACT steps at once: with U_k = I + [[m_k, -q_k], [conj(q_k), m_k]],
-//   U_2 U_1 - I = [[al - 1, -Q], [conj(Q), conj(al) - 1]],
-//   al - 1 = m1 + m2 + m1 m2 - q2 conj(q1),  Q = q1 + q2 + m2 q1 + m1 q2,
-// applied with one compensated update (the product of two SU(2) steps is SU(2)).
-template <int DC, int DS>
-__device__ __forceinline__ void step_pair_mixed(MixedPoint &p, const float2 &a0, const float2 &a1)
-{
-    float m1, q1r, q1i, m2, q2r, q2i, z;
-    step_coeffs_f32<0, DC, DS>(momentum_f32(p.pxh, a0.x, p.pxl), momentum_f32(p.pyh, a0.y, p.pyl),
-                               make_float2(0.0f, 0.0f), m1, q1r, q1i, z);
-    step_coeffs_f32<0, DC, DS>(momentum_f32(p.pxh, a1.x, p.pxl), momentum_f32(p.pyh, a1.y, p.pyl),
-                               make_float2(0.0f, 0.0f), m2, q2r, q2i, z);
-    const float alm1 = fmaf(m1, m2, m1 + m2) - fmaf(q2r, q1r, q2i * q1i);
-    const float ali = fmaf(q2r, q1i, -(q2i * q1r));
-    const float Qr = fmaf(m2, q1r, q1r) + fmaf(m1, q2r, q2r);
-    const float Qi = fmaf(m2, q1i, q1i) + fmaf(m1, q2i, q2i);
-    const float dar = fmaf(alm1, p.ar, fmaf(-ali, p.ai, fmaf(-Qr, p.br, fmaf(Qi, p.bi, p.lar))));
-    const float dai = fmaf(alm1, p.ai, fmaf(ali, p.ar, fmaf(-Qr, p.bi, fmaf(-Qi, p.br, p.lai))));
-    const float dbr = fmaf(alm1, p.br, fmaf(ali, p.bi, fmaf(Qr, p.ar, fmaf(Qi, p.ai, p.lbr))));
-    const float dbi = fmaf(alm1, p.bi, fmaf(-ali, p.br, fmaf(Qr, p.ai, fmaf(-Qi, p.ar, p.lbi))));
-    float t;
-    t = p.ar + dar; p.lar = dar - (t - p.ar); p.ar = t;
-    t = p.ai + dai; p.lai = dai - (t - p.ai); p.ai = t;
-    t = p.br + dbr; p.lbr = dbr - (t - p.br); p.br = t;
-    t = p.bi + dbi; p.lbi = dbi - (t - p.bi); p.bi = t;
-}
-
 // ---------------------------------------------------------------------------
-// Packed FP32x2 form of the paired EXACT path: lane 0 and lane 1 of every
-// float2 belong to two different momenta, and every operation is the scalar
-// path's operation, in the same order, so each lane's result is bitwise the
-// scalar result (the packed instructions round each lane like the scalar ones).
-// One instruction then issues the arithmetic of two spinors.
+// Packed FP32x2 steps: lane 0 and lane 1 of every float2 belong to two
+// different momenta; each lane is rounded as the scalar FP32 operation would
+// be, so one instruction issues the arithmetic of two spinors and either lane's
+// result is the one-momentum result.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
@@ -868,49 +750,12 @@ __device__ __forceinline__ void step_magnus2(MixedPack &p, const float4 &e)
     apply2(p, m, neg2(mul2(sn, nz)), mul2(sn, Py), mul2(sn, Px));
 }
 
-// The product of two EXACT steps, then one update (step_pair_mixed on two momenta).
-__device__ __forceinline__ void pair_apply2(MixedPack &p, float2 m1, float2 q1r, float2 q1i,
-                                            float2 m2, float2 q2r, float2 q2i)
-{
-    const float2 alm1 = sub2(fma2(m1, m2, add2(m1, m2)), fma2(q2r, q1r, mul2(q2i, q1i)));
-    const float2 ali = fma2(q2r, q1i, neg2(mul2(q2i, q1r)));
-    const float2 Qr = add2(fma2(m2, q1r, q1r), fma2(m1, q2r, q2r));
-    const float2 Qi = add2(fma2(m2, q1i, q1i), fma2(m1, q2i, q2i));
-    apply2(p, alm1, ali, Qr, Qi);
-}
-
-template <int DC, int DS>
-__device__ __forceinline__ void step_pair2(MixedPack &p, const float2 &a0, const float2 &a1)
-{
-    float2 m1, q1r, q1i, m2, q2r, q2i;
-    coeffs_exact2<DC, DS>(p, a0, m1, q1r, q1i);
-    coeffs_exact2<DC, DS>(p, a1, m2, q2r, q2i);
-    pair_apply2(p, m1, q1r, q1i, m2, q2r, q2i);
-}
-
 // ---------------------------------------------------------------------------
-// Groups of G EXACT steps (G = 4, 8), written once for one momentum (V = float,
-// MixedPoint) and for two (V = float2, MixedPack) with non-contracting
-// intrinsics, so both forms perform the same roundings.
-//
-// The product U_k ... U_1 = [[alpha, -Q], [conj(Q), conj(alpha)]] is carried as
-// (Re alpha, Im alpha, Q).  With U_k = [[1 + m, -q], [conj(q), 1 + m]],
-// m = cos(theta_k) - 1, q = sin(theta_k)/theta_k (dt P_y + i dt P_x):
-//   alpha' = alpha + m alpha - q conj(Q),   Q' = Q + m Q + q conj(alpha).
-// No coefficient of the form 1 + (small) is ever rounded: cos(theta) enters as
-// X + m X and sin(theta)/theta as P + (sinc - 1) P, both accurate to the
-// rounding of the small part.  (Rounding cos(theta) itself to FP32 next to 1
-// errs by up to 3e-8 absolute, the same for every step while theta barely
-// changes, and the step angle then carries a relative bias of that size, which
-// grows along the whole evolution.)  Re alpha is held near 1, where FP32
-// resolves it only to ~6e-8; Re alpha - 1 is rebuilt at the end of the group
-// from the other three entries and unitarity, (1 + am)^2 + ai^2 + |Q|^2 = 1, by
-// one Newton step, so the operator applied is unitary to the rounding of its
-// entries.
+// Step groups, written for V = float2 (two momenta per instruction; a V = float
+// instantiation performs the same roundings for one) with non-contracting
+// intrinsics.
 // ---------------------------------------------------------------------------
 
-// Either set of forms can go unused, depending on the build (the float forms serve
-// builds without the packed path: DSP_PACKED_PAIRS=0 or an odd DSP_MIXED_SPT).
 [[maybe_unused]] __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
 [[maybe_unused]] __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
 [[maybe_unused]] __device__ __forceinline__ float vfma(float a, float b, float c)
@@ -942,18 +787,33 @@ __device__ __forceinline__ V vhorner(V x)
         return vfma(vhorner<V, D, K + 1, ODD>(x), x, vbc<V>(c));
 }
 
-// m = cos(theta) - 1 and q = (qr, qi) of one EXACT step at dt P = dt p + table
-// entry a, with q = P + (sinc - 1) P.
-template <int DC, int DS, typename Pt, typename V>
-__device__ __forceinline__ void coeffs_group(const Pt &p, const float2 &a, V &m, V &qr, V &qi)
+// Coefficient sets of the tan-normalised groups (kTanSeries, kSecSeries) and of
+// (1 + y)^(-1/2): c_k = binom(-1/2, k) = prod_{j=1..k} -(2j - 1)/(2j).
+struct TanCoef {
+    __host__ __device__ static constexpr double at(int k) { return kTanSeries[k]; }
+};
+struct SecCoef {
+    __host__ __device__ static constexpr double at(int k) { return kSecSeries[k]; }
+};
+struct RsqrtCoef {
+    __host__ __device__ static constexpr double at(int k)
+    {
+        double c = 1.0;
+        for (int j = 1; j <= k; ++j)
+            c *= -static_cast<double>(2 * j - 1) / static_cast<double>(2 * j);
+        return c;
+    }
+};
+
+// Horner tail sum_{k=K..D} C::at(k) x^(k-K), coefficients rounded once to float.
+template <typename V, typename C, int D, int K>
+__device__ __forceinline__ V vseries(V x)
 {
-    const V Px = vadd(p.pxh, vadd(vbc<V>(a.x), p.pxl));
-    const V Py = vadd(p.pyh, vadd(vbc<V>(a.y), p.pyl));
-    const V x = vfma(Px, Px, vmul(Py, Py));
-    m = vmul(vhorner<V, DC, 1, 0>(x), x);
-    const V s1 = vmul(vhorner<V, DS, 1, 1>(x), x);  // sin(theta)/theta - 1
-    qr = vfma(s1, Py, Py);
-    qi = vfma(s1, Px, Px);
+    constexpr float c = static_cast<float>(C::at(K));
+    if constexpr (K == D)
+        return vbc<V>(c);
+    else
+        return vfma(vseries<V, C, D, K + 1>(x), x, vbc<V>(c));
 }
 
 // Compensated update psi <- psi + d, d = (M - I) psi_hi + psi_lo, for
@@ -976,10 +836,10 @@ __device__ __forceinline__ void apply_group(Pt &p, V am, V ai, V Qr, V Qi)
 // STRANG_XY's merged step X(a) Y(b) X(a), 2a = dt Px, b = dt Py, as m = cos b
 // cos 2a - 1 and q = sin b + i cos b sin 2a, from small parts only:
 // m = cx + cy + cx cy (cx = cos 2a - 1, cy = cos b - 1), sin 2a = Px + (sinc - 1) Px,
-// sin b likewise, cos b sin 2a = sin 2a + cy sin 2a.
+// sin b likewise, cos b sin 2a = sin 2a + cy sin 2a.  (Steps taken one at a time,
+// G = 1.)
 template <int DC, int DS, typename Pt, typename V>
-__device__ __forceinline__ void coeffs_strang_group(const Pt &p, const float2 &a, V &m, V &qr,
-                                                    V &qi)
+__device__ __forceinline__ void coeffs_strang(const Pt &p, const float2 &a, V &m, V &qr, V &qi)
 {
     const V Px = vadd(p.pxh, vadd(vbc<V>(a.x), p.pxl));
     const V Py = vadd(p.pyh, vadd(vbc<V>(a.y), p.pyl));
@@ -991,104 +851,155 @@ __device__ __forceinline__ void coeffs_strang_group(const Pt &p, const float2 &a
     m = vfma(cx, cy, vadd(cx, cy));
 }
 
-// (m, q) of one step of an EXACT-structured scheme: 0 = EXACT, 1 = STRANG_XY.
-template <int SCHEME, int DC, int DS, typename Pt, typename V>
-__device__ __forceinline__ void coeffs_scheme(const Pt &p, const float2 &a, V &m, V &qr, V &qi)
-{
-    if constexpr (SCHEME == 1)
-        coeffs_strang_group<DC, DS>(p, a, m, qr, qi);
-    else
-        coeffs_group<DC, DS>(p, a, m, qr, qi);
-}
-
-// One step alone through the group update (ragged ends of a grouped STRANG_XY
-// run, or all of an ungrouped one): U - I = [[m, -q], [conj(q), m]].
-template <int SCHEME, int DC, int DS, typename Pt>
-__device__ __forceinline__ void step_single_scheme(Pt &p, const float2 &a)
+// One STRANG_XY step alone: U - I = [[m, -q], [conj(q), m]].
+template <int DC, int DS, typename Pt>
+__device__ __forceinline__ void step_strang(Pt &p, const float2 &a)
 {
     using V = decltype(p.ar);
     V m, qr, qi;
-    coeffs_scheme<SCHEME, DC, DS>(p, a, m, qr, qi);
+    coeffs_strang<DC, DS>(p, a, m, qr, qi);
     apply_group(p, m, vbc<V>(0.0f), qr, qi);
 }
 
-// The chain, one step k >= 2 at a time (the second step, with Im alpha still 0,
-// drops its terms):
-//   Re alpha' = Re alpha + m Re alpha - (qr Qr + qi Qi)
-//   Im alpha' = Im alpha + m Im alpha - (qi Qr - qr Qi)
-//   Qr'       = Qr + m Qr + qr Re alpha + qi Im alpha
-//   Qi'       = Qi + m Qi + qi Re alpha - qr Im alpha
-// then Re alpha - 1 rebuilt from unitarity and one compensated update.  Every
-// EXACT-structured group (either tiling) goes through these operations.
-template <typename V>
-struct Chain {
-    V Ar, ai, Qr, Qi;
+// ---------------------------------------------------------------------------
+// Tan-normalised step groups (EXACT and STRANG_XY, G = 2, 4, 8, 16)
+//
+// Both schemes step with a real diagonal: U = [[c, -q], [conj(q), c]], c =
+// cos(theta) (STRANG_XY: cos b cos 2a).  Divided by c a step is
+// N = [[1, -tau], [conj(tau), 1]], tau = q / c, and since its diagonal is 1 a
+// product W = N_k ... N_1 = [[alpha, -Q], [conj(Q), conj(alpha)]] takes 8
+// multiply-adds per step:
+//   alpha' = alpha - tau conj(Q),   Q' = Q + tau conj(alpha).
+// W differs from U_k ... U_1 by the positive factor 1 / (c_1 ... c_k), and
+// det W = |alpha|^2 + |Q|^2 = 1 / (c_1 ... c_k)^2, so the group's operator is
+// W / sqrt(det W).  The chain carries Re alpha - 1 (a small part, never rounded
+// next to 1), Im alpha and Q:
+//   (Re alpha - 1)' = (Re alpha - 1) - (tr Qr + ti Qi)
+//   Im alpha'       = Im alpha - (ti Qr - tr Qi)
+//   Qr'             = Qr + tr Re alpha + ti Im alpha
+//   Qi'             = Qi + ti Re alpha - tr Im alpha
+// (Re alpha = 1 + (Re alpha - 1) rounded once per step for the last two).  At
+// the end y = det W - 1 = 2 (Re alpha - 1) + (Re alpha - 1)^2 + (Im alpha)^2 +
+// |Q|^2 comes from small parts only, f = (1 + y)^(-1/2) - 1 from its binomial
+// series, and the compensated update applies
+//   M - I = [[am + i ai, -Q'], [conj(Q'), am - i ai]],
+//   am = (Re alpha - 1) + f + (Re alpha - 1) f,  ai = Im alpha + f Im alpha,
+//   Q' = Q + f Q,
+// unitary to the rounding of its small entries.  Per step the chain costs 9
+// operations where the product of the U costs 12, and cos(theta) - 1 is never
+// evaluated.
+//   EXACT:     tau = (tan theta / theta)(dt P_y + i dt P_x) = P + (tan theta/theta - 1) P
+//   STRANG_XY: tau = tan b sec 2a + i tan 2a,  b = dt P_y, 2a = dt P_x,
+//              tan b sec 2a = tan b + tan b (sec 2a - 1)
+// A launch that starts or ends inside a group takes those steps as chains of
+// one step each (first, then finish).
+// ---------------------------------------------------------------------------
 
-    __device__ __forceinline__ void first(V m, V qr, V qi)
+template <typename V>
+struct TanChain {
+    V as, ai, Qr, Qi;  // Re alpha - 1, Im alpha, Q
+
+    __device__ __forceinline__ void first(V tr, V ti)
     {
-        Ar = vadd(m, vbc<V>(1.0f));
-        Qr = qr;
-        Qi = qi;
+        as = vbc<V>(0.0f);
+        ai = vbc<V>(0.0f);
+        Qr = tr;
+        Qi = ti;
     }
-    __device__ __forceinline__ void second(V m, V qr, V qi)
+    // the second step (alpha = 1 still)
+    __device__ __forceinline__ void second(V tr, V ti)
     {
-        ai = vfma(vneg(qi), Qr, vmul(qr, Qi));
-        const V nAr = vfma(m, Ar, vfma(vneg(qr), Qr, vfma(vneg(qi), Qi, Ar)));
-        const V nQr = vfma(m, Qr, vfma(qr, Ar, Qr));
-        const V nQi = vfma(m, Qi, vfma(qi, Ar, Qi));
-        Ar = nAr;
-        Qr = nQr;
-        Qi = nQi;
+        as = vfma(vneg(tr), Qr, vmul(vneg(ti), Qi));
+        ai = vfma(vneg(ti), Qr, vmul(tr, Qi));
+        Qr = vadd(Qr, tr);
+        Qi = vadd(Qi, ti);
     }
-    __device__ __forceinline__ void next(V m, V qr, V qi)
+    __device__ __forceinline__ void next(V tr, V ti)
     {
-        const V nAr = vfma(m, Ar, vfma(vneg(qr), Qr, vfma(vneg(qi), Qi, Ar)));
-        const V nai = vfma(m, ai, vfma(vneg(qi), Qr, vfma(qr, Qi, ai)));
-        const V nQr = vfma(m, Qr, vfma(qr, Ar, vfma(qi, ai, Qr)));
-        const V nQi = vfma(m, Qi, vfma(qi, Ar, vfma(vneg(qr), ai, Qi)));
-        Ar = nAr;
+        const V Ar = vadd(as, vbc<V>(1.0f));
+        const V nas = vfma(vneg(tr), Qr, vfma(vneg(ti), Qi, as));
+        const V nai = vfma(vneg(ti), Qr, vfma(tr, Qi, ai));
+        const V nQr = vfma(tr, Ar, vfma(ti, ai, Qr));
+        const V nQi = vfma(ti, Ar, vfma(vneg(tr), ai, Qi));
+        as = nas;
         ai = nai;
         Qr = nQr;
         Qi = nQi;
     }
-    template <typename Pt>
+    template <int DF, typename Pt>
     __device__ __forceinline__ void finish(Pt &p) const
     {
-        V am = vadd(Ar, vbc<V>(-1.0f));  // exact: Re alpha is within [1/2, 2]
-        const V u = vfma(am, am, vfma(Qi, Qi, vfma(Qr, Qr, vfma(ai, ai, vadd(am, am)))));
-        am = vfma(vneg(u), vfma(vbc<V>(-0.5f), am, vbc<V>(0.5f)), am);  // am -= u / (2 (1 + am))
-        apply_group(p, am, ai, Qr, Qi);
+        const V y = vfma(as, as, vfma(Qi, Qi, vfma(Qr, Qr, vfma(ai, ai, vadd(as, as)))));
+        const V f = vmul(vseries<V, RsqrtCoef, DF, 1>(y), y);
+        const V am = vfma(as, f, vadd(as, f));
+        apply_group(p, am, vfma(f, ai, ai), vfma(f, Qr, Qr), vfma(f, Qi, Qi));
     }
 };
 
-template <int G, int DC, int DS, int SCHEME = 0, typename Pt>
-__device__ __forceinline__ void step_group(Pt &p, const float2 *e)
+// tau of one step (contiguous tiles): SCHEME 0 = EXACT, 1 = STRANG_XY.
+template <int SCHEME, int DT, typename Pt, typename V>
+__device__ __forceinline__ void coeffs_tan(const Pt &p, const float2 &a, V &tr, V &ti)
+{
+    const V Px = vadd(p.pxh, vadd(vbc<V>(a.x), p.pxl));
+    const V Py = vadd(p.pyh, vadd(vbc<V>(a.y), p.pyl));
+    if constexpr (SCHEME == 0) {
+        const V x = vfma(Px, Px, vmul(Py, Py));
+        const V t1 = vmul(vseries<V, TanCoef, DT, 1>(x), x);  // tan(theta)/theta - 1
+        tr = vfma(t1, Py, Py);
+        ti = vfma(t1, Px, Px);
+    } else {
+        const V xx = vmul(Px, Px), xy = vmul(Py, Py);
+        const V tb = vfma(vmul(vseries<V, TanCoef, DT, 1>(xy), xy), Py, Py);  // tan b
+        ti = vfma(vmul(vseries<V, TanCoef, DT, 1>(xx), xx), Px, Px);          // tan 2a
+        const V sc = vmul(vseries<V, SecCoef, DT, 1>(xx), xx);                // sec 2a - 1
+        tr = vfma(tb, sc, tb);
+    }
+}
+
+template <int G, int DT, int SCHEME, typename Pt>
+__device__ __forceinline__ void step_group_tan(Pt &p, const float2 *e)
 {
     using V = decltype(p.ar);
-    Chain<V> c;
-    V m, qr, qi;
-    coeffs_scheme<SCHEME, DC, DS>(p, e[0], m, qr, qi);
-    c.first(m, qr, qi);
-    coeffs_scheme<SCHEME, DC, DS>(p, e[1], m, qr, qi);
-    c.second(m, qr, qi);
+    TanChain<V> c;
+    V tr, ti;
+    coeffs_tan<SCHEME, DT>(p, e[0], tr, ti);
+    c.first(tr, ti);
+    coeffs_tan<SCHEME, DT>(p, e[1], tr, ti);
+    c.second(tr, ti);
 #pragma unroll kGroupUnroll
     for (int k = 2; k < G; ++k) {
-        coeffs_scheme<SCHEME, DC, DS>(p, e[k], m, qr, qi);
-        c.next(m, qr, qi);
+        coeffs_tan<SCHEME, DT>(p, e[k], tr, ti);
+        c.next(tr, ti);
     }
-    c.finish(p);
+    c.template finish<kTanNormDegree(G)>(p);
+}
+
+// A step of a grouped run outside whole groups (ragged start or end).
+template <int G, int DT, int SCHEME, typename Pt>
+__device__ __forceinline__ void step_single_tan(Pt &p, const float2 &e)
+{
+    using V = decltype(p.ar);
+    TanChain<V> c;
+    V tr, ti;
+    coeffs_tan<SCHEME, DT>(p, e, tr, ti);
+    c.first(tr, ti);
+    c.template finish<kTanNormDegree(G)>(p);
 }
 
 // MAGNUS4 steps in groups (G = 2, 4, 8, 16).  One step is exp(-i n.sigma) with
 // n = (dt Pbar, n_z): U = [[1 + m - i qz, -q], [conj(q), 1 + m + i qz]], m =
 // cos|n| - 1, (q, qz) = sin|n|/|n| (n_y + i n_x, n_z), formed as n + (sinc - 1) n.
-// The chain is the EXACT one with the sigma_z terms added:
+// The diagonal is not real, so the product U_k ... U_1 = [[alpha, -Q], [conj(Q),
+// conj(alpha)]] is chained as it stands:
 //   Re alpha' = Re alpha + m Re alpha + qz Im alpha - (qr Qr + qi Qi)
 //   Im alpha' = Im alpha + m Im alpha - qz Re alpha - (qi Qr - qr Qi)
 //   Qr'       = Qr + m Qr + qz Qi + qr Re alpha + qi Im alpha
 //   Qi'       = Qi + m Qi - qz Qr + qi Re alpha - qr Im alpha
-// starting from alpha = 1 + m - i qz, Q = q of the group's first step, then the
-// same unitarity rebuild of Re alpha - 1 and compensated update as EXACT groups.
+// starting from alpha = 1 + m - i qz, Q = q of the group's first step.  Re alpha
+// is held near 1, where FP32 resolves it only to ~6e-8, so Re alpha - 1 is
+// rebuilt at the end from the other three entries and unitarity,
+// (1 + am)^2 + ai^2 + |Q|^2 = 1, by one Newton step, before the compensated
+// update.
 template <int DC, int DS, typename Pt, typename V>
 __device__ __forceinline__ void coeffs_magnus_group(const Pt &p, const float4 &e, V &m, V &qr,
                                                     V &qi, V &qz)

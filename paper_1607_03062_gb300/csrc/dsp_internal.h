@@ -20,7 +20,7 @@ constexpr int kGranule = 256;
 // Spinors per thread (independent momenta advanced together for ILP).
 constexpr int kSpinorsPerThread = 2;
 constexpr int kThreads = kTilePoints / kSpinorsPerThread;
-// Requests one evolve launch can carry in its parameter block (96 x 224 bytes:
+// Requests one evolve launch can carry in its parameter block (96 x 232 bytes:
 // within the 32 KB kernel-parameter limit).
 constexpr int kMaxReqPerLaunch = 96;
 // Device-side error bits (the launch's error word).
@@ -41,6 +41,40 @@ constexpr SeriesLevel kLevelsF32[kNumLevels] = {{2, 1}, {2, 2}, {3, 2}, {3, 3},
                                                  {4, 4}, {6, 6}, {9, 9}, {12, 12}};
 constexpr SeriesLevel kLevelsF64[kNumLevels] = {{3, 3}, {4, 3}, {4, 4}, {5, 5},
                                                  {6, 6}, {8, 8}, {11, 11}, {16, 16}};
+
+// FP32_MIXED step groups of EXACT and STRANG_XY divide each step by its real
+// diagonal (the tan-normalised chain of the kernels) and need, in x = theta^2,
+//   tan(theta)/theta = sum_k kTanSeries[k] x^k   (4^(k+1) (4^(k+1) - 1) |B_(2k+2)| / (2k+2)!)
+//   sec(theta)       = sum_k kSecSeries[k] x^k   (|E_2k| / (2k)!)
+// (B: Bernoulli numbers, E: Euler numbers), truncated after x^DT, DT one of
+// kTanDegrees (the lowest whose truncation stays inside the series budget, see
+// choose_tan_degree); and (1 + y)^(-1/2) = sum_k binom(-1/2, k) y^k truncated
+// after y^kTanNormDegree(G) for the group's normalisation.
+constexpr int kTanTerms = 8;
+constexpr double kTanSeries[kTanTerms] = {1.0,
+                                          1.0 / 3.0,
+                                          2.0 / 15.0,
+                                          17.0 / 315.0,
+                                          62.0 / 2835.0,
+                                          1382.0 / 155925.0,
+                                          21844.0 / 6081075.0,
+                                          929569.0 / 638512875.0};
+constexpr double kSecSeries[kTanTerms] = {1.0,
+                                          1.0 / 2.0,
+                                          5.0 / 24.0,
+                                          61.0 / 720.0,
+                                          277.0 / 8064.0,
+                                          50521.0 / 3628800.0,
+                                          540553.0 / 95800320.0,
+                                          199360981.0 / 87178291200.0};
+constexpr int kNumTanDegrees = 5;
+constexpr int kTanDegrees[kNumTanDegrees] = {1, 2, 3, 4, 6};
+// y = det W - 1 <= G tan^2(theta_max) <= 0.04 / G for a group within kGroupAngleMax;
+// the degree keeps the first omitted term below ~1e-14 per group.
+__host__ __device__ constexpr int kTanNormDegree(int G)
+{
+    return G >= 16 ? 4 : G >= 8 ? 5 : G >= 4 ? 6 : 7;
+}
 
 struct ReqDesc {
     // Per step, s = valley (valley K- steps as K+ on -P: its operator is K+'s at -P):
@@ -75,6 +109,8 @@ struct ReqDesc {
     int32_t group;   // FP32_MIXED (every scheme): the steps (G j, ..., G j + G - 1) of
                      // absolute index are multiplied into one operator before one
                      // compensated update; G = 1 (every step alone), 2, 4, 8 or kGroupMax
+    int32_t tdeg;    // FP32_MIXED EXACT / STRANG_XY with G >= 2: degree DT of the tan
+                     // (and sec) series, one of kTanDegrees
     int32_t withhold_first_copy;  // test hook: announce chunk 0 but never copy it, so the
                                   // bounded wait for it runs out (no fault, no hang)
     int32_t strips;  // 1: row strips (nx a multiple of kStripWidth): CTA tile b is rows

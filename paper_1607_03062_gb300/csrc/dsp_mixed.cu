@@ -7,7 +7,119 @@
 namespace dsp {
 namespace {
 
+// The launch's steps on the tile's packs, G = 1 or MAGNUS4 (any G): the series
+// level's degrees (DC, DS) are compile-time constants.
 template <int SCHEME, int DC, int DS>
+__device__ __forceinline__ bool run_level(const ReqDesc &R, unsigned char *smem, uint64_t *bars,
+                                          int *err, MixedPack (&pk)[kMixedSpt / 2])
+{
+    constexpr int NP = kMixedSpt / 2;
+    if constexpr (SCHEME == 2) {
+        const auto single = [&](const float4 &e) {
+#pragma unroll
+            for (int k = 0; k < NP; ++k)
+                step_magnus2<DC, DS>(pk[k], e);
+        };
+        if constexpr (kGroupedLevel<DC, DS>) {
+            const auto group = [&](auto gc, const float4 *e) {
+#pragma unroll
+                for (int k = 0; k < NP; ++k)
+                    step_group_magnus<decltype(gc)::value, DC, DS>(pk[k], e);
+            };
+            if (R.group == kGroupMax)
+                return run_step_groups<float4, kGroupMax>(R, smem, bars, err, single, [&](const float4 *e) {
+                    group(std::integral_constant<int, kGroupMax>{}, e);
+                });
+            if (R.group == 8)
+                return run_step_groups<float4, 8>(R, smem, bars, err, single, [&](const float4 *e) {
+                    group(std::integral_constant<int, 8>{}, e);
+                });
+            if (R.group == 4)
+                return run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
+                    group(std::integral_constant<int, 4>{}, e);
+                });
+            if (R.group == 2)
+                return run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
+                    group(std::integral_constant<int, 2>{}, e);
+                });
+        }
+        return run_steps<float4>(R, smem, bars, err, single);
+    } else {
+        return run_steps<float2>(R, smem, bars, err, [&](const float2 &e) {
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                if constexpr (SCHEME == 0)
+                    step_exact2<DC, DS>(pk[k], e);
+                else
+                    step_strang<DC, DS>(pk[k], e);
+            }
+        });
+    }
+}
+
+template <int SCHEME, int L>
+__device__ __forceinline__ bool dispatch_level(const ReqDesc &R, unsigned char *smem,
+                                               uint64_t *bars, int *err,
+                                               MixedPack (&pk)[kMixedSpt / 2])
+{
+    if constexpr (L + 1 < kNumLevels) {
+        if (R.level != L)
+            return dispatch_level<SCHEME, L + 1>(R, smem, bars, err, pk);
+    }
+    return run_level<SCHEME, kLevelsF32[L].dc, kLevelsF32[L].ds>(R, smem, bars, err, pk);
+}
+
+// EXACT / STRANG_XY in tan-normalised groups of G steps, tan series of degree DT.
+template <int SCHEME, int G, int DT>
+__device__ __forceinline__ bool run_tan(const ReqDesc &R, unsigned char *smem, uint64_t *bars,
+                                        int *err, MixedPack (&pk)[kMixedSpt / 2])
+{
+    constexpr int NP = kMixedSpt / 2;
+    return run_step_groups<float2, G>(
+        R, smem, bars, err,
+        [&](const float2 &e) {
+#pragma unroll
+            for (int k = 0; k < NP; ++k)
+                step_single_tan<G, DT, SCHEME>(pk[k], e);
+        },
+        [&](const float2 *e) {
+#pragma unroll
+            for (int k = 0; k < NP; ++k)
+                step_group_tan<G, DT, SCHEME>(pk[k], e);
+        });
+}
+
+template <int SCHEME, int G, int I>
+__device__ __forceinline__ bool dispatch_tan_degree(const ReqDesc &R, unsigned char *smem,
+                                                    uint64_t *bars, int *err,
+                                                    MixedPack (&pk)[kMixedSpt / 2])
+{
+    constexpr int DT = kTanDegrees[I];
+    if constexpr (I + 1 < kNumTanDegrees) {
+        if (R.tdeg != DT)
+            return dispatch_tan_degree<SCHEME, G, I + 1>(R, smem, bars, err, pk);
+    }
+    return run_tan<SCHEME, G, DT>(R, smem, bars, err, pk);
+}
+
+template <int SCHEME>
+__device__ __forceinline__ bool run_mixed(const ReqDesc &R, unsigned char *smem, uint64_t *bars,
+                                          int *err, MixedPack (&pk)[kMixedSpt / 2])
+{
+    if constexpr (SCHEME != 2) {
+        if (R.group == kGroupMax)
+            return dispatch_tan_degree<SCHEME, kGroupMax, 0>(R, smem, bars, err, pk);
+        if (R.group == 8)
+            return dispatch_tan_degree<SCHEME, 8, 0>(R, smem, bars, err, pk);
+        if (R.group == 4)
+            return dispatch_tan_degree<SCHEME, 4, 0>(R, smem, bars, err, pk);
+        if (R.group == 2)
+            return dispatch_tan_degree<SCHEME, 2, 0>(R, smem, bars, err, pk);
+    }
+    return dispatch_level<SCHEME, 0>(R, smem, bars, err, pk);
+}
+
+template <int SCHEME>
 __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint64_t *bars,
                            int *err)
 {
@@ -53,209 +165,14 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
         }
     }
 
-    constexpr bool packed = kPackedPairs && S % 2 == 0;
-    MixedPack pk[packed ? S / 2 : 1];
-    if constexpr (packed) {  // FP32x2: spinors (2k, 2k + 1) share each instruction
+    MixedPack pk[S / 2];  // FP32x2: spinors (2k, 2k + 1) share each instruction
 #pragma unroll
-        for (int k = 0; k < S / 2; ++k)
-            pk[k] = pack_points(pt[2 * k], pt[2 * k + 1]);
-    }
-    bool ok;
-    if constexpr (SCHEME == 0 && packed) {
-        const auto single = [&](const float2 &e) {
+    for (int k = 0; k < S / 2; ++k)
+        pk[k] = pack_points(pt[2 * k], pt[2 * k + 1]);
+    const bool ok = run_mixed<SCHEME>(R, smem, bars, err, pk);
 #pragma unroll
-            for (int k = 0; k < S / 2; ++k)
-                step_exact2<DC, DS>(pk[k], e);
-        };
-        if constexpr (kGroupedLevel<DC, DS>) {
-            if (R.group == kGroupMax) {
-                ok = run_step_groups<float2, kGroupMax>(R, smem, bars, err, single,
-                                                        [&](const float2 *e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_group<kGroupMax, DC, DS>(pk[k], e);
-                });
-            } else if (R.group == 8) {
-                ok = run_step_groups<float2, 8>(R, smem, bars, err, single, [&](const float2 *e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_group<8, DC, DS>(pk[k], e);
-                });
-            } else if (R.group == 4) {
-                ok = run_step_groups<float2, 4>(R, smem, bars, err, single, [&](const float2 *e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_group<4, DC, DS>(pk[k], e);
-                });
-            } else if (R.group == 2) {
-                ok = run_step_groups<float2, 2>(R, smem, bars, err, single, [&](const float2 *e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_pair2<DC, DS>(pk[k], e[0], e[1]);
-                });
-            } else {
-                ok = run_steps<float2>(R, smem, bars, err, single);
-            }
-        } else {  // no group paths at this level (the host keeps G = 1)
-            ok = run_steps<float2>(R, smem, bars, err, single);
-        }
-    } else if constexpr (SCHEME == 1 && packed) {
-        const auto single = [&](const float2 &e) {
-#pragma unroll
-            for (int k = 0; k < S / 2; ++k)
-                step_single_scheme<1, DC, DS>(pk[k], e);
-        };
-        if constexpr (kGroupedLevel<DC, DS>) {
-            if (R.group == kGroupMax) {
-                ok = run_step_groups<float2, kGroupMax>(R, smem, bars, err, single,
-                                                        [&](const float2 *e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_group<kGroupMax, DC, DS, 1>(pk[k], e);
-                });
-            } else if (R.group == 8) {
-                ok = run_step_groups<float2, 8>(R, smem, bars, err, single, [&](const float2 *e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_group<8, DC, DS, 1>(pk[k], e);
-                });
-            } else if (R.group == 4) {
-                ok = run_step_groups<float2, 4>(R, smem, bars, err, single, [&](const float2 *e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_group<4, DC, DS, 1>(pk[k], e);
-                });
-            } else if (R.group == 2) {
-                ok = run_step_groups<float2, 2>(R, smem, bars, err, single, [&](const float2 *e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_group<2, DC, DS, 1>(pk[k], e);
-                });
-            } else {
-                ok = run_steps<float2>(R, smem, bars, err, single);
-            }
-        } else {  // no group paths at this level (the host keeps G = 1)
-            ok = run_steps<float2>(R, smem, bars, err, single);
-        }
-    } else if constexpr (SCHEME == 2 && packed) {
-        const auto single = [&](const float4 &e) {
-#pragma unroll
-            for (int k = 0; k < S / 2; ++k)
-                step_magnus2<DC, DS>(pk[k], e);
-        };
-        if constexpr (kGroupedLevel<DC, DS>) {
-            if (R.group == kGroupMax) {
-                ok = run_step_groups<float4, kGroupMax>(R, smem, bars, err, single,
-                                                        [&](const float4 *e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_group_magnus<kGroupMax, DC, DS>(pk[k], e);
-                });
-            } else if (R.group == 8) {
-                ok = run_step_groups<float4, 8>(R, smem, bars, err, single, [&](const float4 *e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_group_magnus<8, DC, DS>(pk[k], e);
-                });
-            } else if (R.group == 4) {
-                ok = run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_group_magnus<4, DC, DS>(pk[k], e);
-                });
-            } else if (R.group == 2) {
-                ok = run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
-#pragma unroll
-                    for (int k = 0; k < S / 2; ++k)
-                        step_group_magnus<2, DC, DS>(pk[k], e);
-                });
-            } else {
-                ok = run_steps<float4>(R, smem, bars, err, single);
-            }
-        } else {  // no group paths at this level (the host keeps G = 1)
-            ok = run_steps<float4>(R, smem, bars, err, single);
-        }
-    } else if constexpr (SCHEME == 0) {
-        const auto single = [&](const float2 &e) {
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-                step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
-        };
-        if constexpr (kGroupedLevel<DC, DS>) {
-            if (R.group == kGroupMax) {
-                ok = run_step_groups<float2, kGroupMax>(R, smem, bars, err, single,
-                                                        [&](const float2 *e) {
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        step_group<kGroupMax, DC, DS>(pt[s], e);
-                });
-            } else if (R.group == 8) {
-                ok = run_step_groups<float2, 8>(R, smem, bars, err, single, [&](const float2 *e) {
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        step_group<8, DC, DS>(pt[s], e);
-                });
-            } else if (R.group == 4) {
-                ok = run_step_groups<float2, 4>(R, smem, bars, err, single, [&](const float2 *e) {
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        step_group<4, DC, DS>(pt[s], e);
-                });
-            } else if (R.group == 2) {
-                ok = run_step_groups<float2, 2>(R, smem, bars, err, single, [&](const float2 *e) {
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        step_pair_mixed<DC, DS>(pt[s], e[0], e[1]);
-                });
-            } else {
-                ok = run_steps<float2>(R, smem, bars, err, single);
-            }
-        } else {  // no group paths at this level (the host keeps G = 1)
-            ok = run_steps<float2>(R, smem, bars, err, single);
-        }
-    } else if constexpr (SCHEME == 2) {
-        const auto single = [&](const float4 &e) {
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-                step_mixed<SCHEME, DC, DS>(pt[s], make_float2(e.x, e.y), make_float2(e.z, e.w));
-        };
-        if constexpr (kGroupedLevel<DC, DS>) {
-            if (R.group == 8) {
-                ok = run_step_groups<float4, 8>(R, smem, bars, err, single, [&](const float4 *e) {
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        step_group_magnus<8, DC, DS>(pt[s], e);
-                });
-            } else if (R.group == 4) {
-                ok = run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        step_group_magnus<4, DC, DS>(pt[s], e);
-                });
-            } else if (R.group == 2) {
-                ok = run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        step_group_magnus<2, DC, DS>(pt[s], e);
-                });
-            } else {
-                ok = run_steps<float4>(R, smem, bars, err, single);
-            }
-        } else {  // no group paths at this level (the host keeps G = 1)
-            ok = run_steps<float4>(R, smem, bars, err, single);
-        }
-    } else {
-        ok = run_steps<float2>(R, smem, bars, err, [&](const float2 &e) {
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-                step_mixed<SCHEME, DC, DS>(pt[s], e, make_float2(0.0f, 0.0f));
-        });
-    }
-    if constexpr (packed) {
-#pragma unroll
-        for (int k = 0; k < S / 2; ++k)
-            unpack_points(pk[k], pt[2 * k], pt[2 * k + 1]);
-    }
+    for (int k = 0; k < S / 2; ++k)
+        unpack_points(pk[k], pt[2 * k], pt[2 * k + 1]);
     if (!ok)
         return;
 
@@ -284,17 +201,6 @@ __device__ void body_mixed(const ReqDesc &R, int tile, unsigned char *smem, uint
                      [&](int g) { return base / kGranule + g; });
 }
 
-// Block-uniform dispatch on the request's series level (compile-time degrees).
-template <int SCHEME, int L>
-__device__ __forceinline__ void dispatch_mixed(const ReqDesc &R, int tile, unsigned char *smem,
-                                               uint64_t *bars, int *err)
-{
-    if (R.level == L || L + 1 == kNumLevels)
-        body_mixed<SCHEME, kLevelsF32[L].dc, kLevelsF32[L].ds>(R, tile, smem, bars, err);
-    else if constexpr (L + 1 < kNumLevels)
-        dispatch_mixed<SCHEME, L + 1>(R, tile, smem, bars, err);
-}
-
 // ---------------------------------------------------------------------------
 // Kernel
 // ---------------------------------------------------------------------------
@@ -316,11 +222,11 @@ __global__ void __launch_bounds__(kMixedThreads, kMixedMinBlocks)
     if (!tile_ok(R, tile, R.err))
         return;
     if (R.scheme == 0)
-        dispatch_mixed<0, 0>(R, tile, smem, bars, R.err);
+        body_mixed<0>(R, tile, smem, bars, R.err);
     else if (R.scheme == 1)
-        dispatch_mixed<1, 0>(R, tile, smem, bars, R.err);
+        body_mixed<1>(R, tile, smem, bars, R.err);
     else
-        dispatch_mixed<2, 0>(R, tile, smem, bars, R.err);
+        body_mixed<2>(R, tile, smem, bars, R.err);
 }
 
 }  // namespace

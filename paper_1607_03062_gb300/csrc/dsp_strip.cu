@@ -24,18 +24,22 @@ namespace {
 // thread's spinors share p_x and the CTA's threads share the 4 p_y, so the part
 // of a step's coefficients that depends on dt P_y alone is computed once per row
 // and step into a table in shared memory (built for each chunk of steps), and
-// the part that depends on dt P_x alone once per thread and step, as scalars:
+// the part that depends on dt P_x alone once per thread and step, as scalars.
+// Steps taken one at a time (G = 1) and MAGNUS4 groups:
 //   EXACT:     rows dt P_y and fl(dt P_y^2); column dt P_x;
 //   STRANG_XY: rows cos(dt P_y) - 1 and sin(dt P_y); column cos(dt P_x) - 1 and
 //              sin(dt P_x) (with dt P_x = 2a of the split);
 //   MAGNUS4:   rows dt Pbar_y and -fl(dt Pbar_y D_x); column dt Pbar_x (and the
 //              step's D_y, the same for every thread).
+// Tan-normalised groups (G >= 2):
+//   EXACT:     rows dt P_y and fl(dt P_y^2); column dt P_x;
+//   STRANG_XY: rows tan(dt P_y); column tan(dt P_x) and sec(dt P_x) - 1.
 // Every operation on a point is the contiguous path's (same operands, same
 // order, same rounding), so each point's result is bitwise the same on either
-// tiling; only the work per step shrinks (EXACT: 3.5 + dc + ds coefficient
-// lane-ops per spinor-step instead of 8 + dc + ds; STRANG_XY: 3 per spinor plus
-// (4 + dc + ds)/4 per thread instead of 12 + 2 (dc + ds); MAGNUS4: 7.5 + dc + ds
-// instead of 12 + dc + ds).
+// tiling; only the work per step shrinks.  Coefficient lane-ops per spinor-step
+// of the groups: EXACT 3.5 + DT instead of 8 + DT; STRANG_XY 1 per spinor plus
+// (4 + 2 DT)/4 per thread instead of 9 + 3 DT; MAGNUS4 7.5 + dc + ds instead of
+// 12 + dc + ds.
 // ---------------------------------------------------------------------------
 
 #if !defined(DSP_STRIP_SCHEME) || !defined(DSP_STRIP_NP)
@@ -77,12 +81,12 @@ struct StripSmem {
 static_assert(sizeof(StripSmem) <= 48 * 1024, "static shared memory of one CTA");
 
 // The row part of a step for the two rows of a pack, from dt P_y of each (and,
-// for MAGNUS4, the step's D_x):
+// for MAGNUS4, the step's D_x), for steps taken one at a time (G = 1) and
+// MAGNUS4 groups:
 //   EXACT     {P_y(r0), P_y(r1), fl(P_y(r0)^2), fl(P_y(r1)^2)}
 //   STRANG_XY {cy(r0), cy(r1), sb(r0), sb(r1)}, cy = cos b - 1, sb = sin b, b = dt P_y
 //   MAGNUS4   {P_y(r0), P_y(r1), -fl(P_y(r0) D_x), -fl(P_y(r1) D_x)}
-// each as coeffs_group / coeffs_strang_group / coeffs_magnus_group form it for
-// one lane.
+// each as coeffs_strang / coeffs_magnus_group form it for one lane.
 template <int SCHEME, int DC, int DS>
 __device__ __forceinline__ float4 strip_row(float y0, float y1, float dx)
 {
@@ -100,10 +104,29 @@ __device__ __forceinline__ float4 strip_row(float y0, float y1, float dx)
     }
 }
 
+// The row part of a step of the tan-normalised groups (coeffs_tan's operations):
+//   EXACT     {P_y(r0), P_y(r1), fl(P_y(r0)^2), fl(P_y(r1)^2)}
+//   STRANG_XY {tan b(r0), tan b(r1), 0, 0}, b = dt P_y
+template <int SCHEME, int DT>
+__device__ __forceinline__ float4 strip_row_tan(float y0, float y1)
+{
+    if constexpr (SCHEME == 0) {
+        return make_float4(y0, y1, __fmul_rn(y0, y0), __fmul_rn(y1, y1));
+    } else {
+        const float x0 = vmul(y0, y0), x1 = vmul(y1, y1);
+        const float t0 = vfma(vmul(vseries<float, TanCoef, DT, 1>(x0), x0), y0, y0);
+        const float t1 = vfma(vmul(vseries<float, TanCoef, DT, 1>(x1), x1), y1, y1);
+        return make_float4(t0, t1, 0.0f, 0.0f);
+    }
+}
+
 // The column part of a step, from dt P_x = dt p_hi + (dt A_x + dt p_lo):
 //   EXACT     a = (P_x, P_x);
 //   STRANG_XY a = (cx, cx), b = (sa, sa): cx = cos 2a - 1, sa = sin 2a, 2a = dt P_x;
-//   MAGNUS4   a = (P_x, P_x), b = (D_y, D_y) (P_x from dt Abar_x).
+//   MAGNUS4   a = (P_x, P_x), b = (D_y, D_y) (P_x from dt Abar_x);
+// of the tan-normalised groups (strip_col_tan):
+//   EXACT     a = (P_x, P_x);
+//   STRANG_XY a = (tan 2a, tan 2a), b = (sec 2a - 1, sec 2a - 1).
 struct StripCol {
     float2 a, b;
 };
@@ -124,25 +147,47 @@ __device__ __forceinline__ StripCol strip_col(float pxh, float pxl, float ax, fl
     }
 }
 
-// (m, q) of a step for a pack in the small-part form of the groups
-// (coeffs_group / coeffs_strang_group).
-template <int SCHEME, int DC, int DS>
-__device__ __forceinline__ void strip_coeffs_group(const StripCol &c, float4 r, float2 &m,
-                                                   float2 &qr, float2 &qi)
+template <int SCHEME, int DT>
+__device__ __forceinline__ StripCol strip_col_tan(float pxh, float pxl, float ax)
+{
+    const float px = __fadd_rn(pxh, __fadd_rn(ax, pxl));
+    if constexpr (SCHEME == 0) {
+        return StripCol{make_float2(px, px), make_float2(0.0f, 0.0f)};
+    } else {
+        const float xx = vmul(px, px);
+        const float t = vfma(vmul(vseries<float, TanCoef, DT, 1>(xx), xx), px, px);
+        const float sc = vmul(vseries<float, SecCoef, DT, 1>(xx), xx);
+        return StripCol{make_float2(t, t), make_float2(sc, sc)};
+    }
+}
+
+// tau of a step for a pack in coeffs_tan's form.
+template <int SCHEME, int DT>
+__device__ __forceinline__ void strip_coeffs_tan(const StripCol &c, float4 r, float2 &tr,
+                                                 float2 &ti)
 {
     if constexpr (SCHEME == 0) {
         const float2 Py = make_float2(r.x, r.y), Py2 = make_float2(r.z, r.w);
         const float2 x = vfma(c.a, c.a, Py2);
-        m = vmul(vhorner<float2, DC, 1, 0>(x), x);
-        const float2 s1 = vmul(vhorner<float2, DS, 1, 1>(x), x);
-        qr = vfma(s1, Py, Py);
-        qi = vfma(s1, c.a, c.a);
+        const float2 t1 = vmul(vseries<float2, TanCoef, DT, 1>(x), x);  // tan(theta)/theta - 1
+        tr = vfma(t1, Py, Py);
+        ti = vfma(t1, c.a, c.a);
     } else {
-        const float2 cy = make_float2(r.x, r.y);
-        qr = make_float2(r.z, r.w);
-        qi = vfma(cy, c.b, c.b);
-        m = vfma(c.a, cy, vadd(c.a, cy));
+        const float2 tb = make_float2(r.x, r.y);
+        tr = vfma(tb, c.b, tb);
+        ti = c.a;
     }
+}
+
+// (m, q) of a STRANG_XY step alone for a pack, in coeffs_strang's form.
+template <int DC, int DS>
+__device__ __forceinline__ void strip_coeffs_strang(const StripCol &c, float4 r, float2 &m,
+                                                    float2 &qr, float2 &qi)
+{
+    const float2 cy = make_float2(r.x, r.y);
+    qr = make_float2(r.z, r.w);
+    qi = vfma(cy, c.b, c.b);
+    m = vfma(c.a, cy, vadd(c.a, cy));
 }
 
 // (m, q, q_z) of a MAGNUS4 step for a pack in coeffs_magnus_group's form.
@@ -173,19 +218,26 @@ __device__ __forceinline__ void strip_coeffs_exact(const StripCol &c, float4 r, 
     qi = mul2(sn, c.a);
 }
 
-template <int SCHEME, int DC, int DS, int NP>
+template <int SCHEME, int NP>
 struct StripThread {
     float pxh, pxl;  // dt p_x of the column, hi + lo
     const StripSmem *sm;
 
+    template <int DC, int DS>
     __device__ __forceinline__ StripCol col(int j) const
     {
         return strip_col<SCHEME, DC, DS>(pxh, pxl, sm->ax[j], SCHEME == 2 ? sm->dy[j] : 0.0f);
     }
-    // one step alone: step_exact2 (EXACT) or step_single_scheme (STRANG_XY)
+    template <int DT>
+    __device__ __forceinline__ StripCol col_tan(int j) const
+    {
+        return strip_col_tan<SCHEME, DT>(pxh, pxl, sm->ax[j]);
+    }
+    // one step alone: step_exact2 (EXACT), step_strang (STRANG_XY), step_magnus2 (MAGNUS4)
+    template <int DC, int DS>
     __device__ __forceinline__ void single(MixedPack (&pk)[NP], int j) const
     {
-        const StripCol c = col(j);
+        const StripCol c = col<DC, DS>(j);
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             float2 m, qr, qi;
@@ -201,91 +253,96 @@ struct StripThread {
                 const float2 sn = horner2<DS, 0, 1>(x);
                 apply2(pk[q], m, neg2(mul2(sn, nz)), mul2(sn, Py), mul2(sn, c.a));
             } else {
-                strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j][q], m, qr, qi);
+                strip_coeffs_strang<DC, DS>(c, sm->rows[j][q], m, qr, qi);
                 apply_group(pk[q], m, bc2(0.0f), qr, qi);
             }
         }
     }
-    // two EXACT steps multiplied (step_pair2)
-    __device__ __forceinline__ void pair(MixedPack (&pk)[NP], int j) const
+    // a step of a tan-normalised run outside whole groups (step_single_tan)
+    template <int G, int DT>
+    __device__ __forceinline__ void single_tan(MixedPack (&pk)[NP], int j) const
     {
-        const StripCol c0 = col(j), c1 = col(j + 1);
+        const StripCol c = col_tan<DT>(j);
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            float2 m1, q1r, q1i, m2, q2r, q2i;
-            strip_coeffs_exact<DC, DS>(c0, sm->rows[j][q], m1, q1r, q1i);
-            strip_coeffs_exact<DC, DS>(c1, sm->rows[j + 1][q], m2, q2r, q2i);
-            pair_apply2(pk[q], m1, q1r, q1i, m2, q2r, q2i);
+            float2 tr, ti;
+            strip_coeffs_tan<SCHEME, DT>(c, sm->rows[j][q], tr, ti);
+            TanChain<float2> ch;
+            ch.first(tr, ti);
+            ch.template finish<kTanNormDegree(G)>(pk[q]);
         }
     }
-    // step_group's (step_group_magnus's) chain, both packs advanced step by step
-    template <int G>
-    __device__ __forceinline__ void group(MixedPack (&pk)[NP], int j) const
+    // step_group_tan's chain, the packs advanced step by step
+    template <int G, int DT>
+    __device__ __forceinline__ void group_tan(MixedPack (&pk)[NP], int j) const
     {
-        if constexpr (SCHEME == 2) {
-            MagnusChain<float2> ch[NP];
-            float2 m, qr, qi, qz;
-            StripCol c = col(j);
+        TanChain<float2> ch[NP];
+        float2 tr, ti;
+        StripCol c = col_tan<DT>(j);
 #pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                strip_coeffs_magnus<DC, DS>(c, sm->rows[j][q], m, qr, qi, qz);
-                ch[q].first(m, qr, qi, qz);
-            }
-#pragma unroll kStripChainUnroll
-            for (int k = 1; k < G; ++k) {
-                c = col(j + k);
-#pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                    strip_coeffs_magnus<DC, DS>(c, sm->rows[j + k][q], m, qr, qi, qz);
-                    ch[q].next(m, qr, qi, qz);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < NP; ++q)
-                ch[q].finish(pk[q]);
-        } else {
-            Chain<float2> ch[NP];
-            float2 m, qr, qi;
-            StripCol c = col(j);
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j][q], m, qr, qi);
-                ch[q].first(m, qr, qi);
-            }
-            c = col(j + 1);
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j + 1][q], m, qr, qi);
-                ch[q].second(m, qr, qi);
-            }
-#pragma unroll kStripChainUnroll
-            for (int k = 2; k < G; ++k) {
-                c = col(j + k);
-#pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                    strip_coeffs_group<SCHEME, DC, DS>(c, sm->rows[j + k][q], m, qr, qi);
-                    ch[q].next(m, qr, qi);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < NP; ++q)
-                ch[q].finish(pk[q]);
+        for (int q = 0; q < NP; ++q) {
+            strip_coeffs_tan<SCHEME, DT>(c, sm->rows[j][q], tr, ti);
+            ch[q].first(tr, ti);
         }
+        c = col_tan<DT>(j + 1);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            strip_coeffs_tan<SCHEME, DT>(c, sm->rows[j + 1][q], tr, ti);
+            ch[q].second(tr, ti);
+        }
+#pragma unroll kStripChainUnroll
+        for (int k = 2; k < G; ++k) {
+            c = col_tan<DT>(j + k);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                strip_coeffs_tan<SCHEME, DT>(c, sm->rows[j + k][q], tr, ti);
+                ch[q].next(tr, ti);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+            ch[q].template finish<kTanNormDegree(G)>(pk[q]);
+    }
+    // step_group_magnus's chain, the packs advanced step by step
+    template <int G, int DC, int DS>
+    __device__ __forceinline__ void group_magnus(MixedPack (&pk)[NP], int j) const
+    {
+        MagnusChain<float2> ch[NP];
+        float2 m, qr, qi, qz;
+        StripCol c = col<DC, DS>(j);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            strip_coeffs_magnus<DC, DS>(c, sm->rows[j][q], m, qr, qi, qz);
+            ch[q].first(m, qr, qi, qz);
+        }
+#pragma unroll kStripChainUnroll
+        for (int k = 1; k < G; ++k) {
+            c = col<DC, DS>(j + k);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                strip_coeffs_magnus<DC, DS>(c, sm->rows[j + k][q], m, qr, qi, qz);
+                ch[q].next(m, qr, qi, qz);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+            ch[q].finish(pk[q]);
     }
 };
 
 // The launch's steps on a strip tile: each chunk of table entries is staged by
 // bulk copy (double buffered, bounded waits), expanded into the row table,
 // then stepped in groups of G aligned to absolute step indices (ragged ends one
-// step at a time, as run_step_groups).  G = 1: every step alone.  EXACT pairs
-// (G = 2) take step_pair2's form; STRANG_XY and MAGNUS4 pairs take the chain,
-// as on the contiguous tiles.
-template <int SCHEME, int G, int DC, int DS, int NP>
+// step at a time, as run_step_groups).  G = 1: every step alone (series degrees
+// DC, DS).  G >= 2: tan-normalised groups of degree DT (EXACT, STRANG_XY) or
+// MAGNUS4 chains (DC, DS), as on the contiguous tiles.
+template <int SCHEME, int G, int DC, int DS, int DT, int NP>
 __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint64_t *bars, int *err,
-                                          const StripThread<SCHEME, DC, DS, NP> &th,
+                                          const StripThread<SCHEME, NP> &th,
                                           const float (&pyh)[2 * NP],
                                           const float (&pyl)[2 * NP], MixedPack (&pk)[NP])
 {
+    constexpr bool kTan = SCHEME != 2 && G >= 2;
     using E = StripEntry<SCHEME>;
     using St = Stager<E, kStripStage>;
     constexpr int GA = G > St::kAlign ? G : St::kAlign;  // staging starts on a group and 16 bytes
@@ -302,6 +359,12 @@ __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint6
         if (st.nchunks > 0) st.issue(0);
         if (st.nchunks > 1) st.issue(1);
     }
+    const auto one = [&](int j) {
+        if constexpr (kTan)
+            th.template single_tan<G, DT>(pk, j);
+        else
+            th.template single<DC, DS>(pk, j);
+    };
     for (int c = 0; c < st.nchunks; ++c) {
         const bool ok = mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1);
         if (!__syncthreads_and(ok)) {
@@ -324,7 +387,10 @@ __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint6
             for (int q = 0; q < NP; ++q) {
                 const float y0 = __fadd_rn(pyh[2 * q], __fadd_rn(a.y, pyl[2 * q]));
                 const float y1 = __fadd_rn(pyh[2 * q + 1], __fadd_rn(a.y, pyl[2 * q + 1]));
-                sm.rows[j][q] = strip_row<SCHEME, DC, DS>(y0, y1, dx);
+                if constexpr (kTan)
+                    sm.rows[j][q] = strip_row_tan<SCHEME, DT>(y0, y1);
+                else
+                    sm.rows[j][q] = strip_row<SCHEME, DC, DS>(y0, y1, dx);
             }
         }
         __syncthreads();  // the table is built and stage c & 1 is free again
@@ -335,30 +401,96 @@ __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint6
         if constexpr (G == 1) {
 #pragma unroll 2
             for (; j < len; ++j)
-                th.single(pk, j);
+                one(j);
         } else {
             for (; j < len && (j & (G - 1)) != 0; ++j)  // ragged start
-                th.single(pk, j);
-            if constexpr (G == 2 && SCHEME == 0) {
-#pragma unroll kPairUnroll
-                for (; j + G <= len; j += G)
-                    th.pair(pk, j);
-            } else {
+                one(j);
 #pragma unroll kStripGroupUnroll
-                for (; j + G <= len; j += G)
-                    th.template group<G>(pk, j);
+            for (; j + G <= len; j += G) {
+                if constexpr (kTan)
+                    th.template group_tan<G, DT>(pk, j);
+                else
+                    th.template group_magnus<G, DC, DS>(pk, j);
             }
             for (; j < len; ++j)  // ragged end (last chunk only)
-                th.single(pk, j);
+                one(j);
         }
         __syncthreads();  // everyone is done with the row table
     }
     return true;
 }
 
+// Block-uniform dispatch of a strip's steps: tan-normalised groups on (G, DT);
+// everything else on the series level (DC, DS), MAGNUS4 groups on G inside it.
+template <int SCHEME, int DC, int DS, int NP>
+__device__ __forceinline__ bool strip_level_steps(const ReqDesc &R, StripSmem &sm, uint64_t *bars,
+                                                  int *err, const StripThread<SCHEME, NP> &th,
+                                                  const float (&pyh)[2 * NP],
+                                                  const float (&pyl)[2 * NP], MixedPack (&pk)[NP])
+{
+    if constexpr (SCHEME == 2 && kGroupedLevel<DC, DS>) {
+        if (R.group == kGroupMax)
+            return run_strip<SCHEME, kGroupMax, DC, DS, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+        if (R.group == 8)
+            return run_strip<SCHEME, 8, DC, DS, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+        if (R.group == 4)
+            return run_strip<SCHEME, 4, DC, DS, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+        if (R.group == 2)
+            return run_strip<SCHEME, 2, DC, DS, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+    }
+    return run_strip<SCHEME, 1, DC, DS, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+}
+
+template <int SCHEME, int L, int NP>
+__device__ __forceinline__ bool strip_level(const ReqDesc &R, StripSmem &sm, uint64_t *bars,
+                                            int *err, const StripThread<SCHEME, NP> &th,
+                                            const float (&pyh)[2 * NP],
+                                            const float (&pyl)[2 * NP], MixedPack (&pk)[NP])
+{
+    if constexpr (L + 1 < kNumLevels) {
+        if (R.level != L)
+            return strip_level<SCHEME, L + 1>(R, sm, bars, err, th, pyh, pyl, pk);
+    }
+    return strip_level_steps<SCHEME, kLevelsF32[L].dc, kLevelsF32[L].ds>(R, sm, bars, err, th,
+                                                                         pyh, pyl, pk);
+}
+
+template <int SCHEME, int G, int I, int NP>
+__device__ __forceinline__ bool strip_tan(const ReqDesc &R, StripSmem &sm, uint64_t *bars,
+                                          int *err, const StripThread<SCHEME, NP> &th,
+                                          const float (&pyh)[2 * NP],
+                                          const float (&pyl)[2 * NP], MixedPack (&pk)[NP])
+{
+    constexpr int DT = kTanDegrees[I];
+    if constexpr (I + 1 < kNumTanDegrees) {
+        if (R.tdeg != DT)
+            return strip_tan<SCHEME, G, I + 1>(R, sm, bars, err, th, pyh, pyl, pk);
+    }
+    return run_strip<SCHEME, G, 0, 0, DT>(R, sm, bars, err, th, pyh, pyl, pk);
+}
+
+template <int SCHEME, int NP>
+__device__ __forceinline__ bool strip_steps(const ReqDesc &R, StripSmem &sm, uint64_t *bars,
+                                            int *err, const StripThread<SCHEME, NP> &th,
+                                            const float (&pyh)[2 * NP],
+                                            const float (&pyl)[2 * NP], MixedPack (&pk)[NP])
+{
+    if constexpr (SCHEME != 2) {
+        if (R.group == kGroupMax)
+            return strip_tan<SCHEME, kGroupMax, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+        if (R.group == 8)
+            return strip_tan<SCHEME, 8, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+        if (R.group == 4)
+            return strip_tan<SCHEME, 4, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+        if (R.group == 2)
+            return strip_tan<SCHEME, 2, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+    }
+    return strip_level<SCHEME, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+}
+
 // A strip tile of NP packs per thread (2 NP rows: 4 normally, 2 for the strips
 // that split a launch's last wave, see ReqDesc::strip_h).
-template <int SCHEME, int DC, int DS, int NP>
+template <int SCHEME, int NP>
 __device__ void body_strip(const ReqDesc &R, int tile, unsigned char *smem, uint64_t *bars,
                            int *err)
 {
@@ -375,7 +507,7 @@ __device__ void body_strip(const ReqDesc &R, int tile, unsigned char *smem, uint
     // valley K- is stepped as K+ on -P: the table holds -dt*A, here -dt*p
     const double px = grid_node(R.px_min, R.hx, col);
     const double tx = vs * (R.dt * px);
-    StripThread<SCHEME, DC, DS, NP> th;
+    StripThread<SCHEME, NP> th;
     th.pxh = static_cast<float>(tx);
     th.pxl = static_cast<float>(tx - static_cast<double>(th.pxh));
     th.sm = &sm;
@@ -413,21 +545,7 @@ __device__ void body_strip(const ReqDesc &R, int tile, unsigned char *smem, uint
 #pragma unroll
     for (int q = 0; q < NP; ++q)
         pk[q] = pack_points(pt[2 * q], pt[2 * q + 1]);
-    bool ok;
-    if constexpr (kGroupedLevel<DC, DS>) {
-        if (R.group == kGroupMax)
-            ok = run_strip<SCHEME, kGroupMax>(R, sm, bars, err, th, pyh, pyl, pk);
-        else if (R.group == 8)
-            ok = run_strip<SCHEME, 8>(R, sm, bars, err, th, pyh, pyl, pk);
-        else if (R.group == 4)
-            ok = run_strip<SCHEME, 4>(R, sm, bars, err, th, pyh, pyl, pk);
-        else if (R.group == 2)
-            ok = run_strip<SCHEME, 2>(R, sm, bars, err, th, pyh, pyl, pk);
-        else
-            ok = run_strip<SCHEME, 1>(R, sm, bars, err, th, pyh, pyl, pk);
-    } else {  // no group paths at this level (the host keeps G = 1)
-        ok = run_strip<SCHEME, 1>(R, sm, bars, err, th, pyh, pyl, pk);
-    }
+    const bool ok = strip_steps(R, sm, bars, err, th, pyh, pyl, pk);
 #pragma unroll
     for (int q = 0; q < NP; ++q)
         unpack_points(pk[q], pt[2 * q], pt[2 * q + 1]);
@@ -459,18 +577,6 @@ __device__ void body_strip(const ReqDesc &R, int tile, unsigned char *smem, uint
                      [&](int g) { return (row_first + g) * ncb + cb; });
 }
 
-template <int SCHEME, int L>
-__device__ __forceinline__ void dispatch_strip(const ReqDesc &R, int tile, unsigned char *smem,
-                                               uint64_t *bars, int *err)
-{
-    if (R.level == L || L + 1 == kNumLevels) {
-        body_strip<SCHEME, kLevelsF32[L].dc, kLevelsF32[L].ds, DSP_STRIP_NP>(R, tile, smem, bars,
-                                                                            err);
-    } else if constexpr (L + 1 < kNumLevels) {
-        dispatch_strip<SCHEME, L + 1>(R, tile, smem, bars, err);
-    }
-}
-
 template <int SCHEME, int NP>
 __global__ void __launch_bounds__(kStripThreads, kMixedMinBlocks)
     evolve_strip_kernel(const __grid_constant__ EvolveArgs args)
@@ -488,7 +594,7 @@ __global__ void __launch_bounds__(kStripThreads, kMixedMinBlocks)
     const int tile = static_cast<int>(blockIdx.x) - R.tile_begin;
     if (!tile_ok(R, tile, R.err))
         return;
-    dispatch_strip<SCHEME, 0>(R, tile, smem, bars, R.err);
+    body_strip<SCHEME, NP>(R, tile, smem, bars, R.err);
 }
 
 }  // namespace
