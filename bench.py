@@ -171,27 +171,6 @@ def load_peaks():
         return {}
 
 
-# ------------------------------------------------------------------------------------------
-# FP32 lane instructions of the FP32-mixed EXACT path, with series degrees dc (cos) and
-# ds (sin/theta) as the library reports them.  Per step:
-#   P = p_h + (A + p_l) (x and y)                               4
-#   theta^2 = fma(Px, Px, Py*Py)                               2
-#   cos(theta) - 1 (Horner, dc - 1 FMA + 1 MUL)                dc
-#   sin(theta)/theta (Horner)                                  ds
-#   q = sinc * (P_y + i P_x)                                   2
-# per PAIR of steps (G = 2: the two operators multiplied, then one compensated update):
-#   U2 U1 - I: al - 1 (5), Im al (2), Q (6)                    13
-#   (U2 U1 - I) psi_hi + psi_lo                                16
-#   Fast2Sum of the 4 components                               12
-# i.e. 28.5 + dc + ds per spinor-step.
-# per GROUP of G = 4 or 8 steps (same per-step coefficients, with sin/theta - 1 and
-# q = P + (sinc - 1) P):
-#   alpha = 1 + m1 (1), second step (9), 12 per further step   10 + 12 (G - 2)
-#   Re alpha - 1 rebuilt from unitarity (one Newton step)       8
-#   update and Fast2Sum as above                                28
-# i.e. 20 + dc + ds + 22/G per spinor-step.  Single steps (G = 1): 32 + dc + ds.
-# ------------------------------------------------------------------------------------------
-
 def tan_norm_degree(group):
     """Degree of the (1 + y)^(-1/2) series that normalises a tan-normalised group."""
     return 4 if group >= 16 else 5 if group >= 8 else 6 if group >= 4 else 7
@@ -209,15 +188,19 @@ def ops_mixed(dc, ds, group=2, strips=False, tdeg=0):
     """FP32 lane instructions per spinor-step of the FP32-mixed EXACT path.  Steps one
     at a time (G = 1): dt P (4) + theta^2 (2) + dc + ds + q (2) + the update (12) and
     Fast2Sum (12) = 32 + dc + ds.  Tan-normalised groups: dt P (4) + theta^2 (2) +
-    tan(theta)/theta - 1 (tdeg) + tau (2) + tan_chain_ops.  On row strips the
-    momentum work of a step is shared: each thread forms dt P_x once for its 4 spinors
-    (2 scalar adds: 0.5 per spinor) and reads dt P_y and fl(dt P_y^2) from the strip's
-    row table: 4.5 fewer per spinor-step (the table itself, a few operations per row
-    and step for 1024 spinors, is left out)."""
-    save = 4.5 if strips else 0.0
+    tan(theta)/theta - 1 (tdeg) + tau (2) + tan_chain_ops; at tdeg = 1 the product
+    c1 theta^2 is formed from fl(c1 P_x) and fl(fl(c1 P_y) P_y) (2 + 1) and one
+    multiply-add: 4 + 4 + 2.  On row strips the momentum work of a step is shared:
+    each thread forms dt P_x (and at tdeg = 1 fl(c1 P_x)) once for its 4 spinors (2
+    or 3 scalar ops: 0.5 or 0.75 per spinor) and reads dt P_y and fl(dt P_y^2) (or
+    fl(fl(c1 P_y) P_y)) from the strip's row table: 4.5 (tdeg = 1: 6.25) fewer per
+    spinor-step (the table itself, a few operations per row and step for 1024
+    spinors, is left out)."""
     if group == 1:
-        return 32 + dc + ds - save
-    return 8 + tdeg + tan_chain_ops(group) - save
+        return 32 + dc + ds - (4.5 if strips else 0.0)
+    if tdeg == 1:
+        return 10 + tan_chain_ops(group) - (6.25 if strips else 0.0)
+    return 8 + tdeg + tan_chain_ops(group) - (4.5 if strips else 0.0)
 
 
 def ops_magnus4(dc, ds, group=1, strips=False, tdeg=0):

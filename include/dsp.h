@@ -153,9 +153,11 @@ dsp_status dsp_evolve(dsp_grid *g, int64_t steps);
  * double for DSP_FP64, float for DSP_FP32_MIXED.  Needs cursor == n_steps
  * (DSP_E_STATE otherwise).  Also leaves per-tile FP64 partial sums for
  * dsp_reduce_density.  Points with |p + A_out| == 0 get |c+|^2 = 0.
- * In both precisions |c+|^2 is evaluated in double-float arithmetic (pairs of
- * FP32, about 48 bits, ~1e-14 absolute), the same code as the projection fused
- * into the last evolve launch, so the two give the same bits.  A projection of
+ * DSP_FP64 evaluates |c+|^2 in double-float arithmetic (pairs of FP32, about
+ * 48 bits, ~1e-14 absolute); DSP_FP32_MIXED in FP32 from the hi parts of the
+ * state (error below ~4e-7 |c+|, the size of the float map's own rounding).
+ * Either way it is the same code as the projection fused into the last evolve
+ * launch, so the two give the same bits.  A projection of
  * a state already on the device reads it (32 bytes per point) without writing
  * it back and writes the map (4 or 8 bytes per point).  Asynchronous. */
 dsp_status dsp_project(dsp_grid *g, void *map_dev);

@@ -936,13 +936,25 @@ struct TanChain {
     }
 };
 
+// The coefficient of theta^2 in tan(theta)/theta, rounded to float.  With tan
+// degree DT = 1 the EXACT step forms tan(theta)/theta - 1 = c1 theta^2 as
+// fma(fl(c1 P_x), P_x, fl(fl(c1 P_y) P_y)): one multiply-add per spinor once the
+// column part fl(c1 P_x) and the row part fl(fl(c1 P_y) P_y) are known.
+constexpr float kTanC1 = static_cast<float>(kTanSeries[1]);
+
 // tau of one step (contiguous tiles): SCHEME 0 = EXACT, 1 = STRANG_XY.
 template <int SCHEME, int DT, typename Pt, typename V>
 __device__ __forceinline__ void coeffs_tan(const Pt &p, const float2 &a, V &tr, V &ti)
 {
     const V Px = vadd(p.pxh, vadd(vbc<V>(a.x), p.pxl));
     const V Py = vadd(p.pyh, vadd(vbc<V>(a.y), p.pyl));
-    if constexpr (SCHEME == 0) {
+    if constexpr (SCHEME == 0 && DT == 1) {
+        // tan(theta)/theta - 1 = c1 theta^2 = (c1 P_x) P_x + (c1 P_y) P_y, the column
+        // and row parts formed apart (the row strips share them)
+        const V t1 = vfma(vmul(vbc<V>(kTanC1), Px), Px, vmul(vmul(vbc<V>(kTanC1), Py), Py));
+        tr = vfma(t1, Py, Py);
+        ti = vfma(t1, Px, Px);
+    } else if constexpr (SCHEME == 0) {
         const V x = vfma(Px, Px, vmul(Py, Py));
         const V t1 = vmul(vseries<V, TanCoef, DT, 1>(x), x);  // tan(theta)/theta - 1
         tr = vfma(t1, Py, Py);

@@ -32,14 +32,15 @@ namespace {
 //   MAGNUS4:   rows dt Pbar_y and -fl(dt Pbar_y D_x); column dt Pbar_x (and the
 //              step's D_y, the same for every thread).
 // Tan-normalised groups (G >= 2):
-//   EXACT:     rows dt P_y and fl(dt P_y^2); column dt P_x;
+//   EXACT:     rows dt P_y and fl(dt P_y^2); column dt P_x (tan degree 1: rows
+//              dt P_y and fl(fl(c1 dt P_y) dt P_y), column dt P_x and fl(c1 dt P_x));
 //   STRANG_XY: rows tan(dt P_y); column tan(dt P_x) and sec(dt P_x) - 1.
 // Every operation on a point is the contiguous path's (same operands, same
 // order, same rounding), so each point's result is bitwise the same on either
 // tiling; only the work per step shrinks.  Coefficient lane-ops per spinor-step
-// of the groups: EXACT 3.5 + DT instead of 8 + DT; STRANG_XY 1 per spinor plus
-// (4 + 2 DT)/4 per thread instead of 9 + 3 DT; MAGNUS4 7.5 + dc + ds instead of
-// 12 + dc + ds.
+// of the groups: EXACT 3.5 + DT instead of 8 + DT (DT = 1: 3.75 instead of 10);
+// STRANG_XY 1 per spinor plus (4 + 2 DT)/4 per thread instead of 9 + 3 DT;
+// MAGNUS4 7.5 + dc + ds instead of 12 + dc + ds.
 // ---------------------------------------------------------------------------
 
 #if !defined(DSP_STRIP_SCHEME) || !defined(DSP_STRIP_NP)
@@ -105,12 +106,16 @@ __device__ __forceinline__ float4 strip_row(float y0, float y1, float dx)
 }
 
 // The row part of a step of the tan-normalised groups (coeffs_tan's operations):
-//   EXACT     {P_y(r0), P_y(r1), fl(P_y(r0)^2), fl(P_y(r1)^2)}
+//   EXACT     {P_y(r0), P_y(r1), fl(P_y(r0)^2), fl(P_y(r1)^2)}; with tan degree 1
+//             {P_y(r0), P_y(r1), fl(fl(c1 P_y(r0)) P_y(r0)), fl(fl(c1 P_y(r1)) P_y(r1))}
 //   STRANG_XY {tan b(r0), tan b(r1), 0, 0}, b = dt P_y
 template <int SCHEME, int DT>
 __device__ __forceinline__ float4 strip_row_tan(float y0, float y1)
 {
-    if constexpr (SCHEME == 0) {
+    if constexpr (SCHEME == 0 && DT == 1) {  // coeffs_tan's row part fl(fl(c1 P_y) P_y)
+        return make_float4(y0, y1, __fmul_rn(__fmul_rn(kTanC1, y0), y0),
+                           __fmul_rn(__fmul_rn(kTanC1, y1), y1));
+    } else if constexpr (SCHEME == 0) {
         return make_float4(y0, y1, __fmul_rn(y0, y0), __fmul_rn(y1, y1));
     } else {
         const float x0 = vmul(y0, y0), x1 = vmul(y1, y1);
@@ -125,7 +130,7 @@ __device__ __forceinline__ float4 strip_row_tan(float y0, float y1)
 //   STRANG_XY a = (cx, cx), b = (sa, sa): cx = cos 2a - 1, sa = sin 2a, 2a = dt P_x;
 //   MAGNUS4   a = (P_x, P_x), b = (D_y, D_y) (P_x from dt Abar_x);
 // of the tan-normalised groups (strip_col_tan):
-//   EXACT     a = (P_x, P_x);
+//   EXACT     a = (P_x, P_x) (tan degree 1: b = (fl(c1 P_x), fl(c1 P_x)));
 //   STRANG_XY a = (tan 2a, tan 2a), b = (sec 2a - 1, sec 2a - 1).
 struct StripCol {
     float2 a, b;
@@ -151,7 +156,10 @@ template <int SCHEME, int DT>
 __device__ __forceinline__ StripCol strip_col_tan(float pxh, float pxl, float ax)
 {
     const float px = __fadd_rn(pxh, __fadd_rn(ax, pxl));
-    if constexpr (SCHEME == 0) {
+    if constexpr (SCHEME == 0 && DT == 1) {  // coeffs_tan's column part fl(c1 P_x)
+        const float cpx = __fmul_rn(kTanC1, px);
+        return StripCol{make_float2(px, px), make_float2(cpx, cpx)};
+    } else if constexpr (SCHEME == 0) {
         return StripCol{make_float2(px, px), make_float2(0.0f, 0.0f)};
     } else {
         const float xx = vmul(px, px);
@@ -166,7 +174,12 @@ template <int SCHEME, int DT>
 __device__ __forceinline__ void strip_coeffs_tan(const StripCol &c, float4 r, float2 &tr,
                                                  float2 &ti)
 {
-    if constexpr (SCHEME == 0) {
+    if constexpr (SCHEME == 0 && DT == 1) {
+        const float2 Py = make_float2(r.x, r.y), rY = make_float2(r.z, r.w);
+        const float2 t1 = vfma(c.b, c.a, rY);  // c1 theta^2 = tan(theta)/theta - 1
+        tr = vfma(t1, Py, Py);
+        ti = vfma(t1, c.a, c.a);
+    } else if constexpr (SCHEME == 0) {
         const float2 Py = make_float2(r.x, r.y), Py2 = make_float2(r.z, r.w);
         const float2 x = vfma(c.a, c.a, Py2);
         const float2 t1 = vmul(vseries<float2, TanCoef, DT, 1>(x), x);  // tan(theta)/theta - 1
