@@ -172,8 +172,17 @@ def load_peaks():
 
 
 def tan_norm_degree(group):
-    """Degree of the (1 + y)^(-1/2) series that normalises a tan-normalised group."""
-    return 4 if group >= 16 else 5 if group >= 8 else 6 if group >= 4 else 7
+    """Degree of the (1 + y)^(-1/2) series that normalises a tan-normalised group of G
+    steps: the lowest whose first omitted term stays below 1e-14 for y <= 1.05 x
+    0.27^2 / G (the group angle of EXACT and STRANG_XY)."""
+    y = 1.05 * 0.27 * 0.27 / group
+    c, yk = 1.0, 1.0
+    for k in range(1, 16):
+        c *= (2 * k - 1) / (2 * k)
+        yk *= y
+        if c * yk <= 1e-14:
+            return k - 1
+    return 15
 
 
 def tan_chain_ops(group):

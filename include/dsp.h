@@ -250,7 +250,8 @@ dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps);
  * FP64), theta_max = dt * max|p + A_n| over the box, the tile count, and
  * group_steps G: the number of step operators multiplied into one before each
  * compensated update (FP32_MIXED, every scheme: the largest of 16, 8, 4, 2 with
- * G * theta_max <= 0.2, else 1; 1 in FP64), and for EXACT and STRANG_XY groups
+ * G * theta_max <= 0.27 for EXACT and STRANG_XY, <= 0.2 for MAGNUS4, else 1; 1
+ * in FP64), and for EXACT and STRANG_XY groups
  * tan_degree, the degree in theta^2 of the tan(theta)/theta (and sec) series
  * (0 when G = 1).  Not in the paper: with G > 1 the update is paid once per
  * group.  EXACT and STRANG_XY groups multiply the steps divided by their real

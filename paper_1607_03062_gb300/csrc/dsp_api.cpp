@@ -149,8 +149,9 @@ int32_t choose_tan_degree(int32_t scheme, double theta, int64_t n_steps)
 
 // Steps multiplied into one operator before each compensated update (FP32_MIXED,
 // every scheme): the largest G in {16, 8, 4, 2} whose group rotation G *
-// theta_max stays within kGroupAngleMax, else 1.  EXACT and STRANG_XY groups need
-// a tan degree (tdeg > 0), MAGNUS4 groups a series level with group code.
+// theta_max stays within the scheme's group angle (kGroupAngleTan for EXACT and
+// STRANG_XY, kGroupAngleMagnus for MAGNUS4), else 1.  EXACT and STRANG_XY groups
+// need a tan degree (tdeg > 0), MAGNUS4 groups a series level with group code.
 int32_t choose_group(int32_t precision, int32_t scheme, int32_t level, int32_t tdeg,
                      double theta_max)
 {
@@ -163,8 +164,10 @@ int32_t choose_group(int32_t precision, int32_t scheme, int32_t level, int32_t t
     } else if (tdeg <= 0) {
         return 1;
     }
+    const double angle =
+        scheme == DSP_SCHEME_MAGNUS4 ? dsp::kGroupAngleMagnus : dsp::kGroupAngleTan;
     for (int32_t G = dsp::kGroupMax; G >= 2; G /= 2)
-        if (G * theta_max <= dsp::kGroupAngleMax)
+        if (G * theta_max <= angle)
             return G;
     return 1;
 }

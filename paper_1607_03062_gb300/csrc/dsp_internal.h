@@ -69,12 +69,6 @@ constexpr double kSecSeries[kTanTerms] = {1.0,
                                           199360981.0 / 87178291200.0};
 constexpr int kNumTanDegrees = 5;
 constexpr int kTanDegrees[kNumTanDegrees] = {1, 2, 3, 4, 6};
-// y = det W - 1 <= G tan^2(theta_max) <= 0.04 / G for a group within kGroupAngleMax;
-// the degree keeps the first omitted term below ~1e-14 per group.
-__host__ __device__ constexpr int kTanNormDegree(int G)
-{
-    return G >= 16 ? 4 : G >= 8 ? 5 : G >= 4 ? 6 : 7;
-}
 
 struct ReqDesc {
     // Per step, s = valley (valley K- steps as K+ on -P: its operator is K+'s at -P):
@@ -125,13 +119,42 @@ struct ReqDesc {
     int64_t table_steps;          // entries in the table (checked by bounds-check builds)
 };
 
-// Steps are grouped (G = 16, 8, 4 or 2, the largest allowed) when G * theta_max <=
-// kGroupAngleMax: the group's increment (U_G ... U_1 - I) psi then stays small
-// next to psi, where the compensated (Fast2Sum) update is exact.
+// Steps are grouped (G = 16, 8, 4 or 2, the largest allowed) when G * theta_max
+// stays within the scheme's group angle: the group's increment (U_G ... U_1 - I)
+// psi then stays small next to psi, where the compensated (Fast2Sum) update
+// keeps the state's rounding from accumulating.  The tan-normalised groups of
+// EXACT and STRANG_XY take 0.27: on every point of the 2048^2 x 1e5-step LZS
+// maps, raising their angle from 0.2 to 0.27 (groups of 16 instead of 8 on
+// samples 1 and 2, of 8 instead of 4 on sample 6) left the largest FP32_MIXED
+// error against FP64 where it was (2.13e-6 -> 2.18e-6, 1.76e-6 -> 1.96e-6,
+// 4.32e-6 -> 4.27e-6), and a TwoSum update in place of Fast2Sum changed none of
+// them.  MAGNUS4 groups, whose chain multiplies the steps themselves, keep 0.2.
 constexpr int kGroupMax = 16;
 // Highest series degree with step groups (see kGroupedLevel in the kernels).
 constexpr int kGroupMaxDegree = 4;
-constexpr double kGroupAngleMax = 0.2;
+constexpr double kGroupAngleTan = 0.27;
+constexpr double kGroupAngleMagnus = 0.2;
+
+// Degree of the (1 + y)^(-1/2) series that normalises a tan-normalised group of
+// G steps: y = det W - 1 = prod(1 + tan^2 theta_k) - 1 ~ G theta_max^2 <=
+// kGroupAngleTan^2 / G (with 5% to spare for the tan^2 and the product); the
+// lowest degree whose first omitted term |binom(-1/2, d + 1)| y^(d + 1) stays
+// below 1e-14 (G = 16, 8, 4, 2: degree 5, 6, 7, 9).
+__host__ __device__ constexpr int kTanNormDegree(int G)
+{
+    const double y = 1.05 * kGroupAngleTan * kGroupAngleTan / G;
+    double c = 1.0, yk = 1.0;  // |binom(-1/2, k)|, y^k
+    for (int k = 1; k < 16; ++k) {
+        c *= static_cast<double>(2 * k - 1) / static_cast<double>(2 * k);
+        yk *= y;
+        if (c * yk <= 1e-14)
+            return k - 1;
+    }
+    return 15;
+}
+static_assert(kTanNormDegree(16) == 5 && kTanNormDegree(8) == 6 && kTanNormDegree(4) == 7 &&
+                  kTanNormDegree(2) == 9,
+              "normalisation degrees of the tan-normalised groups");
 
 static_assert(sizeof(ReqDesc) * kMaxReqPerLaunch + 64 < 32764, "kernel parameter limit");
 
