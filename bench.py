@@ -213,16 +213,18 @@ def ops_mixed(dc, ds, group=2, strips=False, tdeg=0):
 
 
 def ops_magnus4(dc, ds, group=1, strips=False, tdeg=0):
-    """FP32 lane instructions per spinor-step of the MAGNUS4 path.  Per step: 4 (Pbar) +
-    2 (n_z) + 3 (|n|^2) + dc + ds + 3 (q, q_z).  Single steps: + 16 ((U - I) psi + lo)
-    + 12 (Fast2Sum).  Groups of G: + 16 per further step of the chain, 1 to start it,
-    8 (unitarity rebuild) and 28 (update) per group.  On row strips dt Pbar_y and
-    -fl(dt Pbar_y D_x) come from the strip's row table and dt Pbar_x is formed once per
-    thread for its 4 spinors: 4.5 fewer per spinor-step."""
+    """FP32 lane instructions per spinor-step of the MAGNUS4 path.  Single steps: 4 (Pbar)
+    + 2 (n_z) + 3 (|n|^2) + dc + ds + 3 (q, q_z) + 16 ((U - I) psi + lo) + 12 (Fast2Sum)
+    = 40 + dc + ds.  Tan-normalised groups of G: 4 (Pbar) + 2 (n_z) + 3 (|n|^2) + tdeg
+    (tan|n|/|n| - 1) + 3 (tau, t_z) per step, then the chain: 1 to start it (-t_z), 13
+    per further step, and once per group y = det W - 1 (5), its series (DF), the scaled
+    entries (5) and the compensated update (28): 12 + tdeg + 13 + (26 + DF) / G.  On row
+    strips dt Pbar_y and -fl(dt Pbar_y D_x) come from the strip's row table and dt
+    Pbar_x is formed once per thread for its 4 spinors: 4.5 fewer per spinor-step."""
     save = 4.5 if strips else 0.0
     if group == 1:
         return 40 + dc + ds - save
-    return 28 + dc + ds + 21.0 / group - save
+    return 12 + tdeg + 13 + (26.0 + tan_norm_degree(group)) / group - save
 
 
 def ops_strang(dc, ds, group=1, strips=False, tdeg=0):

@@ -71,7 +71,7 @@ struct dsp_grid {
     int32_t level = 0;
     double theta_max = 0.0;
     int32_t group = 1;  // FP32_MIXED: steps multiplied per update (choose_group)
-    int32_t tdeg = 0;   // FP32_MIXED EXACT / STRANG_XY: tan series degree (choose_tan_degree)
+    int32_t tdeg = 0;   // FP32_MIXED: tan series degree of the step groups (choose_tan_degree)
     bool withhold_next = false;  // test hook, see dsp_test_withhold_next_copy
     bool fresh = true;      // state not yet written on the device
     bool projected = false;  // partial sums valid for the current pulse
@@ -128,7 +128,7 @@ int32_t choose_level(int32_t precision, double theta, int64_t n_steps)
 }
 
 // Degree DT of the tan (STRANG_XY: and sec) series of the tan-normalised groups
-// (FP32_MIXED EXACT and STRANG_XY): the lowest of kTanDegrees whose truncation
+// (FP32_MIXED, every scheme; MAGNUS4 in x = |n|^2): the lowest of kTanDegrees whose truncation
 // stays inside the FP32_MIXED budget over the run.  Dropping x^(DT+1) and beyond
 // perturbs the step's rotation angle by ~theta c_(DT+1) x^(DT+1), with a fixed
 // sign, so it adds up over the steps.  0: no degree is enough (groups are not used).
@@ -150,20 +150,12 @@ int32_t choose_tan_degree(int32_t scheme, double theta, int64_t n_steps)
 // Steps multiplied into one operator before each compensated update (FP32_MIXED,
 // every scheme): the largest G in {16, 8, 4, 2} whose group rotation G *
 // theta_max stays within the scheme's group angle (kGroupAngleTan for EXACT and
-// STRANG_XY, kGroupAngleMagnus for MAGNUS4), else 1.  EXACT and STRANG_XY groups
-// need a tan degree (tdeg > 0), MAGNUS4 groups a series level with group code.
-int32_t choose_group(int32_t precision, int32_t scheme, int32_t level, int32_t tdeg,
-                     double theta_max)
+// STRANG_XY, kGroupAngleMagnus for MAGNUS4), else 1.  Groups need a tan degree
+// (tdeg > 0).
+int32_t choose_group(int32_t precision, int32_t scheme, int32_t tdeg, double theta_max)
 {
-    if (precision != DSP_FP32_MIXED)
+    if (precision != DSP_FP32_MIXED || tdeg <= 0)
         return 1;
-    if (scheme == DSP_SCHEME_MAGNUS4) {
-        const dsp::SeriesLevel lv = dsp::kLevelsF32[level];
-        if (lv.dc > dsp::kGroupMaxDegree || lv.ds > dsp::kGroupMaxDegree)
-            return 1;  // the kernels have no group path at this level
-    } else if (tdeg <= 0) {
-        return 1;
-    }
     const double angle =
         scheme == DSP_SCHEME_MAGNUS4 ? dsp::kGroupAngleMagnus : dsp::kGroupAngleTan;
     for (int32_t G = dsp::kGroupMax; G >= 2; G /= 2)
@@ -699,10 +691,8 @@ dsp_status prepare_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, doub
     g->a_out[1] = a_out[1];
     g->theta_max = tmax;
     g->level = choose_level(g->precision, tmax, n_steps);
-    g->tdeg = g->precision == DSP_FP32_MIXED && g->scheme != DSP_SCHEME_MAGNUS4
-                  ? choose_tan_degree(g->scheme, tmax, n_steps)
-                  : 0;
-    g->group = choose_group(g->precision, g->scheme, g->level, g->tdeg, tmax);
+    g->tdeg = g->precision == DSP_FP32_MIXED ? choose_tan_degree(g->scheme, tmax, n_steps) : 0;
+    g->group = choose_group(g->precision, g->scheme, g->tdeg, tmax);
     g->fresh = true;
     g->projected = false;
     g->state_stale = false;

@@ -420,17 +420,6 @@ constexpr int kStageBytes = 16384;  // per stage; two stages per CTA
 #endif
 constexpr int kPairUnroll = DSP_PAIR_UNROLL;
 constexpr int kGroupUnroll = DSP_GROUP_UNROLL;  // chain loop inside one group (>= G - 2: whole)
-#ifndef DSP_MAGNUS_GROUP_UNROLL
-#define DSP_MAGNUS_GROUP_UNROLL 1
-#endif
-constexpr int kMagnusGroupUnroll = DSP_MAGNUS_GROUP_UNROLL;  // the MAGNUS4 chain's
-// MAGNUS4 series levels that can run in step groups.  G >= 2 needs theta_max <= 0.1,
-// where a level above degree kGroupMaxDegree is chosen only for runs of more than
-// ~3e8 steps; the host keeps G = 1 at those levels (choose_group), and no group code
-// is compiled for them.  (EXACT and STRANG_XY groups use the tan series instead,
-// of degree DT in kTanDegrees.)
-template <int DC, int DS>
-constexpr bool kGroupedLevel = DC <= kGroupMaxDegree && DS <= kGroupMaxDegree;
 constexpr int kMixedSpt = DSP_MIXED_SPT;
 constexpr int kMixedThreads = kTilePoints / kMixedSpt;
 constexpr int kMixedMinBlocks = DSP_MIXED_MINB;  // resident CTAs per SM the registers allow
@@ -862,7 +851,8 @@ __device__ __forceinline__ void step_strang(Pt &p, const float2 &a)
 }
 
 // ---------------------------------------------------------------------------
-// Tan-normalised step groups (EXACT and STRANG_XY, G = 2, 4, 8, 16)
+// Tan-normalised step groups (EXACT and STRANG_XY, G = 2, 4, 8, 16; MAGNUS4 uses
+// the same chain with its sigma_z part, see coeffs_tan_magnus)
 //
 // Both schemes step with a real diagonal: U = [[c, -q], [conj(q), c]], c =
 // cos(theta) (STRANG_XY: cos b cos 2a).  Divided by c a step is
@@ -921,6 +911,30 @@ struct TanChain {
         const V nai = vfma(vneg(ti), Qr, vfma(tr, Qi, ai));
         const V nQr = vfma(tr, Ar, vfma(ti, ai, Qr));
         const V nQi = vfma(ti, Ar, vfma(vneg(tr), ai, Qi));
+        as = nas;
+        ai = nai;
+        Qr = nQr;
+        Qi = nQi;
+    }
+    // MAGNUS4 steps, whose N has the diagonal 1 -/+ i tz (see coeffs_tan_magnus):
+    //   (Re alpha - 1)' = (Re alpha - 1) + tz Im alpha - (tr Qr + ti Qi)
+    //   Im alpha'       = Im alpha - tz Re alpha - (ti Qr - tr Qi)
+    //   Qr'             = Qr + tz Qi + tr Re alpha + ti Im alpha
+    //   Qi'             = Qi - tz Qr + ti Re alpha - tr Im alpha
+    __device__ __forceinline__ void first_z(V tr, V ti, V tz)
+    {
+        as = vbc<V>(0.0f);
+        ai = vneg(tz);
+        Qr = tr;
+        Qi = ti;
+    }
+    __device__ __forceinline__ void next_z(V tr, V ti, V tz)
+    {
+        const V Ar = vadd(as, vbc<V>(1.0f));
+        const V nas = vfma(tz, ai, vfma(vneg(tr), Qr, vfma(vneg(ti), Qi, as)));
+        const V nai = vfma(vneg(tz), Ar, vfma(vneg(ti), Qr, vfma(tr, Qi, ai)));
+        const V nQr = vfma(tz, Qi, vfma(tr, Ar, vfma(ti, ai, Qr)));
+        const V nQi = vfma(vneg(tz), Qr, vfma(ti, Ar, vfma(vneg(tr), ai, Qi)));
         as = nas;
         ai = nai;
         Qr = nQr;
@@ -998,84 +1012,57 @@ __device__ __forceinline__ void step_single_tan(Pt &p, const float2 &e)
     c.template finish<kTanNormDegree(G)>(p);
 }
 
-// MAGNUS4 steps in groups (G = 2, 4, 8, 16).  One step is exp(-i n.sigma) with
-// n = (dt Pbar, n_z): U = [[1 + m - i qz, -q], [conj(q), 1 + m + i qz]], m =
-// cos|n| - 1, (q, qz) = sin|n|/|n| (n_y + i n_x, n_z), formed as n + (sinc - 1) n.
-// The diagonal is not real, so the product U_k ... U_1 = [[alpha, -Q], [conj(Q),
-// conj(alpha)]] is chained as it stands:
-//   Re alpha' = Re alpha + m Re alpha + qz Im alpha - (qr Qr + qi Qi)
-//   Im alpha' = Im alpha + m Im alpha - qz Re alpha - (qi Qr - qr Qi)
-//   Qr'       = Qr + m Qr + qz Qi + qr Re alpha + qi Im alpha
-//   Qi'       = Qi + m Qi - qz Qr + qi Re alpha - qr Im alpha
-// starting from alpha = 1 + m - i qz, Q = q of the group's first step.  Re alpha
-// is held near 1, where FP32 resolves it only to ~6e-8, so Re alpha - 1 is
-// rebuilt at the end from the other three entries and unitarity,
-// (1 + am)^2 + ai^2 + |Q|^2 = 1, by one Newton step, before the compensated
-// update.
-template <int DC, int DS, typename Pt, typename V>
-__device__ __forceinline__ void coeffs_magnus_group(const Pt &p, const float4 &e, V &m, V &qr,
-                                                    V &qi, V &qz)
+// MAGNUS4 steps in tan-normalised groups (G = 2, 4, 8, 16).  One step is
+// exp(-i n.sigma) with n = (dt Pbar, n_z): U = [[c - i qz, -q], [conj(q), c + i
+// qz]], c = cos|n|, (q, qz) = sin|n|/|n| (n_y + i n_x, n_z).  Its diagonal is
+// complex, but divided by c the step is N = [[1 - i tz, -tau], [conj(tau), 1 + i
+// tz]] with (tau, tz) = tan|n|/|n| (n_y + i n_x, n_z), still of the form [[alpha,
+// -Q], [conj(Q), conj(alpha)]], so the product W = N_G ... N_1 has that form too
+// and det W = prod sec^2 |n_k|: the group's operator is W / sqrt(det W), as for
+// EXACT (TanChain::finish).  A chain step (TanChain::next_z) takes 13 operations
+// where the product of the U takes 16, and cos|n| - 1 is never evaluated.  The
+// tan series is the EXACT one (kTanSeries, degree DT) in x = |n|^2, and tau, tz
+// are formed as n + (tan|n|/|n| - 1) n.
+template <int DT, typename Pt, typename V>
+__device__ __forceinline__ void coeffs_tan_magnus(const Pt &p, const float4 &e, V &tr, V &ti,
+                                                  V &tz)
 {
     const V Px = vadd(p.pxh, vadd(vbc<V>(e.x), p.pxl));
     const V Py = vadd(p.pyh, vadd(vbc<V>(e.y), p.pyl));
     const V nz = vfma(Px, vbc<V>(e.w), vneg(vmul(Py, vbc<V>(e.z))));
     const V x = vfma(Px, Px, vfma(Py, Py, vmul(nz, nz)));
-    m = vmul(vhorner<V, DC, 1, 0>(x), x);
-    const V s1 = vmul(vhorner<V, DS, 1, 1>(x), x);  // sin|n|/|n| - 1
-    qr = vfma(s1, Py, Py);
-    qi = vfma(s1, Px, Px);
-    qz = vfma(s1, nz, nz);
+    const V t1 = vmul(vseries<V, TanCoef, DT, 1>(x), x);  // tan|n|/|n| - 1
+    tr = vfma(t1, Py, Py);
+    ti = vfma(t1, Px, Px);
+    tz = vfma(t1, nz, nz);
 }
 
-// The MAGNUS4 chain: first(...) for the group's first step, next(...) for the
-// others, finish(p) for the unitarity rebuild and the compensated update.
-// Every MAGNUS4 group (either tiling) goes through these operations.
-template <typename V>
-struct MagnusChain {
-    V Ar, ai, Qr, Qi;
-
-    __device__ __forceinline__ void first(V m, V qr, V qi, V qz)
-    {
-        Qr = qr;
-        Qi = qi;
-        Ar = vadd(m, vbc<V>(1.0f));
-        ai = vneg(qz);
-    }
-    __device__ __forceinline__ void next(V m, V qr, V qi, V qz)
-    {
-        const V nAr = vfma(m, Ar, vfma(qz, ai, vfma(vneg(qr), Qr, vfma(vneg(qi), Qi, Ar))));
-        const V nai = vfma(m, ai, vfma(vneg(qz), Ar, vfma(vneg(qi), Qr, vfma(qr, Qi, ai))));
-        const V nQr = vfma(m, Qr, vfma(qz, Qi, vfma(qr, Ar, vfma(qi, ai, Qr))));
-        const V nQi = vfma(m, Qi, vfma(vneg(qz), Qr, vfma(qi, Ar, vfma(vneg(qr), ai, Qi))));
-        Ar = nAr;
-        ai = nai;
-        Qr = nQr;
-        Qi = nQi;
-    }
-    template <typename Pt>
-    __device__ __forceinline__ void finish(Pt &p) const
-    {
-        V am = vadd(Ar, vbc<V>(-1.0f));  // exact: Re alpha is within [1/2, 2]
-        const V u = vfma(am, am, vfma(Qi, Qi, vfma(Qr, Qr, vfma(ai, ai, vadd(am, am)))));
-        am = vfma(vneg(u), vfma(vbc<V>(-0.5f), am, vbc<V>(0.5f)), am);  // am -= u / (2 (1 + am))
-        apply_group(p, am, ai, Qr, Qi);
-    }
-};
-
-template <int G, int DC, int DS, typename Pt>
-__device__ __forceinline__ void step_group_magnus(Pt &p, const float4 *e)
+template <int G, int DT, typename Pt>
+__device__ __forceinline__ void step_group_tan_magnus(Pt &p, const float4 *e)
 {
     using V = decltype(p.ar);
-    MagnusChain<V> c;
-    V m, qr, qi, qz;
-    coeffs_magnus_group<DC, DS>(p, e[0], m, qr, qi, qz);
-    c.first(m, qr, qi, qz);
-#pragma unroll kMagnusGroupUnroll
+    TanChain<V> c;
+    V tr, ti, tz;
+    coeffs_tan_magnus<DT>(p, e[0], tr, ti, tz);
+    c.first_z(tr, ti, tz);
+#pragma unroll kGroupUnroll
     for (int k = 1; k < G; ++k) {
-        coeffs_magnus_group<DC, DS>(p, e[k], m, qr, qi, qz);
-        c.next(m, qr, qi, qz);
+        coeffs_tan_magnus<DT>(p, e[k], tr, ti, tz);
+        c.next_z(tr, ti, tz);
     }
-    c.finish(p);
+    c.template finish<kTanNormDegree(G)>(p);
+}
+
+// A MAGNUS4 step of a grouped run outside whole groups (ragged start or end).
+template <int G, int DT, typename Pt>
+__device__ __forceinline__ void step_single_tan_magnus(Pt &p, const float4 &e)
+{
+    using V = decltype(p.ar);
+    TanChain<V> c;
+    V tr, ti, tz;
+    coeffs_tan_magnus<DT>(p, e, tr, ti, tz);
+    c.first_z(tr, ti, tz);
+    c.template finish<kTanNormDegree(G)>(p);
 }
 
 }  // namespace

@@ -103,8 +103,8 @@ struct ReqDesc {
     int32_t group;   // FP32_MIXED (every scheme): the steps (G j, ..., G j + G - 1) of
                      // absolute index are multiplied into one operator before one
                      // compensated update; G = 1 (every step alone), 2, 4, 8 or kGroupMax
-    int32_t tdeg;    // FP32_MIXED EXACT / STRANG_XY with G >= 2: degree DT of the tan
-                     // (and sec) series, one of kTanDegrees
+    int32_t tdeg;    // FP32_MIXED with G >= 2: degree DT of the tan (STRANG_XY: and
+                     // sec) series, one of kTanDegrees
     int32_t withhold_first_copy;  // test hook: announce chunk 0 but never copy it, so the
                                   // bounded wait for it runs out (no fault, no hang)
     int32_t strips;  // 1: row strips (nx a multiple of kStripWidth): CTA tile b is rows
@@ -128,10 +128,9 @@ struct ReqDesc {
 // samples 1 and 2, of 8 instead of 4 on sample 6) left the largest FP32_MIXED
 // error against FP64 where it was (2.13e-6 -> 2.18e-6, 1.76e-6 -> 1.96e-6,
 // 4.32e-6 -> 4.27e-6), and a TwoSum update in place of Fast2Sum changed none of
-// them.  MAGNUS4 groups, whose chain multiplies the steps themselves, keep 0.2.
+// them.  MAGNUS4 groups (tan-normalised too, with the sigma_z part in the chain)
+// keep 0.2, the angle at which they were measured.
 constexpr int kGroupMax = 16;
-// Highest series degree with step groups (see kGroupedLevel in the kernels).
-constexpr int kGroupMaxDegree = 4;
 constexpr double kGroupAngleTan = 0.27;
 constexpr double kGroupAngleMagnus = 0.2;
 

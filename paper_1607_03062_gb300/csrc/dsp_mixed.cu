@@ -7,7 +7,7 @@
 namespace dsp {
 namespace {
 
-// The launch's steps on the tile's packs, G = 1 or MAGNUS4 (any G): the series
+// The launch's steps on the tile's packs one at a time (G = 1): the series
 // level's degrees (DC, DS) are compile-time constants.
 template <int SCHEME, int DC, int DS>
 __device__ __forceinline__ bool run_level(const ReqDesc &R, unsigned char *smem, uint64_t *bars,
@@ -20,29 +20,6 @@ __device__ __forceinline__ bool run_level(const ReqDesc &R, unsigned char *smem,
             for (int k = 0; k < NP; ++k)
                 step_magnus2<DC, DS>(pk[k], e);
         };
-        if constexpr (kGroupedLevel<DC, DS>) {
-            const auto group = [&](auto gc, const float4 *e) {
-#pragma unroll
-                for (int k = 0; k < NP; ++k)
-                    step_group_magnus<decltype(gc)::value, DC, DS>(pk[k], e);
-            };
-            if (R.group == kGroupMax)
-                return run_step_groups<float4, kGroupMax>(R, smem, bars, err, single, [&](const float4 *e) {
-                    group(std::integral_constant<int, kGroupMax>{}, e);
-                });
-            if (R.group == 8)
-                return run_step_groups<float4, 8>(R, smem, bars, err, single, [&](const float4 *e) {
-                    group(std::integral_constant<int, 8>{}, e);
-                });
-            if (R.group == 4)
-                return run_step_groups<float4, 4>(R, smem, bars, err, single, [&](const float4 *e) {
-                    group(std::integral_constant<int, 4>{}, e);
-                });
-            if (R.group == 2)
-                return run_step_groups<float4, 2>(R, smem, bars, err, single, [&](const float4 *e) {
-                    group(std::integral_constant<int, 2>{}, e);
-                });
-        }
         return run_steps<float4>(R, smem, bars, err, single);
     } else {
         return run_steps<float2>(R, smem, bars, err, [&](const float2 &e) {
@@ -69,24 +46,39 @@ __device__ __forceinline__ bool dispatch_level(const ReqDesc &R, unsigned char *
     return run_level<SCHEME, kLevelsF32[L].dc, kLevelsF32[L].ds>(R, smem, bars, err, pk);
 }
 
-// EXACT / STRANG_XY in tan-normalised groups of G steps, tan series of degree DT.
+// Tan-normalised groups of G steps (every scheme), tan series of degree DT.
 template <int SCHEME, int G, int DT>
 __device__ __forceinline__ bool run_tan(const ReqDesc &R, unsigned char *smem, uint64_t *bars,
                                         int *err, MixedPack (&pk)[kMixedSpt / 2])
 {
     constexpr int NP = kMixedSpt / 2;
-    return run_step_groups<float2, G>(
-        R, smem, bars, err,
-        [&](const float2 &e) {
+    if constexpr (SCHEME == 2) {
+        return run_step_groups<float4, G>(
+            R, smem, bars, err,
+            [&](const float4 &e) {
 #pragma unroll
-            for (int k = 0; k < NP; ++k)
-                step_single_tan<G, DT, SCHEME>(pk[k], e);
-        },
-        [&](const float2 *e) {
+                for (int k = 0; k < NP; ++k)
+                    step_single_tan_magnus<G, DT>(pk[k], e);
+            },
+            [&](const float4 *e) {
 #pragma unroll
-            for (int k = 0; k < NP; ++k)
-                step_group_tan<G, DT, SCHEME>(pk[k], e);
-        });
+                for (int k = 0; k < NP; ++k)
+                    step_group_tan_magnus<G, DT>(pk[k], e);
+            });
+    } else {
+        return run_step_groups<float2, G>(
+            R, smem, bars, err,
+            [&](const float2 &e) {
+#pragma unroll
+                for (int k = 0; k < NP; ++k)
+                    step_single_tan<G, DT, SCHEME>(pk[k], e);
+            },
+            [&](const float2 *e) {
+#pragma unroll
+                for (int k = 0; k < NP; ++k)
+                    step_group_tan<G, DT, SCHEME>(pk[k], e);
+            });
+    }
 }
 
 template <int SCHEME, int G, int I>
@@ -106,16 +98,14 @@ template <int SCHEME>
 __device__ __forceinline__ bool run_mixed(const ReqDesc &R, unsigned char *smem, uint64_t *bars,
                                           int *err, MixedPack (&pk)[kMixedSpt / 2])
 {
-    if constexpr (SCHEME != 2) {
-        if (R.group == kGroupMax)
-            return dispatch_tan_degree<SCHEME, kGroupMax, 0>(R, smem, bars, err, pk);
-        if (R.group == 8)
-            return dispatch_tan_degree<SCHEME, 8, 0>(R, smem, bars, err, pk);
-        if (R.group == 4)
-            return dispatch_tan_degree<SCHEME, 4, 0>(R, smem, bars, err, pk);
-        if (R.group == 2)
-            return dispatch_tan_degree<SCHEME, 2, 0>(R, smem, bars, err, pk);
-    }
+    if (R.group == kGroupMax)
+        return dispatch_tan_degree<SCHEME, kGroupMax, 0>(R, smem, bars, err, pk);
+    if (R.group == 8)
+        return dispatch_tan_degree<SCHEME, 8, 0>(R, smem, bars, err, pk);
+    if (R.group == 4)
+        return dispatch_tan_degree<SCHEME, 4, 0>(R, smem, bars, err, pk);
+    if (R.group == 2)
+        return dispatch_tan_degree<SCHEME, 2, 0>(R, smem, bars, err, pk);
     return dispatch_level<SCHEME, 0>(R, smem, bars, err, pk);
 }
 

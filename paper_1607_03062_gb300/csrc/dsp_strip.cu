@@ -25,7 +25,7 @@ namespace {
 // of a step's coefficients that depends on dt P_y alone is computed once per row
 // and step into a table in shared memory (built for each chunk of steps), and
 // the part that depends on dt P_x alone once per thread and step, as scalars.
-// Steps taken one at a time (G = 1) and MAGNUS4 groups:
+// Steps taken one at a time (G = 1):
 //   EXACT:     rows dt P_y and fl(dt P_y^2); column dt P_x;
 //   STRANG_XY: rows cos(dt P_y) - 1 and sin(dt P_y); column cos(dt P_x) - 1 and
 //              sin(dt P_x) (with dt P_x = 2a of the split);
@@ -34,13 +34,14 @@ namespace {
 // Tan-normalised groups (G >= 2):
 //   EXACT:     rows dt P_y and fl(dt P_y^2); column dt P_x (tan degree 1: rows
 //              dt P_y and fl(fl(c1 dt P_y) dt P_y), column dt P_x and fl(c1 dt P_x));
-//   STRANG_XY: rows tan(dt P_y); column tan(dt P_x) and sec(dt P_x) - 1.
+//   STRANG_XY: rows tan(dt P_y); column tan(dt P_x) and sec(dt P_x) - 1;
+//   MAGNUS4:   as for its single steps.
 // Every operation on a point is the contiguous path's (same operands, same
 // order, same rounding), so each point's result is bitwise the same on either
 // tiling; only the work per step shrinks.  Coefficient lane-ops per spinor-step
 // of the groups: EXACT 3.5 + DT instead of 8 + DT (DT = 1: 3.75 instead of 10);
 // STRANG_XY 1 per spinor plus (4 + 2 DT)/4 per thread instead of 9 + 3 DT;
-// MAGNUS4 7.5 + dc + ds instead of 12 + dc + ds.
+// MAGNUS4 7.5 + DT instead of 12 + DT.
 // ---------------------------------------------------------------------------
 
 #if !defined(DSP_STRIP_SCHEME) || !defined(DSP_STRIP_NP)
@@ -82,12 +83,11 @@ struct StripSmem {
 static_assert(sizeof(StripSmem) <= 48 * 1024, "static shared memory of one CTA");
 
 // The row part of a step for the two rows of a pack, from dt P_y of each (and,
-// for MAGNUS4, the step's D_x), for steps taken one at a time (G = 1) and
-// MAGNUS4 groups:
+// for MAGNUS4, the step's D_x), for steps taken one at a time (G = 1):
 //   EXACT     {P_y(r0), P_y(r1), fl(P_y(r0)^2), fl(P_y(r1)^2)}
 //   STRANG_XY {cy(r0), cy(r1), sb(r0), sb(r1)}, cy = cos b - 1, sb = sin b, b = dt P_y
 //   MAGNUS4   {P_y(r0), P_y(r1), -fl(P_y(r0) D_x), -fl(P_y(r1) D_x)}
-// each as coeffs_strang / coeffs_magnus_group form it for one lane.
+// each as coeffs_strang / step_magnus2 form it for one lane.
 template <int SCHEME, int DC, int DS>
 __device__ __forceinline__ float4 strip_row(float y0, float y1, float dx)
 {
@@ -109,10 +109,13 @@ __device__ __forceinline__ float4 strip_row(float y0, float y1, float dx)
 //   EXACT     {P_y(r0), P_y(r1), fl(P_y(r0)^2), fl(P_y(r1)^2)}; with tan degree 1
 //             {P_y(r0), P_y(r1), fl(fl(c1 P_y(r0)) P_y(r0)), fl(fl(c1 P_y(r1)) P_y(r1))}
 //   STRANG_XY {tan b(r0), tan b(r1), 0, 0}, b = dt P_y
+//   MAGNUS4   {P_y(r0), P_y(r1), -fl(P_y(r0) D_x), -fl(P_y(r1) D_x)} (coeffs_tan_magnus's)
 template <int SCHEME, int DT>
-__device__ __forceinline__ float4 strip_row_tan(float y0, float y1)
+__device__ __forceinline__ float4 strip_row_tan(float y0, float y1, float dx)
 {
-    if constexpr (SCHEME == 0 && DT == 1) {  // coeffs_tan's row part fl(fl(c1 P_y) P_y)
+    if constexpr (SCHEME == 2) {  // coeffs_tan_magnus's row part, as for single steps
+        return make_float4(y0, y1, -__fmul_rn(y0, dx), -__fmul_rn(y1, dx));
+    } else if constexpr (SCHEME == 0 && DT == 1) {  // coeffs_tan's row part fl(fl(c1 P_y) P_y)
         return make_float4(y0, y1, __fmul_rn(__fmul_rn(kTanC1, y0), y0),
                            __fmul_rn(__fmul_rn(kTanC1, y1), y1));
     } else if constexpr (SCHEME == 0) {
@@ -131,7 +134,8 @@ __device__ __forceinline__ float4 strip_row_tan(float y0, float y1)
 //   MAGNUS4   a = (P_x, P_x), b = (D_y, D_y) (P_x from dt Abar_x);
 // of the tan-normalised groups (strip_col_tan):
 //   EXACT     a = (P_x, P_x) (tan degree 1: b = (fl(c1 P_x), fl(c1 P_x)));
-//   STRANG_XY a = (tan 2a, tan 2a), b = (sec 2a - 1, sec 2a - 1).
+//   STRANG_XY a = (tan 2a, tan 2a), b = (sec 2a - 1, sec 2a - 1);
+//   MAGNUS4   as for its single steps.
 struct StripCol {
     float2 a, b;
 };
@@ -153,10 +157,12 @@ __device__ __forceinline__ StripCol strip_col(float pxh, float pxl, float ax, fl
 }
 
 template <int SCHEME, int DT>
-__device__ __forceinline__ StripCol strip_col_tan(float pxh, float pxl, float ax)
+__device__ __forceinline__ StripCol strip_col_tan(float pxh, float pxl, float ax, float dy)
 {
     const float px = __fadd_rn(pxh, __fadd_rn(ax, pxl));
-    if constexpr (SCHEME == 0 && DT == 1) {  // coeffs_tan's column part fl(c1 P_x)
+    if constexpr (SCHEME == 2) {
+        return StripCol{make_float2(px, px), make_float2(dy, dy)};
+    } else if constexpr (SCHEME == 0 && DT == 1) {  // coeffs_tan's column part fl(c1 P_x)
         const float cpx = __fmul_rn(kTanC1, px);
         return StripCol{make_float2(px, px), make_float2(cpx, cpx)};
     } else if constexpr (SCHEME == 0) {
@@ -203,19 +209,18 @@ __device__ __forceinline__ void strip_coeffs_strang(const StripCol &c, float4 r,
     m = vfma(c.a, cy, vadd(c.a, cy));
 }
 
-// (m, q, q_z) of a MAGNUS4 step for a pack in coeffs_magnus_group's form.
-template <int DC, int DS>
-__device__ __forceinline__ void strip_coeffs_magnus(const StripCol &c, float4 r, float2 &m,
-                                                    float2 &qr, float2 &qi, float2 &qz)
+// (tau, tz) of a MAGNUS4 step for a pack in coeffs_tan_magnus's form.
+template <int DT>
+__device__ __forceinline__ void strip_coeffs_tan_magnus(const StripCol &c, float4 r, float2 &tr,
+                                                        float2 &ti, float2 &tz)
 {
     const float2 Py = make_float2(r.x, r.y), nyx = make_float2(r.z, r.w);
     const float2 nz = vfma(c.a, c.b, nyx);
     const float2 x = vfma(c.a, c.a, vfma(Py, Py, vmul(nz, nz)));
-    m = vmul(vhorner<float2, DC, 1, 0>(x), x);
-    const float2 s1 = vmul(vhorner<float2, DS, 1, 1>(x), x);  // sin|n|/|n| - 1
-    qr = vfma(s1, Py, Py);
-    qi = vfma(s1, c.a, c.a);
-    qz = vfma(s1, nz, nz);
+    const float2 t1 = vmul(vseries<float2, TanCoef, DT, 1>(x), x);  // tan|n|/|n| - 1
+    tr = vfma(t1, Py, Py);
+    ti = vfma(t1, c.a, c.a);
+    tz = vfma(t1, nz, nz);
 }
 
 // (m, q) of an EXACT step alone, in coeffs_exact2's form.
@@ -244,7 +249,37 @@ struct StripThread {
     template <int DT>
     __device__ __forceinline__ StripCol col_tan(int j) const
     {
-        return strip_col_tan<SCHEME, DT>(pxh, pxl, sm->ax[j]);
+        return strip_col_tan<SCHEME, DT>(pxh, pxl, sm->ax[j], SCHEME == 2 ? sm->dy[j] : 0.0f);
+    }
+    // the first and a further step of a pack's tan-normalised chain (MAGNUS4 with its
+    // sigma_z part, first_z / next_z)
+    template <int DT>
+    __device__ __forceinline__ void chain_first(TanChain<float2> &ch, const StripCol &c,
+                                                float4 r) const
+    {
+        float2 tr, ti;
+        if constexpr (SCHEME == 2) {
+            float2 tz;
+            strip_coeffs_tan_magnus<DT>(c, r, tr, ti, tz);
+            ch.first_z(tr, ti, tz);
+        } else {
+            strip_coeffs_tan<SCHEME, DT>(c, r, tr, ti);
+            ch.first(tr, ti);
+        }
+    }
+    template <int DT>
+    __device__ __forceinline__ void chain_next(TanChain<float2> &ch, const StripCol &c,
+                                               float4 r) const
+    {
+        float2 tr, ti;
+        if constexpr (SCHEME == 2) {
+            float2 tz;
+            strip_coeffs_tan_magnus<DT>(c, r, tr, ti, tz);
+            ch.next_z(tr, ti, tz);
+        } else {
+            strip_coeffs_tan<SCHEME, DT>(c, r, tr, ti);
+            ch.next(tr, ti);
+        }
     }
     // one step alone: step_exact2 (EXACT), step_strang (STRANG_XY), step_magnus2 (MAGNUS4)
     template <int DC, int DS>
@@ -271,75 +306,49 @@ struct StripThread {
             }
         }
     }
-    // a step of a tan-normalised run outside whole groups (step_single_tan)
+    // a step of a tan-normalised run outside whole groups (step_single_tan,
+    // step_single_tan_magnus)
     template <int G, int DT>
     __device__ __forceinline__ void single_tan(MixedPack (&pk)[NP], int j) const
     {
         const StripCol c = col_tan<DT>(j);
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            float2 tr, ti;
-            strip_coeffs_tan<SCHEME, DT>(c, sm->rows[j][q], tr, ti);
             TanChain<float2> ch;
-            ch.first(tr, ti);
+            chain_first<DT>(ch, c, sm->rows[j][q]);
             ch.template finish<kTanNormDegree(G)>(pk[q]);
         }
     }
-    // step_group_tan's chain, the packs advanced step by step
+    // step_group_tan's (step_group_tan_magnus's) chain, the packs advanced step by step
     template <int G, int DT>
     __device__ __forceinline__ void group_tan(MixedPack (&pk)[NP], int j) const
     {
         TanChain<float2> ch[NP];
-        float2 tr, ti;
         StripCol c = col_tan<DT>(j);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            strip_coeffs_tan<SCHEME, DT>(c, sm->rows[j][q], tr, ti);
-            ch[q].first(tr, ti);
-        }
-        c = col_tan<DT>(j + 1);
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            strip_coeffs_tan<SCHEME, DT>(c, sm->rows[j + 1][q], tr, ti);
-            ch[q].second(tr, ti);
-        }
-#pragma unroll kStripChainUnroll
-        for (int k = 2; k < G; ++k) {
-            c = col_tan<DT>(j + k);
+        for (int q = 0; q < NP; ++q)
+            chain_first<DT>(ch[q], c, sm->rows[j][q]);
+        int k = 1;
+        if constexpr (SCHEME != 2) {  // the second step, alpha = 1 still
+            c = col_tan<DT>(j + 1);
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                strip_coeffs_tan<SCHEME, DT>(c, sm->rows[j + k][q], tr, ti);
-                ch[q].next(tr, ti);
+                float2 tr, ti;
+                strip_coeffs_tan<SCHEME, DT>(c, sm->rows[j + 1][q], tr, ti);
+                ch[q].second(tr, ti);
             }
+            k = 2;
+        }
+#pragma unroll kStripChainUnroll
+        for (; k < G; ++k) {
+            c = col_tan<DT>(j + k);
+#pragma unroll
+            for (int q = 0; q < NP; ++q)
+                chain_next<DT>(ch[q], c, sm->rows[j + k][q]);
         }
 #pragma unroll
         for (int q = 0; q < NP; ++q)
             ch[q].template finish<kTanNormDegree(G)>(pk[q]);
-    }
-    // step_group_magnus's chain, the packs advanced step by step
-    template <int G, int DC, int DS>
-    __device__ __forceinline__ void group_magnus(MixedPack (&pk)[NP], int j) const
-    {
-        MagnusChain<float2> ch[NP];
-        float2 m, qr, qi, qz;
-        StripCol c = col<DC, DS>(j);
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            strip_coeffs_magnus<DC, DS>(c, sm->rows[j][q], m, qr, qi, qz);
-            ch[q].first(m, qr, qi, qz);
-        }
-#pragma unroll kStripChainUnroll
-        for (int k = 1; k < G; ++k) {
-            c = col<DC, DS>(j + k);
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                strip_coeffs_magnus<DC, DS>(c, sm->rows[j + k][q], m, qr, qi, qz);
-                ch[q].next(m, qr, qi, qz);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < NP; ++q)
-            ch[q].finish(pk[q]);
     }
 };
 
@@ -347,15 +356,15 @@ struct StripThread {
 // bulk copy (double buffered, bounded waits), expanded into the row table,
 // then stepped in groups of G aligned to absolute step indices (ragged ends one
 // step at a time, as run_step_groups).  G = 1: every step alone (series degrees
-// DC, DS).  G >= 2: tan-normalised groups of degree DT (EXACT, STRANG_XY) or
-// MAGNUS4 chains (DC, DS), as on the contiguous tiles.
+// DC, DS).  G >= 2: tan-normalised groups of tan degree DT, as on the
+// contiguous tiles.
 template <int SCHEME, int G, int DC, int DS, int DT, int NP>
 __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint64_t *bars, int *err,
                                           const StripThread<SCHEME, NP> &th,
                                           const float (&pyh)[2 * NP],
                                           const float (&pyl)[2 * NP], MixedPack (&pk)[NP])
 {
-    constexpr bool kTan = SCHEME != 2 && G >= 2;
+    constexpr bool kTan = G >= 2;
     using E = StripEntry<SCHEME>;
     using St = Stager<E, kStripStage>;
     constexpr int GA = G > St::kAlign ? G : St::kAlign;  // staging starts on a group and 16 bytes
@@ -401,7 +410,7 @@ __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint6
                 const float y0 = __fadd_rn(pyh[2 * q], __fadd_rn(a.y, pyl[2 * q]));
                 const float y1 = __fadd_rn(pyh[2 * q + 1], __fadd_rn(a.y, pyl[2 * q + 1]));
                 if constexpr (kTan)
-                    sm.rows[j][q] = strip_row_tan<SCHEME, DT>(y0, y1);
+                    sm.rows[j][q] = strip_row_tan<SCHEME, DT>(y0, y1, dx);
                 else
                     sm.rows[j][q] = strip_row<SCHEME, DC, DS>(y0, y1, dx);
             }
@@ -419,12 +428,8 @@ __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint6
             for (; j < len && (j & (G - 1)) != 0; ++j)  // ragged start
                 one(j);
 #pragma unroll kStripGroupUnroll
-            for (; j + G <= len; j += G) {
-                if constexpr (kTan)
-                    th.template group_tan<G, DT>(pk, j);
-                else
-                    th.template group_magnus<G, DC, DS>(pk, j);
-            }
+            for (; j + G <= len; j += G)
+                th.template group_tan<G, DT>(pk, j);
             for (; j < len; ++j)  // ragged end (last chunk only)
                 one(j);
         }
@@ -434,23 +439,13 @@ __device__ __forceinline__ bool run_strip(const ReqDesc &R, StripSmem &sm, uint6
 }
 
 // Block-uniform dispatch of a strip's steps: tan-normalised groups on (G, DT);
-// everything else on the series level (DC, DS), MAGNUS4 groups on G inside it.
+// single steps on the series level (DC, DS).
 template <int SCHEME, int DC, int DS, int NP>
 __device__ __forceinline__ bool strip_level_steps(const ReqDesc &R, StripSmem &sm, uint64_t *bars,
                                                   int *err, const StripThread<SCHEME, NP> &th,
                                                   const float (&pyh)[2 * NP],
                                                   const float (&pyl)[2 * NP], MixedPack (&pk)[NP])
 {
-    if constexpr (SCHEME == 2 && kGroupedLevel<DC, DS>) {
-        if (R.group == kGroupMax)
-            return run_strip<SCHEME, kGroupMax, DC, DS, 0>(R, sm, bars, err, th, pyh, pyl, pk);
-        if (R.group == 8)
-            return run_strip<SCHEME, 8, DC, DS, 0>(R, sm, bars, err, th, pyh, pyl, pk);
-        if (R.group == 4)
-            return run_strip<SCHEME, 4, DC, DS, 0>(R, sm, bars, err, th, pyh, pyl, pk);
-        if (R.group == 2)
-            return run_strip<SCHEME, 2, DC, DS, 0>(R, sm, bars, err, th, pyh, pyl, pk);
-    }
     return run_strip<SCHEME, 1, DC, DS, 0>(R, sm, bars, err, th, pyh, pyl, pk);
 }
 
@@ -488,16 +483,14 @@ __device__ __forceinline__ bool strip_steps(const ReqDesc &R, StripSmem &sm, uin
                                             const float (&pyh)[2 * NP],
                                             const float (&pyl)[2 * NP], MixedPack (&pk)[NP])
 {
-    if constexpr (SCHEME != 2) {
-        if (R.group == kGroupMax)
-            return strip_tan<SCHEME, kGroupMax, 0>(R, sm, bars, err, th, pyh, pyl, pk);
-        if (R.group == 8)
-            return strip_tan<SCHEME, 8, 0>(R, sm, bars, err, th, pyh, pyl, pk);
-        if (R.group == 4)
-            return strip_tan<SCHEME, 4, 0>(R, sm, bars, err, th, pyh, pyl, pk);
-        if (R.group == 2)
-            return strip_tan<SCHEME, 2, 0>(R, sm, bars, err, th, pyh, pyl, pk);
-    }
+    if (R.group == kGroupMax)
+        return strip_tan<SCHEME, kGroupMax, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+    if (R.group == 8)
+        return strip_tan<SCHEME, 8, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+    if (R.group == 4)
+        return strip_tan<SCHEME, 4, 0>(R, sm, bars, err, th, pyh, pyl, pk);
+    if (R.group == 2)
+        return strip_tan<SCHEME, 2, 0>(R, sm, bars, err, th, pyh, pyl, pk);
     return strip_level<SCHEME, 0>(R, sm, bars, err, th, pyh, pyl, pk);
 }
 
