@@ -139,8 +139,8 @@ class ClockSampler:
 # SHA-256 of the kernel source the counters were taken on; a different source
 # means the counters are stale and the traffic is reported as null.
 KERNEL_TRAFFIC = {
-    "evolve_strip_kernel": {"bytes": 100.34e6,
-                            "source_sha256": "c7880edb99dd9b74e800b8eeabd2abce03b197d1d11d6981548b23a50a0e1e72"},
+    "evolve_strip_kernel": {"bytes": 95.11e6,
+                            "source_sha256": "74889d15ce1ba2e7c4751818ff356b4b99ed59e4886b167b6c79eeb474c6e413"},
 }
 
 
