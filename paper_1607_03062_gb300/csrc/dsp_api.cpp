@@ -275,23 +275,32 @@ std::vector<ReqDesc> split_last_wave(const ReqDesc &r, int precision)
     std::vector<ReqDesc> out(1, r);
     if (!r.strips || !r.tail_split || r.strip_h != dsp::kStripHeight)
         return out;
-    // per kernel: [0] FP64, [1 + scheme] FP32_MIXED
+    // per kernel: [0] FP64, [1 + scheme] FP32_MIXED; looked up once for the process
+    // (handles may be used from different host threads, so under a lock)
+    static std::mutex cache_mutex;
     static int sms[4] = {0, 0, 0, 0}, per_sm[4] = {0, 0, 0, 0};
     const int p = precision == DSP_FP64 ? 0 : 1 + r.scheme;
-    if (sms[p] == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms[p], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            dsp::strip_ctas_per_sm(precision == DSP_FP64 ? 0 : 1, r.scheme, &per_sm[p]) !=
-                cudaSuccess ||
-            per_sm[p] < 1) {
-            cudaGetLastError();
-            sms[p] = -1;
+    int n_sm = 0, n_per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lock(cache_mutex);
+        if (sms[p] == 0) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms[p], cudaDevAttrMultiProcessorCount, dev) !=
+                    cudaSuccess ||
+                dsp::strip_ctas_per_sm(precision == DSP_FP64 ? 0 : 1, r.scheme, &per_sm[p]) !=
+                    cudaSuccess ||
+                per_sm[p] < 1) {
+                cudaGetLastError();
+                sms[p] = -1;
+            }
         }
+        n_sm = sms[p];
+        n_per_sm = per_sm[p];
     }
-    if (sms[p] <= 0)
+    if (n_sm <= 0)
         return out;
-    const int64_t S = static_cast<int64_t>(sms[p]) * per_sm[p];
+    const int64_t S = static_cast<int64_t>(n_sm) * n_per_sm;
     const int64_t ncb = r.nx / dsp::kStripWidth;
     const int64_t nstrips = (r.ny + dsp::kStripHeight - 1) / dsp::kStripHeight;
     const int64_t T = ncb * nstrips;
@@ -925,15 +934,17 @@ dsp_status dsp_solve_segmented(dsp_grid *g, int32_t segments, void *map_dev, dou
         // segments are short and latency bound, and the FP64 combine grows with S: one
         // segment-tile per two SMs.  At least 16 steps a segment.  (Measured on the 64^2
         // x 2000-step case, 4 tiles: S = 38 / 19 beat S = 76 by 8% / 40%.)
-        static int sms = 0;
-        if (sms == 0) {
-            int dev = 0;
+        // looked up once for the process (a thread-safe static initialisation)
+        static const int sms = [] {
+            int dev = 0, n = 0;
             if (cudaGetDevice(&dev) != cudaSuccess ||
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                n < 1) {
                 cudaGetLastError();
-                sms = 152;
+                return 152;
             }
-        }
+            return n;
+        }();
         const int64_t ctas = g->precision == DSP_FP64 ? sms : (sms + 1) / 2;
         S = (ctas + g->n_tiles - 1) / g->n_tiles;
         S = std::min<int64_t>(S, g->n_steps / 16);
