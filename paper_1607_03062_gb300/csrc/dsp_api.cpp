@@ -165,11 +165,24 @@ int32_t choose_group(int32_t precision, int32_t scheme, int32_t tdeg, double the
 }
 
 // dt * max over steps and box corners of |p + A_n| (|P| is convex in p, so the
-// maximum over the box is at a corner).
+// maximum over the box is at a corner).  The squared magnitude of a corner is
+// (c_x + A_x)^2 + (c_y + A_y)^2, and a rounded sum grows with either term, so
+// the largest corner of a step is the larger x square plus the larger y square:
+// two squares per coordinate and one square root for the whole table.  If the
+// squares overflow (|p + A| above ~1e154), the maximum is taken with hypot.
 double theta_max(const dsp_grid *g, const double *a_mid, int64_t n, double dt)
 {
+    const double cx0 = g->px_min, cx1 = g->px_max, cy0 = g->py_min, cy1 = g->py_max;
+    double m2 = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        const double x0 = cx0 + a_mid[2 * k], x1 = cx1 + a_mid[2 * k];
+        const double y0 = cy0 + a_mid[2 * k + 1], y1 = cy1 + a_mid[2 * k + 1];
+        m2 = std::max(m2, std::max(x0 * x0, x1 * x1) + std::max(y0 * y0, y1 * y1));
+    }
+    if (std::isfinite(m2))
+        return dt * std::sqrt(m2);
     double m = 0.0;
-    const double cx[2] = {g->px_min, g->px_max}, cy[2] = {g->py_min, g->py_max};
+    const double cx[2] = {cx0, cx1}, cy[2] = {cy0, cy1};
     for (int64_t k = 0; k < n; ++k)
         for (int i = 0; i < 2; ++i)
             for (int j = 0; j < 2; ++j)
@@ -452,8 +465,11 @@ dsp_status validate_grid_args(int32_t nx, int32_t ny, double px_min, double px_m
     return DSP_OK;
 }
 
+// Checks a pulse's arguments (and its step condition); *tmax_out, when given,
+// receives theta_max of the table (0 for an empty one).
 dsp_status validate_pulse_args(const dsp_grid *g, const double *a_mid, int64_t n_steps, double dt,
-                               const double a_in[2], const double a_out[2])
+                               const double a_in[2], const double a_out[2],
+                               double *tmax_out = nullptr)
 {
     if (n_steps < 0 || (n_steps > 0 && !a_mid) || !a_in || !a_out)
         return DSP_E_INVALID;
@@ -464,8 +480,11 @@ dsp_status validate_pulse_args(const dsp_grid *g, const double *a_mid, int64_t n
     for (int64_t k = 0; k < 2 * n_steps; ++k)
         if (!finite(a_mid[k]))
             return DSP_E_INVALID;
-    if (n_steps > 0 && theta_max(g, a_mid, n_steps, dt) > kPi)
+    const double tmax = n_steps > 0 ? theta_max(g, a_mid, n_steps, dt) : 0.0;
+    if (tmax > kPi)
         return DSP_E_CFL;
+    if (tmax_out)
+        *tmax_out = tmax;
     return DSP_OK;
 }
 
@@ -685,10 +704,10 @@ dsp_status prepare_pulse(dsp_grid *g, const double *a_mid, int64_t n_steps, doub
 {
     // every (A_x, A_y) sample of the table, whatever the samples per step
     const int64_t n_samples = n_steps * samples_per_step(g->scheme);
-    dsp_status s = validate_pulse_args(g, a_mid, n_samples, dt, a_in, a_out);
+    double tmax = 0.0;
+    dsp_status s = validate_pulse_args(g, a_mid, n_samples, dt, a_in, a_out, &tmax);
     if (s != DSP_OK)
         return s;
-    const double tmax = n_steps > 0 ? theta_max(g, a_mid, n_samples, dt) : 0.0;
     build_table(g, a_mid, n_steps, dt, host);
     g->has_pulse = true;
     g->n_steps = n_steps;
