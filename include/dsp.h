@@ -30,7 +30,8 @@
  *     dsp_solve_host and the server's step synchronise with the host;
  *   - a CUDA error is latched in the handle: that call and every later call on
  *     the handle return DSP_E_CUDA (destroy still frees what it can);
- *   - handles are not thread safe: one host thread per handle at a time.
+ *   - handles are not thread safe: one host thread per handle at a time
+ *     (distinct handles may be used from different host threads).
  */
 #ifndef DSP_H
 #define DSP_H
@@ -60,8 +61,9 @@ typedef int32_t dsp_status;
 #define DSP_FP32_MIXED 1 /* spinor in compensated FP32 (hi + lo); dt P_n formed as
                             dt p_hi + (dt A_n + dt p_lo) with dt p an FP32 hi/lo
                             pair and dt A_n one FP32 per step, rounded on the host
-                            with error feedback; cos/sin of the phase argument
-                            dt|P| in FP32; initial state in FP64               */
+                            with error feedback; the trigonometric factors of
+                            the phase argument dt|P| (cos/sin series, or the tan
+                            series of step groups) in FP32; initial state in FP64 */
 
 /* Time-step scheme. */
 #define DSP_SCHEME_EXACT 0     /* the paper's closed-form exponential (Sec. III)    */
