@@ -472,7 +472,7 @@ int orc_solve_points(int64_t npts, const double *px, const double *py, int schem
     return 0;
 }
 
-/* Cell-centred grid node (reading of "px in [a, b]" on an N-point grid). */
+/* Cell-centred grid node: the reading of a momentum interval [a, b] sampled at N points. */
 double orc_grid_node(double lo, double hi, int n, int i)
 {
     double h = (hi - lo) / (double)n;
