@@ -4,8 +4,8 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * benchmark's CPU-baseline leg may load this file.  It shares no code, header,
- * table or constant generator with the CUDA library; it is written to be read
- * against the paper line by line, not to be fast.
+ * table or constant generator with the CUDA library; it is written to be
+ * checked against the paper's equations by eye, not to be fast.
  *
  * Units: hbar = v_F = e = 1, energies and momenta in eV, time in hbar/eV.
  *

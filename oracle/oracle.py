@@ -11,8 +11,8 @@ Paper passages each function follows:
   * ``spinors``       -- Sec. II Eq. (free_spin1..4), normalised to 1.
   * ``step_matrix``   -- Sec. III closed form I cos(dt E) - i sigma.P sin(dt E)/E.
   * ``step_matrix_magnus4``, ``pulse_table_gauss`` -- the fourth-order Magnus
-                         decomposition (Sec. III: the midpoint rule "can be improved
-                         to higher order by other decompositions").
+                         decomposition (Sec. III notes that other decompositions
+                         would raise the order of the midpoint rule).
   * ``solve_points`` / ``solve_grid`` -- Sec. III Eq. (ev_op_dt) product of steps,
                          then the projection of Sec. II Eq. (pair_prod_homo).
   * ``density``       -- Sec. II Eq. (pair_prod_homo) with degeneracy 4.
