@@ -1,8 +1,8 @@
 """Runs GPU parity, time-parallel and serving cases against the library built
 with -DDSP_BOUNDS_CHECK: every device index that the normal build leaves
 unchecked (table ranges staged by a launch, a CTA's tile) is verified, and an
-out-of-range one would surface as DSP_E_BOUNDS and fail those tests.  This
-stands in for a memory checker, which this pool does not provide."""
+out-of-range one would surface as DSP_E_BOUNDS and fail those tests.  The
+library checks its own indexes here, in place of an external memory checker."""
 import os
 import subprocess
 import sys
