@@ -203,10 +203,11 @@ dsp_status dsp_density_noalloc(const void *map_dev, int32_t precision, int32_t n
                                double px_min, double px_max, double py_min, double py_max,
                                void *cuda_stream, double *n_host);
 
-/* The whole hot path in one call: evolves the remaining steps with the
- * projection fused into the same kernel, writes map_dev (may be NULL: then an
- * internal map is used) and the density to *n_host (may be NULL).
- * Synchronises when n_host is not NULL. */
+/* The whole hot path in one call: evolves the remaining steps (Sec. III, Eq.
+ * (ev_op_dt)) with the projection fused into the same kernel, writes map_dev
+ * (may be NULL: then an internal map is used) and the density (Sec. II, Eq.
+ * (pair_prod_homo)) to *n_host (may be NULL).  Synchronises when n_host is
+ * not NULL. */
 dsp_status dsp_solve(dsp_grid *g, void *map_dev, double *n_host);
 
 /* The whole hot path with the time axis split into `segments` pieces that run
@@ -225,9 +226,9 @@ dsp_status dsp_solve(dsp_grid *g, void *map_dev, double *n_host);
 dsp_status dsp_solve_segmented(dsp_grid *g, int32_t segments, void *map_dev, double *n_host);
 
 /* End to end with host buffers: copies the host pulse table in (as
- * dsp_set_pulse), runs dsp_solve, and copies the |c+|^2 map (double or float
- * by precision, nx*ny values) back to map_host (may be NULL) and the density
- * to *n_host.  Synchronises. */
+ * dsp_set_pulse), runs dsp_solve (Sec. III and Sec. II, as there), and copies
+ * the |c+|^2 map (double or float by precision, nx*ny values) back to map_host
+ * (may be NULL) and the density to *n_host.  Synchronises. */
 dsp_status dsp_solve_host(dsp_grid *g, const double *a_mid, int64_t n_steps, double dt,
                           const double a_in[2], const double a_out[2], void *map_host,
                           double *n_host);
@@ -243,7 +244,8 @@ dsp_status dsp_solve_host(dsp_grid *g, const double *a_mid, int64_t n_steps, dou
  * grid's next synchronising call, not by the others'. */
 dsp_status dsp_evolve_batch(dsp_grid *const *grids, const int64_t *steps, int32_t count);
 
-/* Cursor and pulse length of a grid. */
+/* Cursor and pulse length of a grid (bookkeeping: the paper has no
+ * counterpart). */
 dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps);
 
 /* What the library chose for the current pulse: the degrees (in theta^2) of
@@ -300,7 +302,8 @@ dsp_status dsp_test_withhold_next_copy(dsp_grid *g);
 dsp_status dsp_test_tiling(dsp_grid *g, int32_t tiling);
 
 /* Copies the raw spinor state (dsp_state_bytes bytes) to the host, or back
- * from the host, with the step cursor, for checkpoint / resume.  Synchronise. */
+ * from the host, with the step cursor, for checkpoint / resume.  Synchronise.
+ * Checkpointing only: the paper has no counterpart. */
 dsp_status dsp_save_state(dsp_grid *g, void *host_buf, int64_t bytes, int64_t *cursor);
 dsp_status dsp_load_state(dsp_grid *g, const void *host_buf, int64_t bytes, int64_t cursor);
 
@@ -308,7 +311,7 @@ dsp_status dsp_load_state(dsp_grid *g, const void *host_buf, int64_t bytes, int6
  * Resource management only: the paper has no counterpart. */
 dsp_status dsp_destroy_grid(dsp_grid *g);
 
-/* Static string for a status code. */
+/* Static string for a status code (the paper has no counterpart). */
 const char *dsp_status_string(dsp_status s);
 
 /* ------------------------------------------------------------------------- */
@@ -334,13 +337,16 @@ typedef struct {
     double E0, omega, T, tau, t0, eps, phase2, Omega_rise, Omega_fall, phi;
 } dsp_pulse_spec;
 
-/* t_i = 0, t_f = T, dt = T/n_steps.  a_mid: host [n_steps][2] at
- * (n + 1/2) dt; a_in = A(0); a_out = A(T); *dt_out = dt.  n_steps >= 1. */
+/* The midpoint samples of Sec. III, Eq. (approx_time), and the asymptotic
+ * A_in, A_out of Sec. II: t_i = 0, t_f = T, dt = T/n_steps.  a_mid: host
+ * [n_steps][2] at (n + 1/2) dt; a_in = A(0); a_out = A(T); *dt_out = dt.
+ * n_steps >= 1. */
 dsp_status dsp_sample_pulse(const dsp_pulse_spec *spec, int64_t n_steps, double *a_mid,
                             double *a_in, double *a_out, double *dt_out);
 
-/* The same for DSP_SCHEME_MAGNUS4: a_gauss host [n_steps][2][2], A at
- * (n + 1/2 - sqrt(3)/6) dt and (n + 1/2 + sqrt(3)/6) dt. */
+/* The same for DSP_SCHEME_MAGNUS4 (the higher-order decomposition Sec. III
+ * mentions): a_gauss host [n_steps][2][2], A at (n + 1/2 - sqrt(3)/6) dt and
+ * (n + 1/2 + sqrt(3)/6) dt, the two Gauss points of each step. */
 dsp_status dsp_sample_pulse_gauss(const dsp_pulse_spec *spec, int64_t n_steps, double *a_gauss,
                                   double *a_in, double *a_out, double *dt_out);
 
@@ -409,7 +415,8 @@ dsp_status dsp_server_query(dsp_server *s, int64_t id, int32_t *state, double *d
  * step.  Other requests are unaffected. */
 dsp_status dsp_server_cancel(dsp_server *s, int64_t id);
 
-/* Frees everything.  NULL is OK. */
+/* Frees everything.  NULL is OK.  (Like every dsp_server_* call: serving
+ * only, the paper has no counterpart.) */
 dsp_status dsp_server_destroy(dsp_server *s);
 
 #ifdef __cplusplus
