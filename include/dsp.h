@@ -80,7 +80,8 @@ typedef struct dsp_grid dsp_grid;
 
 /* Bytes of device state one grid needs: 32 bytes per point for both
  * precisions (FP64: two complex doubles; FP32_MIXED: hi and lo float4 planes).
- * Returns -1 on invalid sizes or precision. */
+ * Returns -1 on invalid sizes or precision.  (Memory layout of this library:
+ * the paper has no counterpart.) */
 int64_t dsp_state_bytes(int32_t nx, int32_t ny, int32_t precision);
 
 /* Creates a grid.  nx, ny >= 1 and nx*ny <= 2^31 - 1; px_min < px_max and
@@ -255,14 +256,14 @@ dsp_status dsp_get_cursor(const dsp_grid *g, int64_t *cursor, int64_t *n_steps);
  * group_steps G: the number of step operators multiplied into one before each
  * compensated update (FP32_MIXED, every scheme: the largest of 16, 8, 4, 2 with
  * G * theta_max <= 0.27 for EXACT and STRANG_XY, <= 0.2 for MAGNUS4, else 1; 1
- * in FP64), and for EXACT and STRANG_XY groups
- * tan_degree, the degree in theta^2 of the tan(theta)/theta (and sec) series
- * (0 when G = 1).  Not in the paper: with G > 1 the update is paid once per
- * group.  EXACT and STRANG_XY groups multiply the steps divided by their real
- * diagonal cos(theta) (a step then costs 8 multiply-adds instead of 12) and
- * divide the product by the square root of its determinant; MAGNUS4 groups
- * multiply the steps themselves and rebuild Re(alpha) - 1 from unitarity.
- * Either way the applied operator is unitary to FP32 rounding. */
+ * in FP64), and tan_degree, the degree in theta^2 of the groups' tan series
+ * (EXACT: tan(theta)/theta; STRANG_XY: tan and sec; MAGNUS4: tan|n|/|n| in
+ * |n|^2; 0 when G = 1).  Not in the paper: with G > 1 the update is paid once
+ * per group.  The groups multiply the steps divided by the cosine on their
+ * diagonal (EXACT and STRANG_XY: the real diagonal cos(theta), so a step of
+ * the product costs 8 multiply-adds instead of 12; MAGNUS4: cos|n|) and divide
+ * the product by the square root of its determinant, so the applied operator
+ * is unitary to FP32 rounding. */
 typedef struct {
     int32_t nx, ny, precision, scheme, valley;
     int32_t cos_degree, sinc_degree;
@@ -280,6 +281,8 @@ typedef struct {
                            in use. */
     int32_t tan_degree; /* see above */
 } dsp_grid_info;
+/* Fills *info for the grid's current pulse (the fields above; bookkeeping,
+ * the paper has no counterpart). */
 dsp_status dsp_get_info(const dsp_grid *g, dsp_grid_info *info);
 
 /* Test hook for the failure path (not in the paper).  The next launch on this

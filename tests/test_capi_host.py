@@ -32,6 +32,24 @@ def test_header_declares_what_the_binding_wraps():
     assert declared_functions() == sorted(B.EXPORTS)
 
 
+def test_every_entry_point_cites_its_passage_or_has_none():
+    """Each declaration's comment (the last one before it) cites the paper's
+    section or equation that defines the operation, or says that the paper has
+    no counterpart; the serving calls sit under a section comment that says so."""
+    text = open(HEADER).read()
+    serving = text.find("/* Serving:")
+    assert serving > 0 and "not in the paper" in text[serving:serving + 200]
+    names = []
+    for m in re.finditer(r"^(?:dsp_status|int64_t|const char \*)\s*(dsp_\w+)\s*\(", text, re.M):
+        name = m.group(1)
+        names.append(name)
+        before = text[:m.start()]
+        comment = before[before.rfind("/*"):]
+        cites = re.search(r"Sec\.|Eq\.|no[\s*]+counterpart|not in the paper", comment, re.I)
+        assert cites or (name.startswith("dsp_server_") and m.start() > serving), name
+    assert sorted(names) == declared_functions()
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
