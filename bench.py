@@ -249,9 +249,27 @@ def ops_fp64(dc, ds, strips=False):
     arithmetic, series degrees dc and ds; 2 FP64 adds to bring them to double) + q (2) +
     the update (12) = 18, whatever the degrees.  On row strips dt P_x is formed once per
     thread for its 4 spinors (0.25 each) and dt P_y comes from the strip's row table:
-    16.25.  The ~100 FP32 operations of the series issue beside them and are not
-    counted against the FP64 peak."""
+    16.25.  The FP32 instructions of the series (about 300 per spinor-step at degrees
+    (5, 5)) issue beside them and are not counted against the FP64 peak."""
     return 16.25 if strips else 18.0
+
+
+def launches_per_solve(n, strips, sms, ctas_per_sm=2):
+    """Kernel launches of one dsp_solve of an n x n grid: the evolve launch (on row
+    strips, split in two when the library runs the last wave of CTAs in 2-row strips,
+    by the same rule as its split_last_wave: 4-row strips of 256 columns, the strip
+    kernel's 2 CTAs per SM) and the density finalize."""
+    evolve = 1
+    if strips:
+        ncb, nstrips = n // 256, (n + 3) // 4
+        slots = sms * ctas_per_sm
+        rem = (ncb * nstrips) % slots
+        if rem:
+            k = min(nstrips, (rem + ncb - 1) // ncb)
+            tail_tiles = ncb * ((n - 4 * (nstrips - k) + 1) // 2)
+            if tail_tiles <= slots and nstrips > k:
+                evolve = 2
+    return evolve + 1
 
 
 # ------------------------------------------------------------------------------------------
@@ -476,7 +494,9 @@ def run_gpu(args):
                    "samples_rotated": N_SAMPLES, "scheme": "exact midpoint exponential",
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world} (independent samples per rank)"},
-        "gpu_launches": 2 * args.steps, "e2e": e2e,
+        "gpu_launches": args.steps * launches_per_solve(
+            n, strips_used, torch.cuda.get_device_properties(local).multi_processor_count),
+        "e2e": e2e,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
         "arithmetic": "FP32 spinor stored compensated (hi + lo); momentum p + A from an FP32 "

@@ -280,7 +280,7 @@ bool project_only(const ReqDesc &r)
 // last wave of r = T mod S tiles that is at most half full, the last ceil(r /
 // (nx / 256)) 4-row strips are launched instead as twice as many 2-row strips
 // (strip_h = 2, the same points at half the work per CTA), so that the last
-// wave takes about half as long.  Grids of less than one wave are all 2-row
+// wave takes about half as long.  Grids of at most half a wave are all 2-row
 // strips.  Every point's arithmetic, and every granule, is unchanged: only
 // which CTA computes which rows.  Returns the descriptors to launch.
 std::vector<ReqDesc> split_last_wave(const ReqDesc &r, int precision)
